@@ -1,0 +1,330 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the explicit mass-spring step on one GB300.
+
+Workload (default): the 256^3 throughput lattice -- 16,777,216 masses,
+216,338,940 26-neighbourhood springs (k ~ U[5e3, 5e4] N/m per spring,
+c = 0.05 N s/m, bottom layer anchored, v ~ N(0, 1e-3) m/s, dt = 5e-5 s,
+gravity on, no contact).  A bench "step" is one explicit time step over the
+whole lattice (every spring and every mass updated once).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun with N > 1 every rank runs its
+own independent lattice (weak scaling, no data-path collective); the time is
+the max over ranks.  --impl reference times the CPU oracle on the host cores
+over a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "element updates/s (springs+masses) & %HBM roofline; batched robot-sim-s/s"
+UNIT = "elements/s"
+FALLBACK_HBM_GBS = 6800.0
+# algorithmic bytes of one step (general-graph model): per mass read x, v
+# (24 B) + write x, v (24 B) + inverse mass (4 B); per spring i, j, k, L0 (16 B)
+BYTES_PER_MASS = 52
+BYTES_PER_SPRING = 16
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_traffic(kernel_src: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        with open(kernel_src, "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()[:16]
+        ent = d.get("k_step")
+        if ent and ent.get("source_sha256_16") == h:
+            return ent
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for _, _, flags in rows for q, f in enumerate(flags) if f.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def lattice_workload(n: int):
+    s = synth.throughput_lattice(n=n)
+    p = synth.throughput_params()
+    return s, p
+
+
+def workload_config(n, N, S):
+    return {"workload": f"lattice{n} ({n}^3 masses, 26-neighbourhood springs, k~U[5e3,5e4], c=0.05, "
+                        f"anchored bottom layer, v~N(0,1e-3), dt=5e-5, gravity, no contact)",
+            "n_masses": N, "n_springs": S, "elements_per_step": N + S,
+            "l2": "working set > L2 (no flush needed)", "byte_model": "G (52 B/mass + 16 B/spring)"}
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_sample(max_seconds: float = 15.0, side: int = 40):
+    """Time the FP64 oracle on a bounded sample of the workload: a side^3
+    lattice with the same parameters, as many steps as fit in max_seconds."""
+    import oracle
+    s, p = lattice_workload(side)
+    ar = oracle._Arrays(s)
+    x, v = s["x"], s["v"]
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        x, v = oracle.run(s, p, 1, n0=steps, x=x, v=v, arrays=ar)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= max_seconds or steps >= 10000:
+            break
+    N, S = s["x"].shape[0], s["ij"].shape[0]
+    return {"value": steps * (N + S) / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{side}^3 lattice with the workload's parameters, {steps} steps, {el:.1f} s, single thread FP64"}
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the FP64 oracle as it stands, single-threaded on the host,
+    one oracle step per bench step on a bounded sample (ref_side^3 lattice with
+    the workload's parameters)."""
+    if rank != 0:
+        return 0
+    import oracle
+    side = args.ref_side
+    s, p = lattice_workload(side)
+    ar = oracle._Arrays(s)
+    x, v = s["x"], s["v"]
+    for q in range(args.warmup):
+        x, v = oracle.run(s, p, 1, n0=q, x=x, v=v, arrays=ar)
+    t0 = time.perf_counter()
+    for q in range(args.steps):
+        x, v = oracle.run(s, p, 1, n0=args.warmup + q, x=x, v=v, arrays=ar)
+    el = time.perf_counter() - t0
+    Ns, Ss = s["x"].shape[0], s["ij"].shape[0]
+    val = (Ns + Ss) * args.steps / el
+    n = args.n
+    N = n ** 3
+    S = synth.lattice_spring_count(n, n, n)
+    sample = (f"{side}^3 lattice ({Ns} masses, {Ss} springs) with the workload's parameters, "
+              f"{args.steps} timed steps in {el:.2f} s, single-thread FP64; ms_per_step extrapolated to {n}^3")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": (N + S) / val * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "config": workload_config(n, N, S),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_2207_09334_gb300 as ms
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (no CPU fallback)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    ms.load()
+    n = args.n
+    t0 = time.perf_counter()
+    s, p = lattice_workload(n)
+    N, S = s["x"].shape[0], s["ij"].shape[0]
+    t_gen = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    sim = ms.Sim(s, p, reorder=False, stream=stream)
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t0
+    info = sim.info()
+
+    for _ in range(args.warmup):
+        sim.step(1)
+    sim.sync()
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        ev[0].record(stream)
+        for q in range(args.steps):
+            sim.step(1)
+            ev[q + 1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total_ms = ev[0].elapsed_time(ev[-1])
+    per = [ev[q].elapsed_time(ev[q + 1]) for q in range(args.steps)]
+    sim.sync()
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * (N + S) * args.steps / (total_ms * 1e-3)
+
+    # end to end through the public API with host buffers: upload the state
+    # from pinned host memory, run the workload's 200 steps, read it back
+    e2e_steps = args.e2e_sim_steps
+    xh = torch.from_numpy(np.ascontiguousarray(s["x"])).pin_memory()
+    vh = torch.from_numpy(np.ascontiguousarray(s["v"])).pin_memory()
+    xo = torch.empty_like(xh).pin_memory(); vo = torch.empty_like(vh).pin_memory()
+    e2e_times = []
+    for it in range(args.e2e_iters + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.set_state(xh, vh)
+        sim.step(e2e_steps)
+        sim.get_state(xo, vo)
+        el = time.perf_counter() - t0
+        if it > 0:
+            e2e_times.append(el)
+    e2e_val = world * (N + S) * e2e_steps / statistics.median(e2e_times)
+    bytes_state = 2 * N * 3 * 4
+
+    hbm, hbm_kind = peaks()
+    alg_bytes = BYTES_PER_MASS * N + BYTES_PER_SPRING * S
+    kern_ms = statistics.mean(per)
+    achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
+    tr = kernel_traffic(os.path.join(ROOT, "paper_2207_09334_gb300", "csrc", "ms_step.cu"))
+    traffic = None
+    if tr is not None:
+        traffic = tr["dram_bytes_per_launch_at_256"] * (N + S) / tr["elements_at_256"] if n != 256 else tr["dram_bytes_per_launch_at_256"]
+    cpu = oracle_sample(max_seconds=args.cpu_seconds) if (rank == 0 and world == 1 and args.cpu_seconds > 0) else None
+
+    clocks = clk.summary()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+            "config": dict(workload_config(n, N, S), parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
+                           setup_s={"generate": round(t_gen, 1), "create": round(t_create, 1)},
+                           device_bytes=info["device_bytes"], records=info["n_records"]),
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_state,
+                    "d2h_bytes_per_step": bytes_state,
+                    "note": f"each e2e step = ms_set_state(pinned host) + ms_step({e2e_steps}) + ms_get_state(pinned host)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": traffic,
+                         "kernel": "k_step", "peak_kind": f"{hbm_kind} (hbm_gbs)",
+                         "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": kern_ms},
+            "gpu_launches": args.steps,
+            "clocks": clocks}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=256, help="lattice side (256 = the benchmark workload)")
+    ap.add_argument("--e2e-sim-steps", type=int, default=200)
+    ap.add_argument("--e2e-iters", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-side", type=int, default=40)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

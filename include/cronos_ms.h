@@ -1,0 +1,176 @@
+/*
+ * cronos_ms.h -- C ABI of the GB300 mass-spring step library.
+ *
+ * The library advances a nonlinear Hookean mass-spring system with an
+ * explicit scheme on one GPU (sm_103a).  It implements the method of the
+ * Cronos paper (arXiv 2207.09334), section "Method":
+ *   eq. 1-3  m_i a_i = f_i,  f_i = m_i g + f_ext_i + sum_j k_ij (|l_ij| - L_ij) l_ij/|l_ij|,
+ *            l_ij = x_j - x_i, d/dt [x; v] = [v; f/m];
+ *   eq. 4    the explicit time step (read as symplectic Euler: v' = v + dt f/m,
+ *            x' = x + dt v', all forces taken at t_n);
+ *   Algorithm 1 ("Parallel Simulation Process"): spring forces, a grid-wide
+ *            synchronisation, then a per-mass sum and integration.  Here the
+ *            sum is a deterministic per-mass gather (no atomics of any kind).
+ * together with the features the paper names around it: axial spring
+ * damping, actuated ("volumetric") rest lengths, anchored masses, and
+ * ground contact planes with friction (Appendix A).
+ *
+ * Conventions for every entry point:
+ *   - Errors are status codes; nothing aborts or throws across the ABI.
+ *     ms_last_error() gives a message for the calling thread's last failure.
+ *   - All arrays are caller-owned and copied (inputs) or filled (outputs);
+ *     the library never keeps a caller pointer.
+ *   - Masses and springs are addressed in the caller's index order.  Any
+ *     internal reordering is invisible at the ABI.
+ *   - Work is enqueued on the CUDA stream given at creation (NULL = legacy
+ *     default stream).  ms_step is asynchronous; errors detected on the
+ *     device (non-finite state) are reported by the next synchronising call
+ *     (ms_sync, ms_get_state to host).
+ *   - Vectors are float32 triples, row-major (N,3).
+ */
+#ifndef CRONOS_MS_H
+#define CRONOS_MS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MS_OK = 0,
+    MS_ERR_ARG = 1,        /* invalid argument (null pointer, bad size or index, non-finite input) */
+    MS_ERR_OOM = 2,        /* device or host allocation failed */
+    MS_ERR_CUDA = 3,       /* a CUDA runtime call failed */
+    MS_ERR_UNSTABLE = 4,   /* strict_stability set and the step-size bound is violated */
+    MS_ERR_NONFINITE = 5,  /* the device saw a non-finite position or velocity */
+    MS_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up */
+    MS_ERR_STATE = 7       /* call not valid in the object's current state */
+} ms_status;
+
+/* Integration and environment parameters (paper: eq. 2-4; Appendix A for
+ * contact planes).  Ground plane is z = 0 with normal +z. */
+typedef struct {
+    float dt;               /* time step [s] */
+    float g[3];             /* gravity [m/s^2] */
+    float k_c;              /* ground penalty stiffness [N/m]: Fn = k_c max(0, -z), active when z < 0 */
+    float mu;               /* Coulomb friction coefficient on the ground (impulse clamp on tangential v) */
+    float vel_damping;      /* global damping d: v' *= (1 - d) every step (0 = off) */
+    int32_t contact_on;     /* 1 = ground contact active */
+    int32_t integrator;     /* 0 = symplectic Euler (only value supported by the GPU path) */
+    int32_t strict_stability; /* 1 = ms_create fails with MS_ERR_UNSTABLE if the bound below exceeds 4 */
+    int32_t reorder;        /* 0 = keep caller mass order, 1 = Morton order by initial position */
+} ms_params;
+
+/* Optional device allocator (e.g. a framework's caching allocator).
+ * alloc must return device memory aligned to at least 256 bytes usable on
+ * `stream`, or NULL on failure; free receives the same pointer and size. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *ctx);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *ctx);
+    void *ctx;
+} ms_allocator;
+
+typedef struct ms_sim ms_sim;   /* opaque; owns all of its device memory */
+
+typedef struct {
+    int64_t n_masses;          /* N */
+    int64_t n_springs;         /* caller springs S */
+    int64_t n_records;         /* springs after merging parallel springs (same pair) */
+    int64_t n_slots;           /* padded forward record slots (>= n_records) */
+    int64_t n_back_slots;      /* padded back-reference slots */
+    int64_t device_bytes;      /* device memory held */
+    int64_t step_count;        /* steps taken since creation */
+    double stability_bound;    /* dt^2 * max_i (2 sum_{springs at i} k + k_c) / m_i  (Gershgorin; stable if < 4) */
+    int32_t max_fwd_degree;
+    int32_t max_back_degree;
+} ms_info_t;
+
+/*
+ * ms_create -- build a simulation object from a general spring network
+ * (paper: "Generating a Lattice" final paragraph -- masses from nodes,
+ * springs from edges, copied to GPU memory; "GPU Implementation" -- each
+ * mass needs the list of springs attached to it).
+ *
+ *   p        parameters (copied).
+ *   N        number of masses, 1 <= N < 2^27.
+ *   x0, v0   (N,3) initial positions [m] and velocities [m/s].
+ *   mass     (N) masses [kg], > 0 and finite for masses that are not anchored.
+ *   fixed    (N) 1 = anchored: position frozen, velocity held at 0, still
+ *            exerts spring forces (NULL = none anchored).
+ *   fext     (N,3) constant external force [N] (NULL = none).
+ *   S        number of springs, >= 0.
+ *   ij       (S,2) endpoint indices in [0, N), i != j.
+ *   k        (S) stiffness [N/m] >= 0.
+ *   c        (S) axial dashpot coefficient [N s/m] >= 0, or NULL to use
+ *            c_uniform for every spring.
+ *   rest_len (S) rest length [m] >= 0, or NULL = initial distance.
+ *   alloc    device allocator, or NULL for cudaMalloc/cudaFree.
+ *   stream   cudaStream_t to enqueue all work on (NULL = default stream).
+ *   out      receives the new object.
+ * Parallel springs (same unordered pair) are merged into one record with
+ * summed stiffness and damping and the stiffness-weighted rest length; the
+ * merge is exact in real arithmetic because the force is linear in k and in
+ * k*L.  A mass may own at most 31 distinct higher-indexed partners after
+ * reordering (26 in a lattice).  Returns MS_ERR_ARG on invalid input,
+ * MS_ERR_OOM / MS_ERR_CUDA on allocation or copy failure, MS_ERR_UNSTABLE
+ * as described for strict_stability.  On failure *out is set to NULL.
+ */
+ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float *v0,
+                    const float *mass, const uint8_t *fixed, const float *fext,
+                    int64_t S, const int32_t *ij, const float *k, const float *c,
+                    float c_uniform, const float *rest_len, const ms_allocator *alloc,
+                    void *stream, ms_sim **out);
+
+/*
+ * ms_set_actuation -- actuated rest lengths (paper: Introduction and
+ * Applications -- self-actuation by dynamically modifying volumetric
+ * properties; Fig. 2 caption -- springs individually actuated).  Spring s
+ * then has rest length L0_s (1 + amp_s sin(2 pi freq t_n + phase_s)) at the
+ * start-of-step time t_n = n dt.  amp and phase are (S) arrays in caller
+ * spring order; amp = NULL switches actuation off.  Merged parallel springs
+ * combine exactly: sum_s k_s L_s(t) = K L0eff (1 + alpha sin(w t) + beta cos(w t)).
+ * The sine and cosine of 2 pi freq t_n are evaluated in FP64 on the host.
+ */
+ms_status ms_set_actuation(ms_sim *sim, float freq_hz, const float *amp, const float *phase);
+
+/*
+ * ms_step -- advance nsteps explicit steps (eq. 2-4, Algorithm 1), each
+ * reading the state at t_n and writing the state at t_{n+1} (double
+ * buffered).  Asynchronous on the object's stream.  nsteps >= 0.
+ */
+ms_status ms_step(ms_sim *sim, int32_t nsteps);
+
+/*
+ * ms_get_state / ms_set_state -- copy positions and velocities ((N,3) float32,
+ * caller order) out of / into the object.  on_device = 1: x and v are device
+ * pointers (stream-ordered, asynchronous); 0: host pointers (the call
+ * synchronises the stream; page-locked memory gives the fastest copies).
+ * Either pointer may be NULL to skip it.  ms_get_state to host also reports
+ * MS_ERR_NONFINITE if the device flagged a non-finite value.  ms_set_state
+ * keeps anchored masses' velocity at 0.
+ */
+ms_status ms_get_state(ms_sim *sim, float *x, float *v, int32_t on_device);
+ms_status ms_set_state(ms_sim *sim, const float *x, const float *v, int32_t on_device);
+
+/* ms_sync -- wait for the object's stream; returns MS_ERR_NONFINITE if a
+ * step produced a non-finite value since creation (sticky), else MS_OK. */
+ms_status ms_sync(ms_sim *sim);
+
+/* ms_get_info -- sizes and diagnostics of the object. */
+ms_status ms_get_info(const ms_sim *sim, ms_info_t *out);
+
+/* ms_destroy -- free all memory held by the object (after its stream's work). NULL is a no-op. */
+ms_status ms_destroy(ms_sim *sim);
+
+/* Message of the calling thread's last error (static storage, never NULL). */
+const char *ms_last_error(void);
+
+/* Library version string. */
+const char *ms_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CRONOS_MS_H */

@@ -1,0 +1,519 @@
+// ms_api.cu -- C ABI entry points and the host-side builder of the
+// mass-spring library (see include/cronos_ms.h for the contract).
+//
+// The builder turns a caller's spring list into the device layout described
+// in ms_internal.h:
+//   1. optional Morton reordering of the masses by initial position, so that
+//      springs connect masses that are close in memory;
+//   2. each spring is filed in the row of its lower-indexed endpoint; parallel
+//      springs (same pair) are merged (summed k and c, stiffness-weighted rest
+//      length), which is exact for a force linear in k and k*L;
+//   3. rows are laid out sliced-ELL (32 masses per slice), and every record
+//      gets a back reference in its partner's row.
+// Everything is O(S) except the optional Morton sort (O(N log N)).
+#include "../../include/cronos_ms.h"
+#include "ms_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+ms_status fail(ms_status st, const std::string &msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
+#define MS_CUDA_TRY(expr)                                                                     \
+    do {                                                                                      \
+        cudaError_t _e = (expr);                                                              \
+        if (_e != cudaSuccess)                                                                \
+            return fail(MS_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));    \
+    } while (0)
+
+struct Alloc {
+    void *ptr;
+    size_t bytes;
+};
+
+}  // namespace
+
+struct ms_sim {
+    ms_params p{};
+    int32_t N = 0;
+    int64_t S = 0;
+    cudaStream_t stream = nullptr;
+    ms_allocator alloc{};
+    bool custom_alloc = false;
+    std::vector<Alloc> allocs;
+    int64_t device_bytes = 0;
+
+    // ordering
+    bool permuted = false;
+    std::vector<int32_t> perm;      // internal -> caller
+    std::vector<int32_t> iperm;     // caller -> internal
+
+    // host copies needed to rebuild actuation coefficients
+    std::vector<uint32_t> spring_rec;   // caller spring -> record slot
+    std::vector<float> k_caller, L0_caller;
+    std::vector<double> rec_KL;         // per record slot: sum k * L0
+
+    // device layout
+    int n_slices = 0;
+    int64_t n_slots = 0, n_back_slots = 0, n_records = 0;
+    int max_fwd = 0, max_back = 0;
+    float4 *x4[2] = {nullptr, nullptr};
+    float4 *v4[2] = {nullptr, nullptr};
+    int cur = 0;
+    float4 *fext = nullptr;
+    uint4 *slice = nullptr;
+    int32_t *f_nbr = nullptr;
+    float *f_k = nullptr, *f_L0 = nullptr, *f_c = nullptr, *f_al = nullptr, *f_be = nullptr;
+    uint32_t *b_ent = nullptr;
+    int32_t *d_perm = nullptr;
+    float *stage = nullptr;             // (N,3)*2 floats for host copies
+    int *err = nullptr;
+    float c_uniform = 0.f;
+
+    double freq = 0.0;
+    bool actuated = false;
+    int64_t step_count = 0;
+    double stability = 0.0;
+
+    void *dev_alloc(size_t bytes)
+    {
+        if (bytes == 0) bytes = 16;
+        void *ptr = nullptr;
+        if (custom_alloc) {
+            ptr = alloc.alloc(bytes, stream, alloc.ctx);
+        } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            ptr = nullptr;
+        }
+        if (ptr) {
+            allocs.push_back({ptr, bytes});
+            device_bytes += (int64_t)bytes;
+        }
+        return ptr;
+    }
+    void release()
+    {
+        if (stream) cudaStreamSynchronize(stream); else cudaDeviceSynchronize();
+        for (auto &a : allocs) {
+            if (custom_alloc) alloc.free(a.ptr, a.bytes, stream, alloc.ctx);
+            else cudaFree(a.ptr);
+        }
+        allocs.clear();
+        device_bytes = 0;
+    }
+};
+
+namespace {
+
+template <class T>
+ms_status upload(ms_sim *s, T **dst, const T *src, size_t count)
+{
+    *dst = (T *)s->dev_alloc(sizeof(T) * count);
+    if (!*dst) return fail(MS_ERR_OOM, "device allocation failed");
+    if (src && count) {
+        cudaError_t e = cudaMemcpyAsync(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice, s->stream);
+        if (e != cudaSuccess) return fail(MS_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+    }
+    return MS_OK;
+}
+
+uint64_t spread3(uint64_t v)
+{   // spread the low 21 bits of v to every third bit
+    v &= 0x1fffff;
+    v = (v | v << 32) & 0x1f00000000ffffULL;
+    v = (v | v << 16) & 0x1f0000ff0000ffULL;
+    v = (v | v << 8) & 0x100f00f00f00f00fULL;
+    v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
+    v = (v | v << 2) & 0x1249249249249249ULL;
+    return v;
+}
+
+bool finite3(const float *p) { return std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]); }
+
+}  // namespace
+
+extern "C" {
+
+const char *ms_last_error(void) { return g_last_error.c_str(); }
+
+const char *ms_version(void) { return "cronos-ms-gb300 0.1 (sm_103a)"; }
+
+ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float *v0, const float *mass,
+                    const uint8_t *fixed, const float *fext, int64_t S, const int32_t *ij, const float *k,
+                    const float *c, float c_uniform, const float *rest_len, const ms_allocator *alloc,
+                    void *stream, ms_sim **out)
+{
+    if (!out) return fail(MS_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!p || !x0 || !v0 || !mass) return fail(MS_ERR_ARG, "p, x0, v0 and mass are required");
+    if (N < 1 || N >= (1 << ms::kOwnerBits)) return fail(MS_ERR_ARG, "N must be in [1, 2^27)");
+    if (S < 0 || (S > 0 && (!ij || !k))) return fail(MS_ERR_ARG, "S < 0, or ij / k missing");
+    if (!(p->dt > 0.f) || !std::isfinite(p->dt)) return fail(MS_ERR_ARG, "dt must be positive and finite");
+    if (p->integrator != 0) return fail(MS_ERR_ARG, "the GPU path implements integrator 0 (symplectic Euler) only");
+    if (!(p->vel_damping >= 0.f && p->vel_damping < 1.f)) return fail(MS_ERR_ARG, "vel_damping must be in [0, 1)");
+    if (p->contact_on && !(p->k_c >= 0.f && p->mu >= 0.f)) return fail(MS_ERR_ARG, "k_c and mu must be >= 0");
+    if (!c && !(c_uniform >= 0.f && std::isfinite(c_uniform))) return fail(MS_ERR_ARG, "c_uniform must be >= 0");
+    if (alloc && (!alloc->alloc || !alloc->free)) return fail(MS_ERR_ARG, "allocator needs alloc and free");
+
+    for (int32_t i = 0; i < N; ++i) {
+        const bool anchored = fixed && fixed[i];
+        if (!finite3(x0 + 3 * i) || !finite3(v0 + 3 * i)) return fail(MS_ERR_ARG, "non-finite position or velocity at mass " + std::to_string(i));
+        if (!anchored && !(mass[i] > 0.f && std::isfinite(mass[i]))) return fail(MS_ERR_ARG, "mass must be positive and finite at mass " + std::to_string(i));
+        if (fext && !finite3(fext + 3 * i)) return fail(MS_ERR_ARG, "non-finite external force at mass " + std::to_string(i));
+    }
+
+    ms_sim *s = new (std::nothrow) ms_sim();
+    if (!s) return fail(MS_ERR_OOM, "host allocation failed");
+    struct Guard { ms_sim *s; ~Guard() { if (s) { s->release(); delete s; } } } guard{s};
+    s->p = *p; s->N = N; s->S = S;
+    s->stream = (cudaStream_t)stream;
+    if (alloc) { s->alloc = *alloc; s->custom_alloc = true; }
+    s->c_uniform = c_uniform;
+
+    // 1. mass order
+    s->perm.resize(N); s->iperm.resize(N);
+    for (int32_t i = 0; i < N; ++i) s->perm[i] = i;
+    if (p->reorder) {
+        float lo[3] = {x0[0], x0[1], x0[2]}, hi[3] = {x0[0], x0[1], x0[2]};
+        for (int32_t i = 0; i < N; ++i)
+            for (int a = 0; a < 3; ++a) { lo[a] = std::min(lo[a], x0[3 * i + a]); hi[a] = std::max(hi[a], x0[3 * i + a]); }
+        double ext = 0; for (int a = 0; a < 3; ++a) ext = std::max(ext, (double)hi[a] - lo[a]);
+        const double scale = ext > 0 ? 2097151.0 / ext : 0.0;
+        std::vector<std::pair<uint64_t, int32_t>> key(N);
+        for (int32_t i = 0; i < N; ++i) {
+            uint64_t code = 0;
+            for (int a = 0; a < 3; ++a) code |= spread3((uint64_t)((x0[3 * i + a] - lo[a]) * scale)) << a;
+            key[i] = {code, i};
+        }
+        std::sort(key.begin(), key.end());
+        for (int32_t i = 0; i < N; ++i) s->perm[i] = key[i].second;
+        s->permuted = true;
+    }
+    for (int32_t i = 0; i < N; ++i) s->iperm[s->perm[i]] = i;
+
+    // 2. file springs by owner (counting sort), merge parallel springs
+    std::vector<int64_t> row(N + 1, 0);
+    for (int64_t e = 0; e < S; ++e) {
+        const int32_t a = ij[2 * e], b = ij[2 * e + 1];
+        if (a < 0 || a >= N || b < 0 || b >= N) return fail(MS_ERR_ARG, "spring endpoint out of range at spring " + std::to_string(e));
+        if (a == b) return fail(MS_ERR_ARG, "spring joins a mass to itself at spring " + std::to_string(e));
+        if (!(k[e] >= 0.f && std::isfinite(k[e]))) return fail(MS_ERR_ARG, "k must be >= 0 and finite at spring " + std::to_string(e));
+        if (c && !(c[e] >= 0.f && std::isfinite(c[e]))) return fail(MS_ERR_ARG, "c must be >= 0 and finite at spring " + std::to_string(e));
+        if (rest_len && !(rest_len[e] >= 0.f && std::isfinite(rest_len[e]))) return fail(MS_ERR_ARG, "rest length must be >= 0 and finite at spring " + std::to_string(e));
+        row[std::min(s->iperm[a], s->iperm[b]) + 1]++;
+    }
+    for (int32_t i = 0; i < N; ++i) row[i + 1] += row[i];
+    std::vector<int32_t> r_other(S), r_spring(S);
+    {
+        std::vector<int64_t> fill(row.begin(), row.end() - 1);
+        for (int64_t e = 0; e < S; ++e) {
+            const int32_t a = s->iperm[ij[2 * e]], b = s->iperm[ij[2 * e + 1]];
+            const int32_t o = std::min(a, b);
+            const int64_t at = fill[o]++;
+            r_other[at] = std::max(a, b);
+            r_spring[at] = (int32_t)e;
+        }
+    }
+    // sort each row by (partner, spring) and count distinct partners
+    std::vector<int32_t> deg(N, 0);
+    for (int32_t o = 0; o < N; ++o) {
+        const int64_t b0 = row[o], b1 = row[o + 1];
+        // insertion sort (rows are short)
+        for (int64_t q = b0 + 1; q < b1; ++q) {
+            const int32_t vo = r_other[q], vs = r_spring[q];
+            int64_t t = q - 1;
+            while (t >= b0 && (r_other[t] > vo || (r_other[t] == vo && r_spring[t] > vs))) {
+                r_other[t + 1] = r_other[t]; r_spring[t + 1] = r_spring[t]; --t;
+            }
+            r_other[t + 1] = vo; r_spring[t + 1] = vs;
+        }
+        int d = 0;
+        for (int64_t q = b0; q < b1; ++q)
+            if (q == b0 || r_other[q] != r_other[q - 1]) ++d;
+        if (d > ms::kMaxFwdDegree)
+            return fail(MS_ERR_ARG, "mass " + std::to_string(s->perm[o]) + " owns " + std::to_string(d) +
+                                        " distinct partners after ordering; at most 31 are supported");
+        deg[o] = d;
+    }
+
+    // 3. sliced-ELL layout
+    const int n_slices = (N + 31) / 32;
+    s->n_slices = n_slices;
+    std::vector<ms::Slice> sl(n_slices);
+    int64_t off = 0;
+    for (int b = 0; b < n_slices; ++b) {
+        int mx = 0;
+        for (int l = 0; l < 32 && 32 * b + l < N; ++l) mx = std::max(mx, deg[32 * b + l]);
+        sl[b].fwd_off = (uint32_t)off;
+        sl[b].lens = (uint32_t)mx;
+        sl[b].pad = 0;
+        off += 32LL * mx;
+        s->max_fwd = std::max(s->max_fwd, mx);
+    }
+    if (off >= (int64_t)UINT32_MAX) return fail(MS_ERR_ARG, "too many spring slots for 32-bit offsets");
+    const int64_t n_slots = off;
+    s->n_slots = n_slots;
+    std::vector<int32_t> h_nbr(n_slots, -1);
+    std::vector<float> h_k(n_slots, 0.f), h_L0(n_slots, 0.f), h_c;
+    if (c) h_c.assign(n_slots, 0.f);
+    s->rec_KL.assign(n_slots, 0.0);
+    s->spring_rec.resize(S);
+    std::vector<int32_t> bdeg(N, 0);
+    std::vector<double> sumK(N, 0.0);
+    int64_t n_rec = 0;
+    for (int32_t o = 0; o < N; ++o) {
+        int slot = -1;
+        const int64_t b0 = row[o], b1 = row[o + 1];
+        const uint32_t base = sl[o >> 5].fwd_off + (uint32_t)(o & 31);
+        for (int64_t q = b0; q < b1;) {
+            const int32_t j = r_other[q];
+            ++slot;
+            const uint32_t r = base + 32u * (uint32_t)slot;
+            double K = 0, KL = 0, Lsum = 0, Csum = 0;
+            int cnt = 0;
+            for (; q < b1 && r_other[q] == j; ++q) {
+                const int32_t e = r_spring[q];
+                double L;
+                if (rest_len) L = rest_len[e];
+                else {
+                    const int32_t a = ij[2 * e], b = ij[2 * e + 1];
+                    const double dx = (double)x0[3 * b] - x0[3 * a], dy = (double)x0[3 * b + 1] - x0[3 * a + 1],
+                                 dz = (double)x0[3 * b + 2] - x0[3 * a + 2];
+                    L = (double)(float)std::sqrt(dx * dx + dy * dy + dz * dz);
+                }
+                K += k[e]; KL += (double)k[e] * L; Lsum += L; Csum += c ? c[e] : 0.0; ++cnt;
+                s->spring_rec[e] = r;
+            }
+            h_nbr[r] = j;
+            h_k[r] = (float)K;
+            h_L0[r] = (float)(K > 0 ? KL / K : Lsum / cnt);
+            if (c) h_c[r] = (float)Csum;
+            s->rec_KL[r] = K > 0 ? KL : 0.0;
+            bdeg[j]++;
+            sumK[o] += K; sumK[j] += K;
+            ++n_rec;
+        }
+    }
+    s->n_records = n_rec;
+    int64_t boff = 0;
+    for (int b = 0; b < n_slices; ++b) {
+        int mx = 0;
+        for (int l = 0; l < 32 && 32 * b + l < N; ++l) mx = std::max(mx, bdeg[32 * b + l]);
+        if (mx > 0xffff) return fail(MS_ERR_ARG, "a mass has more than 65535 lower-indexed partners");
+        sl[b].bwd_off = (uint32_t)boff;
+        sl[b].lens |= (uint32_t)mx << 16;
+        boff += 32LL * mx;
+        s->max_back = std::max(s->max_back, mx);
+    }
+    if (boff >= (int64_t)UINT32_MAX) return fail(MS_ERR_ARG, "too many back-reference slots for 32-bit offsets");
+    s->n_back_slots = boff;
+    std::vector<uint32_t> h_b(boff, ms::kBackPad);
+    {
+        std::vector<int32_t> bfill(N, 0);
+        for (int32_t o = 0; o < N; ++o) {          // owners ascending: back lists sorted by owner
+            const uint32_t base = sl[o >> 5].fwd_off + (uint32_t)(o & 31);
+            for (int s_ = 0; s_ < deg[o]; ++s_) {
+                const int32_t j = h_nbr[base + 32u * (uint32_t)s_];
+                const int t = bfill[j]++;
+                h_b[sl[j >> 5].bwd_off + 32u * (uint32_t)t + (uint32_t)(j & 31)] = (uint32_t)o | ((uint32_t)s_ << ms::kOwnerBits);
+            }
+        }
+    }
+    r_other.clear(); r_other.shrink_to_fit(); r_spring.clear(); r_spring.shrink_to_fit();
+
+    // masses
+    std::vector<float4> hx(N), hv(N), hf;
+    double bound = 0.0;
+    const double dt2 = (double)p->dt * p->dt;
+    for (int32_t i = 0; i < N; ++i) {
+        const int32_t cidx = s->perm[i];
+        const bool anchored = fixed && fixed[cidx];
+        const float w = anchored ? -1.0f : (float)(1.0 / (double)mass[cidx]);
+        hx[i] = make_float4(x0[3 * cidx], x0[3 * cidx + 1], x0[3 * cidx + 2], w);
+        hv[i] = anchored ? make_float4(0.f, 0.f, 0.f, 0.f)
+                         : make_float4(v0[3 * cidx], v0[3 * cidx + 1], v0[3 * cidx + 2], 0.f);
+        if (!anchored) bound = std::max(bound, dt2 * (2.0 * sumK[i] + (p->contact_on ? p->k_c : 0.0)) / mass[cidx]);
+    }
+    s->stability = bound;
+    if (p->strict_stability && bound >= 4.0) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "stability bound dt^2*max(2 sum k + k_c)/m = %.3g >= 4", bound);
+        return fail(MS_ERR_UNSTABLE, buf);
+    }
+    if (fext) {
+        hf.resize(N);
+        for (int32_t i = 0; i < N; ++i) {
+            const int32_t cidx = s->perm[i];
+            hf[i] = make_float4(fext[3 * cidx], fext[3 * cidx + 1], fext[3 * cidx + 2], 0.f);
+        }
+    }
+
+    // 4. device upload
+    ms_status st;
+    if ((st = upload(s, &s->x4[0], hx.data(), N)) != MS_OK) return st;
+    if ((st = upload(s, &s->v4[0], hv.data(), N)) != MS_OK) return st;
+    if ((st = upload(s, &s->x4[1], hx.data(), N)) != MS_OK) return st;
+    if ((st = upload(s, &s->v4[1], hv.data(), N)) != MS_OK) return st;
+    if (fext && (st = upload(s, &s->fext, hf.data(), N)) != MS_OK) return st;
+    static_assert(sizeof(ms::Slice) == sizeof(uint4), "slice size");
+    if ((st = upload(s, &s->slice, (const uint4 *)sl.data(), n_slices)) != MS_OK) return st;
+    if ((st = upload(s, &s->f_nbr, h_nbr.data(), n_slots)) != MS_OK) return st;
+    if ((st = upload(s, &s->f_k, h_k.data(), n_slots)) != MS_OK) return st;
+    if ((st = upload(s, &s->f_L0, h_L0.data(), n_slots)) != MS_OK) return st;
+    if (c && (st = upload(s, &s->f_c, h_c.data(), n_slots)) != MS_OK) return st;
+    if ((st = upload(s, &s->b_ent, h_b.data(), boff)) != MS_OK) return st;
+    if (s->permuted && (st = upload(s, &s->d_perm, s->perm.data(), N)) != MS_OK) return st;
+    if ((st = upload<float>(s, &s->stage, nullptr, (size_t)N * 6)) != MS_OK) return st;
+    if ((st = upload<int>(s, &s->err, nullptr, 1)) != MS_OK) return st;
+    MS_CUDA_TRY(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
+    // host arrays must outlive the asynchronous copies
+    MS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+
+    s->k_caller.assign(k, k + S);
+    s->L0_caller.resize(S);
+    for (int64_t e = 0; e < S; ++e) {
+        if (rest_len) s->L0_caller[e] = rest_len[e];
+        else {
+            const int32_t a = ij[2 * e], b = ij[2 * e + 1];
+            const double dx = (double)x0[3 * b] - x0[3 * a], dy = (double)x0[3 * b + 1] - x0[3 * a + 1],
+                         dz = (double)x0[3 * b + 2] - x0[3 * a + 2];
+            s->L0_caller[e] = (float)std::sqrt(dx * dx + dy * dy + dz * dz);
+        }
+    }
+    guard.s = nullptr;
+    *out = s;
+    return MS_OK;
+}
+
+ms_status ms_set_actuation(ms_sim *s, float freq_hz, const float *amp, const float *phase)
+{
+    if (!s) return fail(MS_ERR_ARG, "sim is NULL");
+    if (!amp) { s->actuated = false; s->freq = 0.0; return MS_OK; }
+    if (!phase) return fail(MS_ERR_ARG, "phase is required with amp");
+    if (!std::isfinite(freq_hz)) return fail(MS_ERR_ARG, "freq must be finite");
+    const int64_t S = s->S, n = s->n_slots;
+    std::vector<double> sa(n, 0.0), sb(n, 0.0);
+    for (int64_t e = 0; e < S; ++e) {
+        if (!std::isfinite(amp[e]) || !std::isfinite(phase[e])) return fail(MS_ERR_ARG, "non-finite amp or phase at spring " + std::to_string(e));
+        const double w = (double)s->k_caller[e] * s->L0_caller[e] * amp[e];
+        const uint32_t r = s->spring_rec[e];
+        sa[r] += w * std::cos((double)phase[e]);    // coefficient of sin(2 pi f t)
+        sb[r] += w * std::sin((double)phase[e]);    // coefficient of cos(2 pi f t)
+    }
+    std::vector<float> al(n, 0.f), be(n, 0.f);
+    for (int64_t r = 0; r < n; ++r)
+        if (s->rec_KL[r] > 0) { al[r] = (float)(sa[r] / s->rec_KL[r]); be[r] = (float)(sb[r] / s->rec_KL[r]); }
+    ms_status st;
+    if (!s->f_al) {
+        if ((st = upload<float>(s, &s->f_al, nullptr, n)) != MS_OK) return st;
+        if ((st = upload<float>(s, &s->f_be, nullptr, n)) != MS_OK) return st;
+    }
+    MS_CUDA_TRY(cudaMemcpyAsync(s->f_al, al.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s->stream));
+    MS_CUDA_TRY(cudaMemcpyAsync(s->f_be, be.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s->stream));
+    MS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    s->actuated = true;
+    s->freq = freq_hz;
+    return MS_OK;
+}
+
+ms_status ms_step(ms_sim *s, int32_t nsteps)
+{
+    if (!s) return fail(MS_ERR_ARG, "sim is NULL");
+    if (nsteps < 0) return fail(MS_ERR_ARG, "nsteps must be >= 0");
+    ms::StepArgs a{};
+    a.fext = s->fext; a.slice = s->slice; a.f_nbr = s->f_nbr; a.f_k = s->f_k; a.f_L0 = s->f_L0;
+    a.f_c = s->f_c; a.f_al = s->actuated ? s->f_al : nullptr; a.f_be = s->actuated ? s->f_be : nullptr;
+    a.b_ent = s->b_ent; a.err = s->err; a.N = s->N; a.c_uniform = s->c_uniform;
+    a.dt = s->p.dt; a.gx = s->p.g[0]; a.gy = s->p.g[1]; a.gz = s->p.g[2];
+    a.k_c = s->p.k_c; a.mu = s->p.mu; a.keep = 1.0f - s->p.vel_damping; a.contact = s->p.contact_on;
+    const double two_pi_f = 2.0 * M_PI * s->freq;
+    for (int32_t n = 0; n < nsteps; ++n) {
+        if (s->actuated) {
+            const double t = (double)(s->step_count + n) * (double)s->p.dt;
+            a.s_n = (float)std::sin(two_pi_f * t);
+            a.c_n = (float)std::cos(two_pi_f * t);
+        }
+        a.x = s->x4[s->cur]; a.v = s->v4[s->cur];
+        a.xo = s->x4[s->cur ^ 1]; a.vo = s->v4[s->cur ^ 1];
+        MS_CUDA_TRY(ms::launch_step(a, s->stream));
+        s->cur ^= 1;
+    }
+    s->step_count += nsteps;
+    return MS_OK;
+}
+
+ms_status ms_get_state(ms_sim *s, float *x, float *v, int32_t on_device)
+{
+    if (!s) return fail(MS_ERR_ARG, "sim is NULL");
+    const int N = s->N;
+    if (on_device) {
+        MS_CUDA_TRY(ms::launch_gather_state(s->x4[s->cur], s->v4[s->cur], s->d_perm, N, x, v, s->stream));
+        return MS_OK;
+    }
+    float *sx = x ? s->stage : nullptr, *sv = v ? s->stage + 3 * (size_t)N : nullptr;
+    MS_CUDA_TRY(ms::launch_gather_state(s->x4[s->cur], s->v4[s->cur], s->d_perm, N, sx, sv, s->stream));
+    if (x) MS_CUDA_TRY(cudaMemcpyAsync(x, sx, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, s->stream));
+    if (v) MS_CUDA_TRY(cudaMemcpyAsync(v, sv, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, s->stream));
+    return ms_sync(s);
+}
+
+ms_status ms_set_state(ms_sim *s, const float *x, const float *v, int32_t on_device)
+{
+    if (!s) return fail(MS_ERR_ARG, "sim is NULL");
+    const int N = s->N;
+    if (!on_device) {
+        for (int i = 0; i < N; ++i)
+            if ((x && !finite3(x + 3 * i)) || (v && !finite3(v + 3 * i))) return fail(MS_ERR_ARG, "non-finite state at mass " + std::to_string(i));
+        if (x) MS_CUDA_TRY(cudaMemcpyAsync(s->stage, x, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, s->stream));
+        if (v) MS_CUDA_TRY(cudaMemcpyAsync(s->stage + 3 * (size_t)N, v, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, s->stream));
+        x = x ? s->stage : nullptr;
+        v = v ? s->stage + 3 * (size_t)N : nullptr;
+    }
+    MS_CUDA_TRY(ms::launch_scatter_state(s->x4[s->cur], s->v4[s->cur], s->d_perm, N, x, v, s->stream));
+    if (!on_device) MS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return MS_OK;
+}
+
+ms_status ms_sync(ms_sim *s)
+{
+    if (!s) return fail(MS_ERR_ARG, "sim is NULL");
+    MS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    int flag = 0;
+    MS_CUDA_TRY(cudaMemcpy(&flag, s->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) return fail(MS_ERR_NONFINITE, "a step produced a non-finite position or velocity");
+    return MS_OK;
+}
+
+ms_status ms_get_info(const ms_sim *s, ms_info_t *out)
+{
+    if (!s || !out) return fail(MS_ERR_ARG, "sim or out is NULL");
+    out->n_masses = s->N; out->n_springs = s->S; out->n_records = s->n_records;
+    out->n_slots = s->n_slots; out->n_back_slots = s->n_back_slots; out->device_bytes = s->device_bytes;
+    out->step_count = s->step_count; out->stability_bound = s->stability;
+    out->max_fwd_degree = s->max_fwd; out->max_back_degree = s->max_back;
+    return MS_OK;
+}
+
+ms_status ms_destroy(ms_sim *s)
+{
+    if (!s) return MS_OK;
+    s->release();
+    delete s;
+    return MS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,187 @@
+"""Python face of the mass-spring library: argument marshalling over the C ABI.
+
+Every step of the simulation runs in the library's CUDA kernels; this module
+only converts numpy / torch arguments into pointers and sizes.  PyTorch
+supplies the CUDA stream and, through the allocator hook, device memory from
+its caching allocator.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import MsAllocator, MsInfo, MsParams, check
+
+__all__ = ["Sim", "make_params", "torch_allocator"]
+
+
+def make_params(params: dict, reorder: bool = False, strict_stability: bool = False) -> MsParams:
+    p = MsParams()
+    p.dt = float(params["dt"])
+    for a in range(3):
+        p.g[a] = float(params["g"][a])
+    p.k_c = float(params.get("k_c", 0.0))
+    p.mu = float(params.get("mu", 0.0))
+    p.vel_damping = float(params.get("vel_damping", 0.0))
+    p.contact_on = 1 if params.get("contact", False) else 0
+    p.integrator = 0
+    p.strict_stability = 1 if strict_stability else 0
+    p.reorder = 1 if reorder else 0
+    return p
+
+
+class _TorchAllocator:
+    """ms_allocator backed by torch's CUDA caching allocator."""
+
+    def __init__(self):
+        import torch
+        self._torch = torch
+        self._alloc = _lib.ALLOC_FN(self._do_alloc)
+        self._free = _lib.FREE_FN(self._do_free)
+        self.struct = MsAllocator(self._alloc, self._free, None)
+
+    def _do_alloc(self, nbytes, stream, ctx):
+        try:
+            return int(self._torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0)))
+        except Exception:
+            return None
+
+    def _do_free(self, ptr, nbytes, stream, ctx):
+        try:
+            self._torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:
+            pass
+
+
+_ALLOCATOR = None
+
+
+def torch_allocator() -> _TorchAllocator:
+    global _ALLOCATOR
+    if _ALLOCATOR is None:
+        _ALLOCATOR = _TorchAllocator()
+    return _ALLOCATOR
+
+
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    return a if shape is None else a.reshape(shape)
+
+
+def _ptr(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class Sim:
+    """One mass-spring system resident on the GPU (ms_create ... ms_destroy).
+
+    system: dict of arrays (x, v, m, fixed, [fext], ij, k, c, L0, [A, phi, freq]);
+    c may be a scalar (uniform damping).  params: dt, g, k_c, mu, vel_damping, contact.
+    """
+
+    def __init__(self, system: dict, params: dict, reorder: bool = False, stream=None,
+                 use_torch_allocator: bool = True, strict_stability: bool = False):
+        lib = _lib.load()
+        self._lib = lib
+        x = _f32(system["x"], (-1, 3)); N = x.shape[0]
+        v = _f32(system["v"], (N, 3)); m = _f32(system["m"], (N,))
+        fixed = np.ascontiguousarray(system.get("fixed", np.zeros(N)), np.uint8)
+        fext = system.get("fext")
+        fext = None if fext is None else _f32(fext, (N, 3))
+        ij = np.ascontiguousarray(system["ij"], np.int32).reshape(-1, 2); S = ij.shape[0]
+        k = _f32(system["k"], (S,))
+        c = system.get("c", 0.0)
+        c_uniform = 0.0
+        if np.isscalar(c) or np.ndim(c) == 0:
+            c_uniform, c = float(c), None
+        elif system.get("c_uniform") is not None:
+            c_uniform, c = float(system["c_uniform"]), None
+        else:
+            c = _f32(c, (S,))
+        L0 = system.get("L0")
+        L0 = None if L0 is None else _f32(L0, (S,))
+        self.N, self.S = N, S
+        self._params = make_params(params, reorder, strict_stability)
+        self._alloc = torch_allocator() if use_torch_allocator else None
+        self.stream = _stream_handle(stream)
+        handle = C.c_void_p()
+        check(lib.ms_create(C.byref(self._params), N, _ptr(x), _ptr(v), _ptr(m), _ptr(fixed), _ptr(fext),
+                            S, _ptr(ij), _ptr(k), _ptr(c), float(c_uniform), _ptr(L0),
+                            C.byref(self._alloc.struct) if self._alloc else None,
+                            C.c_void_p(self.stream), C.byref(handle)))
+        self.h = handle
+        if system.get("A") is not None:
+            self.set_actuation(system.get("freq", 0.0), system["A"], system["phi"])
+
+    # -- C ABI wrappers ---------------------------------------------------
+    def set_actuation(self, freq: float, amp=None, phase=None):
+        if amp is None:
+            check(self._lib.ms_set_actuation(self.h, 0.0, None, None))
+            return
+        amp = _f32(amp, (self.S,)); phase = _f32(phase, (self.S,))
+        check(self._lib.ms_set_actuation(self.h, float(freq), _ptr(amp), _ptr(phase)))
+
+    def step(self, nsteps: int = 1):
+        check(self._lib.ms_step(self.h, int(nsteps)))
+
+    def get_state(self, x=None, v=None):
+        """Host copy (numpy float32 (N,3)) of positions and velocities, or, if
+        torch CUDA tensors are given, a stream-ordered device copy into them."""
+        if x is not None and hasattr(x, "is_cuda") and x.is_cuda:
+            check(self._lib.ms_get_state(self.h, C.c_void_p(x.data_ptr()),
+                                         None if v is None else C.c_void_p(v.data_ptr()), 1))
+            return x, v
+        if x is not None and hasattr(x, "data_ptr"):          # pinned torch host tensors
+            check(self._lib.ms_get_state(self.h, C.c_void_p(x.data_ptr()),
+                                         None if v is None else C.c_void_p(v.data_ptr()), 0))
+            return x, v
+        xo = np.empty((self.N, 3), np.float32); vo = np.empty((self.N, 3), np.float32)
+        check(self._lib.ms_get_state(self.h, _ptr(xo), _ptr(vo), 0))
+        return xo, vo
+
+    def set_state(self, x=None, v=None):
+        if (x is not None and hasattr(x, "is_cuda") and x.is_cuda):
+            check(self._lib.ms_set_state(self.h, C.c_void_p(x.data_ptr()),
+                                         None if v is None else C.c_void_p(v.data_ptr()), 1))
+            return
+        if x is not None and hasattr(x, "data_ptr"):
+            check(self._lib.ms_set_state(self.h, C.c_void_p(x.data_ptr()),
+                                         None if v is None else C.c_void_p(v.data_ptr()), 0))
+            return
+        xa = None if x is None else _f32(x, (self.N, 3))
+        va = None if v is None else _f32(v, (self.N, 3))
+        check(self._lib.ms_set_state(self.h, _ptr(xa), _ptr(va), 0))
+
+    def sync(self):
+        check(self._lib.ms_sync(self.h))
+
+    def info(self) -> dict:
+        inf = MsInfo()
+        check(self._lib.ms_get_info(self.h, C.byref(inf)))
+        return {name: getattr(inf, name) for name, _ in MsInfo._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.ms_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

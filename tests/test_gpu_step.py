@@ -1,0 +1,240 @@
+"""GPU (FP32, sm_103a) explicit step vs the FP64 oracle on identical seeded inputs.
+
+Tolerances (the position gates of the benchmark workloads):
+  * contact-free runs: max |x_gpu - x_oracle| <= 1e-5 x body size after the run;
+  * runs with ground contact: <= 1e-4 x body size after 200 steps, and the
+    centre-of-mass displacement within 1 % of the oracle's.
+Body size = largest axis-aligned extent of the start positions.
+The oracle gets the FP32-rounded values of every parameter the GPU sees.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def ms():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2207_09334_gb300 as ms
+    ms.load()
+    return ms
+
+
+def f32p(p):
+    q = dict(p)
+    for key in ("dt", "k_c", "mu", "vel_damping"):
+        if key in q:
+            q[key] = float(np.float32(q[key]))
+    q["g"] = tuple(float(np.float32(g)) for g in p["g"])
+    return q
+
+
+def body_size(s):
+    return float(np.ptp(np.asarray(s["x"], np.float64), axis=0).max())
+
+
+def gpu_run(ms, s, p, n, reorder=False, chunks=1):
+    with ms.Sim(s, p, reorder=reorder) as sim:
+        done = 0
+        for q in range(chunks):
+            todo = n * (q + 1) // chunks - done
+            sim.step(todo)
+            done += todo
+        assert done == n
+        x, v = sim.get_state()
+    return x.astype(np.float64), v.astype(np.float64)
+
+
+def test_hand_worked_steps_on_gpu(ms):
+    cases = json.load(open(os.path.join(HERE, "golden", "hand_steps.json")))["cases"]
+    for case in cases:
+        s = dict(x=np.array(case["x"], np.float32), v=np.array(case["v"], np.float32),
+                 m=np.array(case["m"], np.float32), fixed=np.array(case["fixed"], np.uint8),
+                 ij=np.array(case["ij"], np.int32), k=np.array(case["k"], np.float32),
+                 c=np.array(case["c"], np.float32), L0=np.array(case["L0"], np.float32),
+                 freq=case.get("freq", 0.0))
+        if "A" in case:
+            s["A"] = np.array(case["A"], np.float32); s["phi"] = np.array(case["phi"], np.float32)
+        x, v = gpu_run(ms, s, synth.params(dt=case["dt"], g=(0, 0, 0)), case["nsteps"])
+        np.testing.assert_allclose(x, case["x_out"], rtol=2e-6, atol=1e-6, err_msg=case["name"])
+        np.testing.assert_allclose(v, case["v_out"], rtol=2e-6, atol=1e-6, err_msg=case["name"])
+
+
+@pytest.mark.parametrize("reorder", [False, True])
+def test_soft_cube_contact_free_1000_steps(ms, ora, reorder):
+    s = synth.soft_cube()
+    p = synth.soft_cube_params(contact=False)
+    xg, vg = gpu_run(ms, s, p, 1000, reorder=reorder, chunks=4)
+    xo, vo = ora.run(s, f32p(p), 1000)
+    err = np.abs(xg - xo).max()
+    assert err <= 1e-5 * body_size(s), (err, 1e-5 * body_size(s))
+
+
+def test_soft_cube_contact_200_steps(ms, ora):
+    """Cube 1 mm above the ground, thrown down and sideways: contact and
+    friction are active within the 200 steps."""
+    s = synth.soft_cube(z0=0.001)
+    s["v"][:] = np.array([0.3, -0.2, -0.6], np.float32)
+    p = synth.soft_cube_params(contact=True)
+    xg, _ = gpu_run(ms, s, p, 200)
+    xo, vo = s["x"], s["v"]
+    zmin = np.inf
+    for c in range(20):
+        xo, vo = ora.run(s, f32p(p), 10, n0=10 * c, x=xo, v=vo)
+        zmin = min(zmin, xo[:, 2].min())
+    assert zmin < -1e-5                       # contact really happened (the cube bounces)
+    err = np.abs(xg - xo).max()
+    assert err <= 1e-4 * body_size(s), (err, 1e-4 * body_size(s))
+    m = s["m"].astype(np.float64)
+    d_o = ora.centre_of_mass(m, xo) - ora.centre_of_mass(m, s["x"])
+    d_g = ora.centre_of_mass(m, xg) - ora.centre_of_mass(m, s["x"])
+    assert np.linalg.norm(d_g - d_o) <= 0.01 * np.linalg.norm(d_o)
+
+
+@pytest.mark.slow
+def test_soft_cube_full_drop_com_travel(ms, ora):
+    """The dropped-cube workload: 0.05 m drop onto the ground, 10,000 steps.
+    The vertical centre-of-mass travel agrees within 1 %.  The sideways drift
+    of this symmetric, bouncing drop is chaotic (perturbing the FP64 start
+    positions by 1e-9 m moves it from 5e-5 m to 2e-4 m), so only its size is
+    bounded: below 5 % of the travel."""
+    s = synth.soft_cube()
+    p = synth.soft_cube_params(contact=True)
+    xg, _ = gpu_run(ms, s, p, 10000, chunks=10)
+    xo, _ = ora.run(s, f32p(p), 10000)
+    m = s["m"].astype(np.float64)
+    d_o = ora.centre_of_mass(m, xo) - ora.centre_of_mass(m, s["x"])
+    d_g = ora.centre_of_mass(m, xg) - ora.centre_of_mass(m, s["x"])
+    assert abs(d_g[2] - d_o[2]) <= 0.01 * abs(d_o[2])
+    assert np.linalg.norm(d_g[:2]) <= 0.05 * np.linalg.norm(d_o)
+    assert xg[:, 2].min() > -1e-3                  # resting on the plane, not through it
+
+
+def test_cantilever_with_anchors_and_external_force(ms, ora):
+    s = synth.cantilever(40, 4, 4, c=0.1)
+    p = synth.params(dt=1e-4, g=(0, 0, 0))
+    xg, vg = gpu_run(ms, s, p, 2000, chunks=2)
+    xo, vo = ora.run(s, f32p(p), 2000)
+    fixed = s["fixed"].astype(bool)
+    assert np.all(xg[fixed] == s["x"][fixed]) and np.all(vg[fixed] == 0)
+    assert np.abs(xo[:, 2] - s["x"][:, 2]).max() > 1e-5
+    err = np.abs(xg - xo).max()
+    assert err <= 1e-5 * body_size(s), (err, 1e-5 * body_size(s))
+
+
+def test_actuated_heterogeneous_lattice(ms, ora):
+    x, ij, L0 = synth.box_lattice(7, 6, 5, 0.01, origin=(0, 0, 0.02))
+    rng = np.random.default_rng(11)
+    S = ij.shape[0]; N = x.shape[0]
+    s = dict(x=x, v=(0.01 * rng.standard_normal((N, 3))).astype(np.float32),
+             m=rng.uniform(1e-3, 4e-3, N).astype(np.float32), fixed=np.zeros(N, np.uint8), ij=ij,
+             k=rng.uniform(1e3, 1e4, S).astype(np.float32), c=rng.uniform(0, 0.1, S).astype(np.float32),
+             L0=L0, A=rng.uniform(0, 0.2, S).astype(np.float32),
+             phi=rng.uniform(0, 2 * np.pi, S).astype(np.float32), freq=5.0)
+    p = synth.params(dt=1e-4, g=(0, 0, -9.81))
+    xg, _ = gpu_run(ms, s, p, 1000, chunks=3)
+    xo, _ = ora.run(s, f32p(p), 1000)
+    err = np.abs(xg - xo).max()
+    assert err <= 1e-5 * body_size(s), (err, 1e-5 * body_size(s))
+
+
+def test_parallel_springs_are_merged_exactly(ms, ora):
+    """A voxel robot expanded by the oracle keeps the springs of neighbouring
+    voxels as separate parallel springs; the library merges each pair into
+    one record (summed k and c, weighted rest length, combined actuation)."""
+    rng = np.random.default_rng(5)
+    mat, phase = synth.random_voxel_design(rng, (4, 3, 3))
+    s = ora.voxel_system(mat, phase, synth.VOXEL_MATERIALS, synth.VOXEL_FREQ, synth.VOXEL_EDGE, synth.VOXEL_MASS)
+    s["m"] = s["m"].astype(np.float32)
+    p = synth.voxel_params()
+    with ms.Sim(s, p) as sim:
+        inf = sim.info()
+        assert inf["n_records"] < s["ij"].shape[0]
+        sim.step(200)
+        xg, _ = sim.get_state()
+    xo, _ = ora.run(s, f32p(p), 200)
+    err = np.abs(xg - xo).max()
+    assert err <= 1e-4 * body_size(s), (err, 1e-4 * body_size(s))
+
+
+def test_throughput_lattice_ragged(ms, ora):
+    """Throughput-lattice parameters (k ~ U[5e3,5e4], c = 0.05, anchored
+    bottom, v ~ N(0,1e-3), dt = 5e-5) on a 23x24x25 box: many slices and
+    blocks and a ragged last block; 200 steps."""
+    x, ij, L0 = synth.box_lattice(23, 24, 25, 1e-3)
+    N = x.shape[0]; S = ij.shape[0]
+    rk = np.random.default_rng(0)
+    rv = np.random.default_rng(1)
+    fixed = (np.arange(N) < 23 * 24).astype(np.uint8)
+    v = (rv.standard_normal((N, 3)) * 1e-3).astype(np.float32); v[fixed == 1] = 0
+    s = dict(x=x, v=v, m=np.full(N, 1e-3, np.float32), fixed=fixed, ij=ij,
+             k=rk.uniform(5e3, 5e4, S).astype(np.float32), c=np.float32(0.05), L0=L0)
+    p = synth.throughput_params()
+    xg, vg = gpu_run(ms, s, p, 200)
+    xo, vo = ora.run(s, f32p(p), 200)
+    err = np.abs(xg - xo).max()
+    assert err <= 1e-5 * body_size(s), (err, 1e-5 * body_size(s))
+
+
+def test_runs_are_bit_identical(ms):
+    s = synth.soft_cube(z0=0.001)
+    s["v"][:] = np.array([0.3, -0.2, -0.6], np.float32)
+    p = synth.soft_cube_params(contact=True)
+    a, _ = gpu_run(ms, s, p, 300)
+    b, _ = gpu_run(ms, s, p, 300)
+    assert np.array_equal(a, b)
+
+
+def test_state_round_trip_and_resume(ms):
+    """get_state / set_state checkpoint: 100 + 100 steps with a save/restore
+    in between equals 200 straight steps (bit for bit)."""
+    import torch
+    s = synth.soft_cube(n=5, z0=0.001)
+    s["v"][:] = np.array([0.1, 0.0, -0.4], np.float32)
+    p = synth.soft_cube_params(contact=True)
+    with ms.Sim(s, p, reorder=True) as a:
+        a.step(200)
+        xa, va = a.get_state()
+    with ms.Sim(s, p, reorder=True) as b:
+        b.step(100)
+        xd = torch.empty((s["x"].shape[0], 3), device="cuda")
+        vd = torch.empty_like(xd)
+        b.get_state(xd, vd)                      # device-side checkpoint
+        b.step(37)                               # wander off ...
+        b.set_state(xd, vd)                      # ... and restore
+        b.step(100)
+        xb, vb = b.get_state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+
+
+def test_nonfinite_state_is_reported(ms):
+    s = synth.soft_cube(n=3)
+    s["k"][:] = 1e9                                # violently unstable at this dt
+    p = synth.soft_cube_params(contact=False, dt=1e-2)
+    s["x"][0, 0] += 1e-3
+    with ms.Sim(s, p) as sim:
+        sim.step(2000)
+        with pytest.raises(ms.MsError) as e:
+            sim.sync()
+        assert e.value.code == 5
+
+
+def test_empty_spring_set_is_free_fall(ms):
+    s = dict(x=np.array([[0, 0, 1.0]], np.float32), v=np.array([[0.5, 0, 0]], np.float32),
+             m=np.array([1e-3], np.float32), fixed=np.zeros(1, np.uint8),
+             ij=np.zeros((0, 2), np.int32), k=np.zeros(0, np.float32), c=np.zeros(0, np.float32),
+             L0=np.zeros(0, np.float32))
+    p = synth.params(dt=1e-3)
+    x, v = gpu_run(ms, s, p, 100)
+    g = np.float32(-9.81); dt = np.float32(1e-3)
+    assert abs(v[0, 2] - 100 * dt * g) < 1e-4
+    assert abs(x[0, 0] - (0.0 + 100 * dt * 0.5)) < 1e-6
