@@ -52,7 +52,7 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_traffic(kernel_src: str):
+def kernel_traffic(kernel_src: str, kname: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
@@ -61,7 +61,7 @@ def kernel_traffic(kernel_src: str):
             d = json.load(f)
         with open(kernel_src, "rb") as f:
             h = hashlib.sha256(f.read()).hexdigest()[:16]
-        ent = d.get("k_step")
+        ent = d.get(kname)
         if ent and ent.get("source_sha256_16") == h:
             return ent
     except Exception:
@@ -219,7 +219,7 @@ def run_ours(args, world, rank, local):
     t_gen = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
-    sim = ms.Sim(s, p, reorder=False, stream=stream)
+    sim = ms.Sim(s, p, reorder=args.order, kernel=args.kernel, stream=stream)
     torch.cuda.synchronize()
     t_create = time.perf_counter() - t0
     info = sim.info()
@@ -253,27 +253,33 @@ def run_ours(args, world, rank, local):
     # end to end through the public API with host buffers: upload the state
     # from pinned host memory, run the workload's 200 steps, read it back
     e2e_steps = args.e2e_sim_steps
-    xh = torch.from_numpy(np.ascontiguousarray(s["x"])).pin_memory()
-    vh = torch.from_numpy(np.ascontiguousarray(s["v"])).pin_memory()
-    xo = torch.empty_like(xh).pin_memory(); vo = torch.empty_like(vh).pin_memory()
-    e2e_times = []
-    for it in range(args.e2e_iters + 1):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        sim.set_state(xh, vh)
-        sim.step(e2e_steps)
-        sim.get_state(xo, vo)
-        el = time.perf_counter() - t0
-        if it > 0:
-            e2e_times.append(el)
-    e2e_val = world * (N + S) * e2e_steps / statistics.median(e2e_times)
     bytes_state = 2 * N * 3 * 4
+    e2e = None
+    if args.e2e_iters > 0:
+        xh = torch.from_numpy(np.ascontiguousarray(s["x"])).pin_memory()
+        vh = torch.from_numpy(np.ascontiguousarray(s["v"])).pin_memory()
+        xo = torch.empty_like(xh).pin_memory(); vo = torch.empty_like(vh).pin_memory()
+        e2e_times = []
+        for it in range(args.e2e_iters + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sim.set_state(xh, vh)
+            sim.step(e2e_steps)
+            sim.get_state(xo, vo)
+            el = time.perf_counter() - t0
+            if it > 0:
+                e2e_times.append(el)
+        e2e_val = world * (N + S) * e2e_steps / statistics.median(e2e_times)
+        e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_state,
+               "d2h_bytes_per_step": bytes_state,
+               "note": f"each e2e step = ms_set_state(pinned host) + ms_step({e2e_steps}) + ms_get_state(pinned host)"}
 
     hbm, hbm_kind = peaks()
     alg_bytes = BYTES_PER_MASS * N + BYTES_PER_SPRING * S
     kern_ms = statistics.mean(per)
     achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
-    tr = kernel_traffic(os.path.join(ROOT, "paper_2207_09334_gb300", "csrc", "ms_step.cu"))
+    kname = "k_step_tiled" if info["kernel"] == 2 else "k_step"
+    tr = kernel_traffic(os.path.join(ROOT, "paper_2207_09334_gb300", "csrc", "ms_step.cu"), kname)
     traffic = None
     if tr is not None:
         traffic = tr["dram_bytes_per_launch_at_256"] * (N + S) / tr["elements_at_256"] if n != 256 else tr["dram_bytes_per_launch_at_256"]
@@ -285,13 +291,12 @@ def run_ours(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
             "config": dict(workload_config(n, N, S), parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
                            setup_s={"generate": round(t_gen, 1), "create": round(t_create, 1)},
+                           mass_order=args.order, kernel=["", "gather", "tiled"][info["kernel"]],
                            device_bytes=info["device_bytes"], records=info["n_records"]),
-            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_state,
-                    "d2h_bytes_per_step": bytes_state,
-                    "note": f"each e2e step = ms_set_state(pinned host) + ms_step({e2e_steps}) + ms_get_state(pinned host)"},
+            "e2e": e2e,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
-                         "kernel": "k_step", "peak_kind": f"{hbm_kind} (hbm_gbs)",
+                         "kernel": kname, "peak_kind": f"{hbm_kind} (hbm_gbs)",
                          "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": kern_ms},
             "gpu_launches": args.steps,
             "clocks": clocks}
@@ -312,6 +317,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=256, help="lattice side (256 = the benchmark workload)")
+    ap.add_argument("--order", default="auto", choices=["auto", "morton", "caller"], help="internal mass order")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "gather", "tiled"])
     ap.add_argument("--e2e-sim-steps", type=int, default=200)
     ap.add_argument("--e2e-iters", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -60,7 +60,11 @@ typedef struct {
     int32_t contact_on;     /* 1 = ground contact active */
     int32_t integrator;     /* 0 = symplectic Euler (only value supported by the GPU path) */
     int32_t strict_stability; /* 1 = ms_create fails with MS_ERR_UNSTABLE if the bound below exceeds 4 */
-    int32_t reorder;        /* 0 = keep caller mass order, 1 = Morton order by initial position */
+    int32_t reorder;        /* mass order: 0 = library default (Morton for the tiled kernel, caller
+                               order for the gather kernel), 1 = Morton order by initial position,
+                               2 = caller order */
+    int32_t kernel;         /* 0 = library default (tiled, or gather when a tile's partners do not fit
+                               shared memory), 1 = gather, 2 = tiled (MS_ERR_ARG if a tile does not fit) */
 } ms_params;
 
 /* Optional device allocator (e.g. a framework's caching allocator).
@@ -83,8 +87,11 @@ typedef struct {
     int64_t device_bytes;      /* device memory held */
     int64_t step_count;        /* steps taken since creation */
     double stability_bound;    /* dt^2 * max_i (2 sum_{springs at i} k + k_c) / m_i  (Gershgorin; stable if < 4) */
-    int32_t max_fwd_degree;
+    int32_t max_fwd_degree;    /* gather: most springs owned by one mass; tiled: most springs of one mass */
     int32_t max_back_degree;
+    int32_t kernel;            /* 1 = gather, 2 = tiled */
+    int32_t n_tiles;
+    int32_t max_tile_local;    /* tiled: largest members + halo of a tile */
 } ms_info_t;
 
 /*
@@ -169,6 +176,158 @@ const char *ms_last_error(void);
 
 /* Library version string. */
 const char *ms_version(void);
+
+
+/* ------------------------------------------------------------------------
+ * Batched voxel-robot populations.
+ *
+ * Many independent voxel robots (each with its own ground plane, no contact
+ * between robots) advanced together by ONE persistent kernel launch that is
+ * captured in a CUDA graph.  Each robot is built as in the paper's voxel
+ * lattice ("Generating a Lattice", Fig. figure1): the corners of its
+ * non-empty voxels are masses, and every voxel links all 28 pairs of its 8
+ * corners (12 edges, 12 face diagonals, 4 long diagonals); springs that
+ * neighbouring voxels share are merged exactly (summed k and c, combined
+ * actuation).  Materials set k, c and the actuation amplitude; actuated
+ * springs have rest length L0 (1 + amp sin(2 pi freq t_n + phase_voxel)).
+ * Masses of a robot are numbered in raster order (x fastest) of its
+ * (nx+1)(ny+1)(nz+1) corner grid, keeping only corners of non-empty voxels;
+ * corner (cx, cy, cz) starts at (cx a, cy a, cz a), so the robot rests on
+ * z = 0, at rest.  Each corner weighs voxel_mass / 8 per non-empty voxel it
+ * touches.  A robot may have at most 4096 masses.
+ * ---------------------------------------------------------------------- */
+typedef struct msb_batch msb_batch;
+
+typedef struct {
+    float voxel_edge;        /* voxel edge length a [m] */
+    float voxel_mass;        /* mass of one voxel [kg] */
+    float freq;              /* actuation frequency [Hz] */
+    int32_t n_materials;     /* entries in the tables below; id 0 is always "empty" */
+    const float *mat_k;      /* stiffness of each of a voxel's 28 springs [N/m] */
+    const float *mat_c;      /* axial dashpot of each spring [N s/m] */
+    const float *mat_amp;    /* actuation amplitude (0 = passive) */
+} msb_voxel_spec;
+
+typedef struct {
+    int32_t n_robots;
+    int64_t n_masses;        /* over all robots */
+    int64_t n_records;       /* merged springs over all robots */
+    int32_t max_robot_masses;
+    int32_t n_block_items;   /* robots run block-per-robot by the current schedule */
+    int32_t n_warp_items;    /* robots run warp-per-robot */
+    int64_t device_bytes;
+    int64_t step_count;
+} msb_info_t;
+
+/*
+ * msb_create -- build a population.
+ *   p          environment and step parameters (contact, friction, dt, g).
+ *   spec       voxel material table and geometry.
+ *   n_robots   >= 1.
+ *   dims       [n_robots][3] = (nx, ny, nz) voxels, each >= 1.
+ *   materials  concatenated grids, robot r has nz*ny*nx ids, index
+ *              ix + nx*(iy + ny*iz); ids in [0, n_materials).
+ *   phase      same layout, actuation phase per voxel [rad] (NULL = 0).
+ *   logk       same layout or NULL: per-voxel log-stiffness; when given,
+ *              every spring of voxel v uses k = exp(logk[v]) instead of its
+ *              material's k (empty voxels stay empty).
+ * Robots with no non-empty voxel are rejected (MS_ERR_ARG).
+ */
+ms_status msb_create(const ms_params *p, const msb_voxel_spec *spec, int32_t n_robots,
+                     const int32_t *dims, const uint8_t *materials, const float *phase,
+                     const float *logk, const ms_allocator *alloc, void *stream, msb_batch **out);
+
+/*
+ * msb_autotune -- time block-per-robot against warp-per-robot on a sample of
+ * robots of every size bucket (sample_steps steps each) and keep the faster
+ * schedule per bucket.  Without it, robots of up to 64 masses run
+ * warp-per-robot and the rest block-per-robot.  Synchronises the stream.
+ * policy: 0 = autotune, 1 = force block-per-robot, 2 = force warp-per-robot
+ * wherever a robot fits a warp's share of shared memory.
+ */
+ms_status msb_autotune(msb_batch *b, int32_t sample_steps, int32_t policy);
+
+/*
+ * msb_run -- advance every robot nsteps steps in one persistent launch
+ * (replayed from a CUDA graph after the first call with the same nsteps).
+ * Asynchronous on the batch's stream.
+ */
+ms_status msb_run(msb_batch *b, int32_t nsteps);
+
+/*
+ * msb_run_loop -- the same nsteps advanced robot by robot: one kernel launch
+ * per robot per step (the plain per-robot loop the batched launch replaces;
+ * kept for comparison).
+ */
+ms_status msb_run_loop(msb_batch *b, int32_t nsteps);
+
+/* msb_com_travel -- per robot, x-travel of the mass-weighted centre of mass
+ * since creation or the last msb_reset ([n_robots] floats; on_device: out is
+ * device memory, stream-ordered; else host, synchronising). */
+ms_status msb_com_travel(msb_batch *b, float *out, int32_t on_device);
+
+/* msb_robot_info -- number of masses of robot r and its first index in the
+ * population-wide mass numbering. */
+ms_status msb_robot_info(const msb_batch *b, int32_t robot, int32_t *n_masses, int64_t *first_mass);
+
+/* msb_get_state -- positions and velocities of all masses, robots in order,
+ * each robot in its own corner order ((n_masses,3) float32 host arrays;
+ * either may be NULL).  Synchronises. */
+ms_status msb_get_state(msb_batch *b, float *x, float *v);
+
+/* msb_reset -- restore the initial state and time t = 0. */
+ms_status msb_reset(msb_batch *b);
+
+ms_status msb_get_info(const msb_batch *b, msb_info_t *out);
+ms_status msb_destroy(msb_batch *b);
+
+/* ------------------------------------------------------------------------
+ * Adjoint of voxel-robot rollouts (reverse-mode gradients).
+ *
+ * The paper notes that differentiability is enabled by the method (Related
+ * Work, on ChainQueen).  This is a hand-written reverse pass of the
+ * explicit step above (symplectic Euler, ground penalty contact and the
+ * Coulomb clamp -- differentiated along the branch the forward pass took --
+ * the axial dashpot and the Hooke term with actuated rest length).  The
+ * forward pass keeps a checkpoint of the state every `checkpoint_every`
+ * steps; the reverse pass recomputes each segment from its checkpoint and
+ * walks it backwards.  One CTA per robot; gradients are summed per voxel in
+ * a fixed order (deterministic).
+ * ---------------------------------------------------------------------- */
+typedef struct msa_adjoint msa_adjoint;
+
+/*
+ * msa_create -- build the adjoint for a population (same voxel layout and
+ * mass numbering as msb_create).  Reserves checkpoint and segment memory for
+ * rollouts of up to max_steps steps.  checkpoint_every >= 1.  A robot may
+ * have at most 1024 masses and 4096 voxels here.
+ */
+ms_status msa_create(const ms_params *p, const msb_voxel_spec *spec, int32_t n_robots, const int32_t *dims,
+                     const uint8_t *materials, int32_t checkpoint_every, int32_t max_steps,
+                     const ms_allocator *alloc, void *stream, msa_adjoint **out);
+
+/*
+ * msa_gradients -- run nsteps (<= max_steps) steps from rest and return, per
+ * robot r, a scalar loss and its gradient with respect to every voxel's
+ * actuation phase and log-stiffness.
+ *   phase, logk  [total voxels] parameters (layout of msb_create's grids);
+ *                voxel v's 28 springs use k = exp(logk[v]) and rest length
+ *                L0 (1 + amp sin(2 pi freq t_n + phase[v])).
+ *   seed_x       NULL: loss_r = centre-of-mass x-travel of robot r after
+ *                nsteps; else [n_masses][3] weights w and loss_r = sum over
+ *                robot r's masses of w_i . x_i(t_end).
+ *   loss         [n_robots] out; g_phase, g_logk [total voxels] out (0 for
+ *                empty voxels).
+ *   on_device    1: every array argument is device memory (stream-ordered);
+ *                0: host memory (synchronising).
+ */
+ms_status msa_gradients(msa_adjoint *a, int32_t nsteps, const float *phase, const float *logk,
+                        const float *seed_x, float *loss, float *g_phase, float *g_logk, int32_t on_device);
+
+/* msa_sizes -- total voxels and masses of the population. */
+ms_status msa_sizes(const msa_adjoint *a, int64_t *n_voxels, int64_t *n_masses);
+
+ms_status msa_destroy(msa_adjoint *a);
 
 #ifdef __cplusplus
 }

@@ -7,5 +7,7 @@ missing, loading fails.
 """
 from ._lib import MsError, library_path, load  # noqa: F401
 from .sim import Sim, make_params, torch_allocator  # noqa: F401
+from .batch import Population  # noqa: F401
+from .adjoint import Adjoint, RolloutLoss  # noqa: F401
 
 __version__ = "0.1.0"

@@ -14,7 +14,7 @@ _lib = None
 class MsParams(C.Structure):
     _fields_ = [("dt", C.c_float), ("g", C.c_float * 3), ("k_c", C.c_float), ("mu", C.c_float),
                 ("vel_damping", C.c_float), ("contact_on", C.c_int32), ("integrator", C.c_int32),
-                ("strict_stability", C.c_int32), ("reorder", C.c_int32)]
+                ("strict_stability", C.c_int32), ("reorder", C.c_int32), ("kernel", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -29,7 +29,20 @@ class MsInfo(C.Structure):
     _fields_ = [("n_masses", C.c_int64), ("n_springs", C.c_int64), ("n_records", C.c_int64),
                 ("n_slots", C.c_int64), ("n_back_slots", C.c_int64), ("device_bytes", C.c_int64),
                 ("step_count", C.c_int64), ("stability_bound", C.c_double),
-                ("max_fwd_degree", C.c_int32), ("max_back_degree", C.c_int32)]
+                ("max_fwd_degree", C.c_int32), ("max_back_degree", C.c_int32), ("kernel", C.c_int32),
+                ("n_tiles", C.c_int32), ("max_tile_local", C.c_int32)]
+
+
+class MsbVoxelSpec(C.Structure):
+    _fields_ = [("voxel_edge", C.c_float), ("voxel_mass", C.c_float), ("freq", C.c_float),
+                ("n_materials", C.c_int32), ("mat_k", C.c_void_p), ("mat_c", C.c_void_p),
+                ("mat_amp", C.c_void_p)]
+
+
+class MsbInfo(C.Structure):
+    _fields_ = [("n_robots", C.c_int32), ("n_masses", C.c_int64), ("n_records", C.c_int64),
+                ("max_robot_masses", C.c_int32), ("n_block_items", C.c_int32),
+                ("n_warp_items", C.c_int32), ("device_bytes", C.c_int64), ("step_count", C.c_int64)]
 
 
 STATUS = {0: "MS_OK", 1: "MS_ERR_ARG", 2: "MS_ERR_OOM", 3: "MS_ERR_CUDA", 4: "MS_ERR_UNSTABLE",
@@ -57,6 +70,22 @@ SIGNATURES = {
     "ms_get_info": (C.c_int, [VP, C.POINTER(MsInfo)]),
     "ms_destroy": (C.c_int, [VP]),
     "ms_last_error": (C.c_char_p, []),
+    "msb_create": (C.c_int, [C.POINTER(MsParams), C.POINTER(MsbVoxelSpec), I32, VP, VP, VP, VP,
+                             C.POINTER(MsAllocator), VP, C.POINTER(VP)]),
+    "msb_autotune": (C.c_int, [VP, I32, I32]),
+    "msb_run": (C.c_int, [VP, I32]),
+    "msb_run_loop": (C.c_int, [VP, I32]),
+    "msb_com_travel": (C.c_int, [VP, VP, I32]),
+    "msb_robot_info": (C.c_int, [VP, I32, C.POINTER(I32), C.POINTER(I64)]),
+    "msb_get_state": (C.c_int, [VP, VP, VP]),
+    "msb_reset": (C.c_int, [VP]),
+    "msb_get_info": (C.c_int, [VP, C.POINTER(MsbInfo)]),
+    "msb_destroy": (C.c_int, [VP]),
+    "msa_create": (C.c_int, [C.POINTER(MsParams), C.POINTER(MsbVoxelSpec), I32, VP, VP, I32, I32,
+                             C.POINTER(MsAllocator), VP, C.POINTER(VP)]),
+    "msa_gradients": (C.c_int, [VP, I32, VP, VP, VP, VP, VP, VP, I32]),
+    "msa_sizes": (C.c_int, [VP, C.POINTER(I64), C.POINTER(I64)]),
+    "msa_destroy": (C.c_int, [VP]),
     "ms_version": (C.c_char_p, []),
 }
 

@@ -11,7 +11,7 @@
 //   3. rows are laid out sliced-ELL (32 masses per slice), and every record
 //      gets a back reference in its partner's row.
 // Everything is O(S) except the optional Morton sort (O(N log N)).
-#include "../../include/cronos_ms.h"
+#include "cronos_ms.h"
 #include "ms_internal.h"
 
 #include <algorithm>
@@ -24,14 +24,19 @@
 #include <vector>
 
 namespace {
-
 thread_local std::string g_last_error = "no error";
+}  // namespace
 
+namespace ms {
 ms_status fail(ms_status st, const std::string &msg)
 {
     g_last_error = msg;
     return st;
 }
+}  // namespace ms
+
+namespace {
+using ms::fail;
 
 #define MS_CUDA_TRY(expr)                                                                     \
     do {                                                                                      \
@@ -63,22 +68,29 @@ struct ms_sim {
     std::vector<int32_t> iperm;     // caller -> internal
 
     // host copies needed to rebuild actuation coefficients
-    std::vector<uint32_t> spring_rec;   // caller spring -> record slot
+    std::vector<uint32_t> spring_rec;   // caller spring -> merged record
+    std::vector<uint32_t> rec_slot_a, rec_slot_b;   // merged record -> device slot(s)
     std::vector<float> k_caller, L0_caller;
-    std::vector<double> rec_KL;         // per record slot: sum k * L0
+    std::vector<double> rec_KL;         // per merged record: sum k * L0
 
     // device layout
     int n_slices = 0;
     int64_t n_slots = 0, n_back_slots = 0, n_records = 0;
     int max_fwd = 0, max_back = 0;
-    float4 *x4[2] = {nullptr, nullptr};
-    float4 *v4[2] = {nullptr, nullptr};
+    float4 *st[2] = {nullptr, nullptr};   // 2 float4 per mass: (x, w), (v, 0)
     int cur = 0;
     float4 *fext = nullptr;
     uint4 *slice = nullptr;
     int32_t *f_nbr = nullptr;
-    float *f_k = nullptr, *f_L0 = nullptr, *f_c = nullptr, *f_al = nullptr, *f_be = nullptr;
+    float2 *f_kl = nullptr, *f_ab = nullptr;
+    float *f_c = nullptr;
     uint32_t *b_ent = nullptr;
+    // tiled layout
+    int kernel = 0;                     // ms::kKernelGather or ms::kKernelTiled
+    int n_tiles = 0, max_tile_local = 0;
+    uint16_t *t_nbr = nullptr;
+    int4 *tiles = nullptr;
+    int32_t *halo = nullptr;
     int32_t *d_perm = nullptr;
     float *stage = nullptr;             // (N,3)*2 floats for host copies
     int *err = nullptr;
@@ -184,19 +196,35 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
     if (alloc) { s->alloc = *alloc; s->custom_alloc = true; }
     s->c_uniform = c_uniform;
 
+    if (p->kernel < 0 || p->kernel > 2 || p->reorder < 0 || p->reorder > 2) return fail(MS_ERR_ARG, "kernel and reorder must be 0, 1 or 2");
+    s->kernel = p->kernel == 1 ? ms::kKernelGather : ms::kKernelTiled;
+
     // 1. mass order
     s->perm.resize(N); s->iperm.resize(N);
     for (int32_t i = 0; i < N; ++i) s->perm[i] = i;
-    if (p->reorder) {
+    const bool morton = p->reorder == 1 || (p->reorder == 0 && s->kernel == ms::kKernelTiled);
+    if (morton) {
         float lo[3] = {x0[0], x0[1], x0[2]}, hi[3] = {x0[0], x0[1], x0[2]};
         for (int32_t i = 0; i < N; ++i)
             for (int a = 0; a < 3; ++a) { lo[a] = std::min(lo[a], x0[3 * i + a]); hi[a] = std::max(hi[a], x0[3 * i + a]); }
         double ext = 0; for (int a = 0; a < 3; ++a) ext = std::max(ext, (double)hi[a] - lo[a]);
-        const double scale = ext > 0 ? 2097151.0 / ext : 0.0;
+        // quantise by the shortest spring, so a lattice maps to its integer
+        // cell coordinates and Morton blocks are aligned cubes of cells
+        double h = 0.0;
+        for (int64_t e = 0; e < S; ++e) {
+            const int32_t a = ij[2 * e], b = ij[2 * e + 1];
+            if (a < 0 || a >= N || b < 0 || b >= N) continue;      // rejected below
+            const double dx = (double)x0[3 * b] - x0[3 * a], dy = (double)x0[3 * b + 1] - x0[3 * a + 1],
+                         dz = (double)x0[3 * b + 2] - x0[3 * a + 2];
+            const double l = std::sqrt(dx * dx + dy * dy + dz * dz);
+            if (l > 0 && (h == 0.0 || l < h)) h = l;
+        }
+        double scale = h > 0 ? 1.0 / h : 0.0;
+        if (ext * scale >= 2097151.0 || scale == 0.0) scale = ext > 0 ? 2097151.0 / ext : 0.0;
         std::vector<std::pair<uint64_t, int32_t>> key(N);
         for (int32_t i = 0; i < N; ++i) {
             uint64_t code = 0;
-            for (int a = 0; a < 3; ++a) code |= spread3((uint64_t)((x0[3 * i + a] - lo[a]) * scale)) << a;
+            for (int a = 0; a < 3; ++a) code |= spread3((uint64_t)(((double)x0[3 * i + a] - lo[a]) * scale + 0.5)) << a;
             key[i] = {code, i};
         }
         std::sort(key.begin(), key.end());
@@ -205,7 +233,8 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
     }
     for (int32_t i = 0; i < N; ++i) s->iperm[s->perm[i]] = i;
 
-    // 2. file springs by owner (counting sort), merge parallel springs
+    // 2. file springs by owner (counting sort), merge parallel springs into
+    //    records: (owner < partner) in internal order, grouped by owner.
     std::vector<int64_t> row(N + 1, 0);
     for (int64_t e = 0; e < S; ++e) {
         const int32_t a = ij[2 * e], b = ij[2 * e + 1];
@@ -228,12 +257,19 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
             r_spring[at] = (int32_t)e;
         }
     }
-    // sort each row by (partner, spring) and count distinct partners
-    std::vector<int32_t> deg(N, 0);
+    // sort each row by (partner, spring) and merge equal partners
+    std::vector<int32_t> deg(N, 0), bdeg(N, 0);
+    std::vector<int64_t> rec_first(N + 1, 0);       // merged records of owner o: [rec_first[o], rec_first[o+1])
+    std::vector<int32_t> rec_partner;
+    std::vector<float2> rec_kl;
+    std::vector<float> rec_c;
+    rec_partner.reserve(S); rec_kl.reserve(S); rec_c.reserve(c ? S : 0);
+    s->rec_KL.clear(); s->rec_KL.reserve(S);
+    s->spring_rec.resize(S);
+    std::vector<double> sumK(N, 0.0);
     for (int32_t o = 0; o < N; ++o) {
         const int64_t b0 = row[o], b1 = row[o + 1];
-        // insertion sort (rows are short)
-        for (int64_t q = b0 + 1; q < b1; ++q) {
+        for (int64_t q = b0 + 1; q < b1; ++q) {      // insertion sort (rows are short)
             const int32_t vo = r_other[q], vs = r_spring[q];
             int64_t t = q - 1;
             while (t >= b0 && (r_other[t] > vo || (r_other[t] == vo && r_spring[t] > vs))) {
@@ -241,48 +277,10 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
             }
             r_other[t + 1] = vo; r_spring[t + 1] = vs;
         }
-        int d = 0;
-        for (int64_t q = b0; q < b1; ++q)
-            if (q == b0 || r_other[q] != r_other[q - 1]) ++d;
-        if (d > ms::kMaxFwdDegree)
-            return fail(MS_ERR_ARG, "mass " + std::to_string(s->perm[o]) + " owns " + std::to_string(d) +
-                                        " distinct partners after ordering; at most 31 are supported");
-        deg[o] = d;
-    }
-
-    // 3. sliced-ELL layout
-    const int n_slices = (N + 31) / 32;
-    s->n_slices = n_slices;
-    std::vector<ms::Slice> sl(n_slices);
-    int64_t off = 0;
-    for (int b = 0; b < n_slices; ++b) {
-        int mx = 0;
-        for (int l = 0; l < 32 && 32 * b + l < N; ++l) mx = std::max(mx, deg[32 * b + l]);
-        sl[b].fwd_off = (uint32_t)off;
-        sl[b].lens = (uint32_t)mx;
-        sl[b].pad = 0;
-        off += 32LL * mx;
-        s->max_fwd = std::max(s->max_fwd, mx);
-    }
-    if (off >= (int64_t)UINT32_MAX) return fail(MS_ERR_ARG, "too many spring slots for 32-bit offsets");
-    const int64_t n_slots = off;
-    s->n_slots = n_slots;
-    std::vector<int32_t> h_nbr(n_slots, -1);
-    std::vector<float> h_k(n_slots, 0.f), h_L0(n_slots, 0.f), h_c;
-    if (c) h_c.assign(n_slots, 0.f);
-    s->rec_KL.assign(n_slots, 0.0);
-    s->spring_rec.resize(S);
-    std::vector<int32_t> bdeg(N, 0);
-    std::vector<double> sumK(N, 0.0);
-    int64_t n_rec = 0;
-    for (int32_t o = 0; o < N; ++o) {
-        int slot = -1;
-        const int64_t b0 = row[o], b1 = row[o + 1];
-        const uint32_t base = sl[o >> 5].fwd_off + (uint32_t)(o & 31);
+        rec_first[o] = (int64_t)rec_partner.size();
         for (int64_t q = b0; q < b1;) {
             const int32_t j = r_other[q];
-            ++slot;
-            const uint32_t r = base + 32u * (uint32_t)slot;
+            const uint32_t m = (uint32_t)rec_partner.size();
             double K = 0, KL = 0, Lsum = 0, Csum = 0;
             int cnt = 0;
             for (; q < b1 && r_other[q] == j; ++q) {
@@ -296,56 +294,213 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
                     L = (double)(float)std::sqrt(dx * dx + dy * dy + dz * dz);
                 }
                 K += k[e]; KL += (double)k[e] * L; Lsum += L; Csum += c ? c[e] : 0.0; ++cnt;
-                s->spring_rec[e] = r;
+                s->spring_rec[e] = m;
             }
-            h_nbr[r] = j;
-            h_k[r] = (float)K;
-            h_L0[r] = (float)(K > 0 ? KL / K : Lsum / cnt);
-            if (c) h_c[r] = (float)Csum;
-            s->rec_KL[r] = K > 0 ? KL : 0.0;
-            bdeg[j]++;
+            rec_partner.push_back(j);
+            rec_kl.push_back(make_float2((float)K, (float)(K > 0 ? KL / K : Lsum / cnt)));
+            if (c) rec_c.push_back((float)Csum);
+            s->rec_KL.push_back(K > 0 ? KL : 0.0);
+            deg[o]++; bdeg[j]++;
             sumK[o] += K; sumK[j] += K;
-            ++n_rec;
         }
     }
+    rec_first[N] = (int64_t)rec_partner.size();
+    const int64_t n_rec = (int64_t)rec_partner.size();
     s->n_records = n_rec;
-    int64_t boff = 0;
-    for (int b = 0; b < n_slices; ++b) {
-        int mx = 0;
-        for (int l = 0; l < 32 && 32 * b + l < N; ++l) mx = std::max(mx, bdeg[32 * b + l]);
-        if (mx > 0xffff) return fail(MS_ERR_ARG, "a mass has more than 65535 lower-indexed partners");
-        sl[b].bwd_off = (uint32_t)boff;
-        sl[b].lens |= (uint32_t)mx << 16;
-        boff += 32LL * mx;
-        s->max_back = std::max(s->max_back, mx);
-    }
-    if (boff >= (int64_t)UINT32_MAX) return fail(MS_ERR_ARG, "too many back-reference slots for 32-bit offsets");
-    s->n_back_slots = boff;
-    std::vector<uint32_t> h_b(boff, ms::kBackPad);
-    {
-        std::vector<int32_t> bfill(N, 0);
-        for (int32_t o = 0; o < N; ++o) {          // owners ascending: back lists sorted by owner
-            const uint32_t base = sl[o >> 5].fwd_off + (uint32_t)(o & 31);
-            for (int s_ = 0; s_ < deg[o]; ++s_) {
-                const int32_t j = h_nbr[base + 32u * (uint32_t)s_];
-                const int t = bfill[j]++;
-                h_b[sl[j >> 5].bwd_off + 32u * (uint32_t)t + (uint32_t)(j & 31)] = (uint32_t)o | ((uint32_t)s_ << ms::kOwnerBits);
+    r_other.clear(); r_other.shrink_to_fit(); r_spring.clear(); r_spring.shrink_to_fit();
+    if (n_rec >= (int64_t)UINT32_MAX / 2) return fail(MS_ERR_ARG, "too many springs for 32-bit record offsets");
+
+    // 3. device layout of the chosen kernel
+    const int n_slices = (N + 31) / 32;
+    s->n_slices = n_slices;
+    std::vector<uint32_t> slot_a(n_rec, 0), slot_b(n_rec, UINT32_MAX);   // record -> its slot(s)
+    std::vector<ms::Slice> sl;
+    std::vector<int32_t> h_nbr;
+    std::vector<uint16_t> h_nbr16;
+    std::vector<uint32_t> h_b;
+    std::vector<int4> h_tiles;
+    std::vector<int32_t> h_halo;
+    std::vector<float2> h_kl;
+    std::vector<float> h_c;
+    int64_t n_slots = 0;
+    if (s->kernel == ms::kKernelTiled) {
+        std::fill(slot_a.begin(), slot_a.end(), UINT32_MAX);
+        // every mass lists all of its springs (both directions); partners are
+        // tile-local indices: members 0..nb-1, then the tile's halo
+        const int B = ms::kTileMasses;
+        const int n_tiles = (N + B - 1) / B;
+        std::vector<int64_t> inc_first(N + 1, 0);
+        for (int32_t i = 0; i < N; ++i) inc_first[i + 1] = inc_first[i] + deg[i] + bdeg[i];
+        std::vector<int32_t> inc_p(inc_first[N]);
+        std::vector<uint32_t> inc_m(inc_first[N]);
+        {
+            std::vector<int64_t> fill(inc_first.begin(), inc_first.end() - 1);
+            // masses ascending: each mass first sees its lower partners (as j), then its own records
+            for (int32_t o = 0; o < N; ++o)
+                for (int64_t m = rec_first[o]; m < rec_first[o + 1]; ++m) {
+                    const int32_t j = rec_partner[m];
+                    inc_p[fill[o]] = j; inc_m[fill[o]++] = (uint32_t)m;
+                    inc_p[fill[j]] = o; inc_m[fill[j]++] = (uint32_t)m;
+                }
+        }
+        int max_deg = 0;
+        for (int32_t i = 0; i < N; ++i) max_deg = std::max<int>(max_deg, (int)(inc_first[i + 1] - inc_first[i]));
+        if (max_deg > 0xffff) return fail(MS_ERR_ARG, "a mass has more than 65535 springs");
+        // Slot order inside a row.  When every mass's springs point in
+        // distinct directions of the 26-neighbourhood (a lattice), slot q is
+        // the direction q for every mass, so the 32 lanes of a warp read
+        // partners that are one shifted block of the Morton order (few
+        // shared-memory bank conflicts).  Otherwise rows are compact, in
+        // partner order.
+        std::vector<int8_t> inc_dir(inc_p.size(), -1);
+        bool by_dir = true;
+        for (int32_t i = 0; i < N && by_dir; ++i) {
+            const float *xi = x0 + 3 * (size_t)s->perm[i];
+            uint32_t seen = 0;
+            for (int64_t q = inc_first[i]; q < inc_first[i + 1]; ++q) {
+                const float *xj = x0 + 3 * (size_t)s->perm[inc_p[q]];
+                const double d[3] = {(double)xj[0] - xi[0], (double)xj[1] - xi[1], (double)xj[2] - xi[2]};
+                const double L = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                int t[3];
+                for (int a = 0; a < 3; ++a) t[a] = d[a] > 0.25 * L ? 1 : (d[a] < -0.25 * L ? -1 : 0);
+                int code = (t[2] + 1) * 9 + (t[1] + 1) * 3 + (t[0] + 1);
+                if (code == 13 || L == 0.0) { by_dir = false; break; }
+                if (code > 13) --code;                    // 0..25
+                if (seen & (1u << code)) { by_dir = false; break; }
+                seen |= 1u << code;
+                inc_dir[q] = (int8_t)code;
+            }
+        }
+        sl.assign(n_slices, ms::Slice{0, 0, 0, 0});
+        h_tiles.resize(2 * (size_t)n_tiles);
+        std::vector<int32_t> halo;
+        int max_local = 0;
+        for (int t = 0; t < n_tiles; ++t) {
+            const int32_t base = t * B, nb = std::min(B, N - base);
+            halo.clear();
+            int slots = 0;
+            for (int32_t i = base; i < base + nb; ++i) {
+                if (by_dir) {
+                    for (int64_t q = inc_first[i]; q < inc_first[i + 1]; ++q) slots = std::max<int>(slots, inc_dir[q] + 1);
+                } else {
+                    slots = std::max<int>(slots, (int)(inc_first[i + 1] - inc_first[i]));
+                }
+                for (int64_t q = inc_first[i]; q < inc_first[i + 1]; ++q)
+                    if (inc_p[q] < base || inc_p[q] >= base + nb) halo.push_back(inc_p[q]);
+            }
+            std::sort(halo.begin(), halo.end());
+            halo.erase(std::unique(halo.begin(), halo.end()), halo.end());
+            const int nloc = nb + (int)halo.size();
+            max_local = std::max(max_local, nloc);
+            if (nloc > ms::kTileMaxLocal) {
+                if (s->p.kernel == ms::kKernelTiled)
+                    return fail(MS_ERR_ARG, "tile " + std::to_string(t) + " needs " + std::to_string(nloc) +
+                                                " shared-memory entries (> " + std::to_string(ms::kTileMaxLocal) + ")");
+                s->kernel = ms::kKernelGather;       // fall back to the gather layout
+                break;
+            }
+            h_tiles[2 * t] = make_int4(base, nb, (int)h_halo.size(), (int)halo.size());
+            h_tiles[2 * t + 1] = make_int4((int)n_slots, slots, 0, 0);
+            h_halo.insert(h_halo.end(), halo.begin(), halo.end());
+            n_slots += (int64_t)slots * B;
+            if (n_slots >= (int64_t)INT32_MAX) return fail(MS_ERR_ARG, "too many spring slots for 32-bit offsets");
+            s->max_fwd = std::max(s->max_fwd, slots);
+        }
+        if (s->kernel == ms::kKernelTiled) {
+            s->max_tile_local = max_local;
+            s->n_tiles = n_tiles;
+            h_nbr16.assign(n_slots, 0xffffu);
+            h_kl.assign(n_slots, make_float2(0.f, 0.f));
+            if (c) h_c.assign(n_slots, 0.f);
+            for (int t = 0; t < n_tiles; ++t) {
+                const int4 T = h_tiles[2 * t], R = h_tiles[2 * t + 1];
+                const int32_t *hb = h_halo.data() + T.z;
+                for (int32_t i = T.x; i < T.x + T.y; ++i) {
+                    int slot = 0;
+                    for (int64_t q = inc_first[i]; q < inc_first[i + 1]; ++q, ++slot) {
+                        if (by_dir) slot = inc_dir[q];
+                        const int32_t pidx = inc_p[q];
+                        int loc;
+                        if (pidx >= T.x && pidx < T.x + T.y) loc = pidx - T.x;
+                        else loc = T.y + (int)(std::lower_bound(hb, hb + T.w, pidx) - hb);
+                        const uint32_t r = (uint32_t)R.x + (uint32_t)slot * B + (uint32_t)(i - T.x);
+                        const uint32_t m = inc_m[q];
+                        h_nbr16[r] = (uint16_t)loc;
+                        h_kl[r] = rec_kl[m];
+                        if (c) h_c[r] = rec_c[m];
+                        if (slot_a[m] == UINT32_MAX) slot_a[m] = r; else slot_b[m] = r;
+                    }
+                }
             }
         }
     }
-    r_other.clear(); r_other.shrink_to_fit(); r_spring.clear(); r_spring.shrink_to_fit();
+    if (s->kernel == ms::kKernelGather) {
+        sl.assign(n_slices, ms::Slice{0, 0, 0, 0});
+        n_slots = 0;
+        for (int b = 0; b < n_slices; ++b) {
+            int mx = 0;
+            for (int l = 0; l < 32 && 32 * b + l < N; ++l) mx = std::max(mx, deg[32 * b + l]);
+            if (mx > ms::kMaxFwdDegree) {
+                int who = 0;
+                for (int l = 0; l < 32 && 32 * b + l < N; ++l) if (deg[32 * b + l] == mx) who = 32 * b + l;
+                return fail(MS_ERR_ARG, "mass " + std::to_string(s->perm[who]) + " owns " + std::to_string(mx) +
+                                            " distinct partners after ordering; at most 31 are supported");
+            }
+            sl[b].fwd_off = (uint32_t)n_slots;
+            sl[b].lens = (uint32_t)mx;
+            n_slots += 32LL * mx;
+            s->max_fwd = std::max(s->max_fwd, mx);
+        }
+        h_nbr.assign(n_slots, -1);
+        h_kl.assign(n_slots, make_float2(0.f, 0.f));
+        if (c) h_c.assign(n_slots, 0.f);
+        for (int32_t o = 0; o < N; ++o) {
+            const uint32_t base = sl[o >> 5].fwd_off + (uint32_t)(o & 31);
+            for (int64_t m = rec_first[o]; m < rec_first[o + 1]; ++m) {
+                const uint32_t r = base + 32u * (uint32_t)(m - rec_first[o]);
+                h_nbr[r] = rec_partner[m];
+                h_kl[r] = rec_kl[m];
+                if (c) h_c[r] = rec_c[m];
+                slot_a[m] = r;
+            }
+        }
+        int64_t boff = 0;
+        for (int b = 0; b < n_slices; ++b) {
+            int mx = 0;
+            for (int l = 0; l < 32 && 32 * b + l < N; ++l) mx = std::max(mx, bdeg[32 * b + l]);
+            if (mx > 0xffff) return fail(MS_ERR_ARG, "a mass has more than 65535 lower-indexed partners");
+            sl[b].bwd_off = (uint32_t)boff;
+            sl[b].lens |= (uint32_t)mx << 16;
+            boff += 32LL * mx;
+            s->max_back = std::max(s->max_back, mx);
+        }
+        if (boff >= (int64_t)UINT32_MAX) return fail(MS_ERR_ARG, "too many back-reference slots for 32-bit offsets");
+        s->n_back_slots = boff;
+        h_b.assign(boff, ms::kBackPad);
+        std::vector<int32_t> bfill(N, 0);
+        for (int32_t o = 0; o < N; ++o)            // owners ascending: back lists sorted by owner
+            for (int64_t m = rec_first[o]; m < rec_first[o + 1]; ++m) {
+                const int32_t j = rec_partner[m];
+                const int t = bfill[j]++;
+                h_b[sl[j >> 5].bwd_off + 32u * (uint32_t)t + (uint32_t)(j & 31)] =
+                    (uint32_t)o | ((uint32_t)(m - rec_first[o]) << ms::kOwnerBits);
+            }
+    }
+    s->n_slots = n_slots;
+    s->rec_slot_a.swap(slot_a);
+    s->rec_slot_b.swap(slot_b);
 
     // masses
-    std::vector<float4> hx(N), hv(N), hf;
+    std::vector<float4> hs(2 * (size_t)N), hf;
     double bound = 0.0;
     const double dt2 = (double)p->dt * p->dt;
     for (int32_t i = 0; i < N; ++i) {
         const int32_t cidx = s->perm[i];
         const bool anchored = fixed && fixed[cidx];
         const float w = anchored ? -1.0f : (float)(1.0 / (double)mass[cidx]);
-        hx[i] = make_float4(x0[3 * cidx], x0[3 * cidx + 1], x0[3 * cidx + 2], w);
-        hv[i] = anchored ? make_float4(0.f, 0.f, 0.f, 0.f)
-                         : make_float4(v0[3 * cidx], v0[3 * cidx + 1], v0[3 * cidx + 2], 0.f);
+        hs[2 * (size_t)i] = make_float4(x0[3 * cidx], x0[3 * cidx + 1], x0[3 * cidx + 2], w);
+        hs[2 * (size_t)i + 1] = anchored ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                         : make_float4(v0[3 * cidx], v0[3 * cidx + 1], v0[3 * cidx + 2], 0.f);
         if (!anchored) bound = std::max(bound, dt2 * (2.0 * sumK[i] + (p->contact_on ? p->k_c : 0.0)) / mass[cidx]);
     }
     s->stability = bound;
@@ -364,18 +519,21 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
 
     // 4. device upload
     ms_status st;
-    if ((st = upload(s, &s->x4[0], hx.data(), N)) != MS_OK) return st;
-    if ((st = upload(s, &s->v4[0], hv.data(), N)) != MS_OK) return st;
-    if ((st = upload(s, &s->x4[1], hx.data(), N)) != MS_OK) return st;
-    if ((st = upload(s, &s->v4[1], hv.data(), N)) != MS_OK) return st;
+    if ((st = upload(s, &s->st[0], hs.data(), 2 * (size_t)N)) != MS_OK) return st;
+    if ((st = upload(s, &s->st[1], hs.data(), 2 * (size_t)N)) != MS_OK) return st;
     if (fext && (st = upload(s, &s->fext, hf.data(), N)) != MS_OK) return st;
     static_assert(sizeof(ms::Slice) == sizeof(uint4), "slice size");
     if ((st = upload(s, &s->slice, (const uint4 *)sl.data(), n_slices)) != MS_OK) return st;
-    if ((st = upload(s, &s->f_nbr, h_nbr.data(), n_slots)) != MS_OK) return st;
-    if ((st = upload(s, &s->f_k, h_k.data(), n_slots)) != MS_OK) return st;
-    if ((st = upload(s, &s->f_L0, h_L0.data(), n_slots)) != MS_OK) return st;
+    if ((st = upload(s, &s->f_kl, h_kl.data(), n_slots)) != MS_OK) return st;
     if (c && (st = upload(s, &s->f_c, h_c.data(), n_slots)) != MS_OK) return st;
-    if ((st = upload(s, &s->b_ent, h_b.data(), boff)) != MS_OK) return st;
+    if (s->kernel == ms::kKernelGather) {
+        if ((st = upload(s, &s->f_nbr, h_nbr.data(), n_slots)) != MS_OK) return st;
+        if ((st = upload(s, &s->b_ent, h_b.data(), h_b.size())) != MS_OK) return st;
+    } else {
+        if ((st = upload(s, &s->t_nbr, h_nbr16.data(), n_slots)) != MS_OK) return st;
+        if ((st = upload(s, &s->tiles, h_tiles.data(), h_tiles.size())) != MS_OK) return st;
+        if ((st = upload(s, &s->halo, h_halo.data(), h_halo.size())) != MS_OK) return st;
+    }
     if (s->permuted && (st = upload(s, &s->d_perm, s->perm.data(), N)) != MS_OK) return st;
     if ((st = upload<float>(s, &s->stage, nullptr, (size_t)N * 6)) != MS_OK) return st;
     if ((st = upload<int>(s, &s->err, nullptr, 1)) != MS_OK) return st;
@@ -405,25 +563,25 @@ ms_status ms_set_actuation(ms_sim *s, float freq_hz, const float *amp, const flo
     if (!amp) { s->actuated = false; s->freq = 0.0; return MS_OK; }
     if (!phase) return fail(MS_ERR_ARG, "phase is required with amp");
     if (!std::isfinite(freq_hz)) return fail(MS_ERR_ARG, "freq must be finite");
-    const int64_t S = s->S, n = s->n_slots;
-    std::vector<double> sa(n, 0.0), sb(n, 0.0);
+    const int64_t S = s->S, nrec = s->n_records, n = s->n_slots;
+    std::vector<double> sa(nrec, 0.0), sb(nrec, 0.0);
     for (int64_t e = 0; e < S; ++e) {
         if (!std::isfinite(amp[e]) || !std::isfinite(phase[e])) return fail(MS_ERR_ARG, "non-finite amp or phase at spring " + std::to_string(e));
         const double w = (double)s->k_caller[e] * s->L0_caller[e] * amp[e];
-        const uint32_t r = s->spring_rec[e];
-        sa[r] += w * std::cos((double)phase[e]);    // coefficient of sin(2 pi f t)
-        sb[r] += w * std::sin((double)phase[e]);    // coefficient of cos(2 pi f t)
+        const uint32_t m = s->spring_rec[e];
+        sa[m] += w * std::cos((double)phase[e]);    // coefficient of sin(2 pi f t)
+        sb[m] += w * std::sin((double)phase[e]);    // coefficient of cos(2 pi f t)
     }
-    std::vector<float> al(n, 0.f), be(n, 0.f);
-    for (int64_t r = 0; r < n; ++r)
-        if (s->rec_KL[r] > 0) { al[r] = (float)(sa[r] / s->rec_KL[r]); be[r] = (float)(sb[r] / s->rec_KL[r]); }
+    std::vector<float2> ab(n, make_float2(0.f, 0.f));
+    for (int64_t m = 0; m < nrec; ++m) {
+        if (!(s->rec_KL[m] > 0)) continue;
+        const float2 v = make_float2((float)(sa[m] / s->rec_KL[m]), (float)(sb[m] / s->rec_KL[m]));
+        ab[s->rec_slot_a[m]] = v;
+        if (s->rec_slot_b[m] != UINT32_MAX) ab[s->rec_slot_b[m]] = v;
+    }
     ms_status st;
-    if (!s->f_al) {
-        if ((st = upload<float>(s, &s->f_al, nullptr, n)) != MS_OK) return st;
-        if ((st = upload<float>(s, &s->f_be, nullptr, n)) != MS_OK) return st;
-    }
-    MS_CUDA_TRY(cudaMemcpyAsync(s->f_al, al.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s->stream));
-    MS_CUDA_TRY(cudaMemcpyAsync(s->f_be, be.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s->stream));
+    if (!s->f_ab && (st = upload<float2>(s, &s->f_ab, nullptr, n)) != MS_OK) return st;
+    MS_CUDA_TRY(cudaMemcpyAsync(s->f_ab, ab.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, s->stream));
     MS_CUDA_TRY(cudaStreamSynchronize(s->stream));
     s->actuated = true;
     s->freq = freq_hz;
@@ -435,9 +593,11 @@ ms_status ms_step(ms_sim *s, int32_t nsteps)
     if (!s) return fail(MS_ERR_ARG, "sim is NULL");
     if (nsteps < 0) return fail(MS_ERR_ARG, "nsteps must be >= 0");
     ms::StepArgs a{};
-    a.fext = s->fext; a.slice = s->slice; a.f_nbr = s->f_nbr; a.f_k = s->f_k; a.f_L0 = s->f_L0;
-    a.f_c = s->f_c; a.f_al = s->actuated ? s->f_al : nullptr; a.f_be = s->actuated ? s->f_be : nullptr;
+    a.fext = s->fext; a.slice = s->slice; a.f_nbr = s->f_nbr; a.f_kl = s->f_kl;
+    a.f_c = s->f_c; a.f_ab = s->actuated ? s->f_ab : nullptr;
     a.b_ent = s->b_ent; a.err = s->err; a.N = s->N; a.c_uniform = s->c_uniform;
+    a.t_nbr = s->t_nbr; a.tiles = s->tiles; a.halo = s->halo; a.n_tiles = s->n_tiles;
+    a.tile_local = s->max_tile_local; a.tiled = s->kernel == ms::kKernelTiled;
     a.dt = s->p.dt; a.gx = s->p.g[0]; a.gy = s->p.g[1]; a.gz = s->p.g[2];
     a.k_c = s->p.k_c; a.mu = s->p.mu; a.keep = 1.0f - s->p.vel_damping; a.contact = s->p.contact_on;
     const double two_pi_f = 2.0 * M_PI * s->freq;
@@ -447,8 +607,8 @@ ms_status ms_step(ms_sim *s, int32_t nsteps)
             a.s_n = (float)std::sin(two_pi_f * t);
             a.c_n = (float)std::cos(two_pi_f * t);
         }
-        a.x = s->x4[s->cur]; a.v = s->v4[s->cur];
-        a.xo = s->x4[s->cur ^ 1]; a.vo = s->v4[s->cur ^ 1];
+        a.st = s->st[s->cur];
+        a.sto = s->st[s->cur ^ 1];
         MS_CUDA_TRY(ms::launch_step(a, s->stream));
         s->cur ^= 1;
     }
@@ -461,11 +621,11 @@ ms_status ms_get_state(ms_sim *s, float *x, float *v, int32_t on_device)
     if (!s) return fail(MS_ERR_ARG, "sim is NULL");
     const int N = s->N;
     if (on_device) {
-        MS_CUDA_TRY(ms::launch_gather_state(s->x4[s->cur], s->v4[s->cur], s->d_perm, N, x, v, s->stream));
+        MS_CUDA_TRY(ms::launch_gather_state(s->st[s->cur], s->d_perm, N, x, v, s->stream));
         return MS_OK;
     }
     float *sx = x ? s->stage : nullptr, *sv = v ? s->stage + 3 * (size_t)N : nullptr;
-    MS_CUDA_TRY(ms::launch_gather_state(s->x4[s->cur], s->v4[s->cur], s->d_perm, N, sx, sv, s->stream));
+    MS_CUDA_TRY(ms::launch_gather_state(s->st[s->cur], s->d_perm, N, sx, sv, s->stream));
     if (x) MS_CUDA_TRY(cudaMemcpyAsync(x, sx, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, s->stream));
     if (v) MS_CUDA_TRY(cudaMemcpyAsync(v, sv, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, s->stream));
     return ms_sync(s);
@@ -483,7 +643,7 @@ ms_status ms_set_state(ms_sim *s, const float *x, const float *v, int32_t on_dev
         x = x ? s->stage : nullptr;
         v = v ? s->stage + 3 * (size_t)N : nullptr;
     }
-    MS_CUDA_TRY(ms::launch_scatter_state(s->x4[s->cur], s->v4[s->cur], s->d_perm, N, x, v, s->stream));
+    MS_CUDA_TRY(ms::launch_scatter_state(s->st[s->cur], s->d_perm, N, x, v, s->stream));
     if (!on_device) MS_CUDA_TRY(cudaStreamSynchronize(s->stream));
     return MS_OK;
 }
@@ -494,7 +654,8 @@ ms_status ms_sync(ms_sim *s)
     MS_CUDA_TRY(cudaStreamSynchronize(s->stream));
     int flag = 0;
     MS_CUDA_TRY(cudaMemcpy(&flag, s->err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (flag) return fail(MS_ERR_NONFINITE, "a step produced a non-finite position or velocity");
+    if (flag & ms::kErrTimeout) return fail(MS_ERR_TIMEOUT, "a bounded device-side wait gave up (bulk copy never completed)");
+    if (flag & ms::kErrNonFinite) return fail(MS_ERR_NONFINITE, "a step produced a non-finite position or velocity");
     return MS_OK;
 }
 
@@ -505,6 +666,7 @@ ms_status ms_get_info(const ms_sim *s, ms_info_t *out)
     out->n_slots = s->n_slots; out->n_back_slots = s->n_back_slots; out->device_bytes = s->device_bytes;
     out->step_count = s->step_count; out->stability_bound = s->stability;
     out->max_fwd_degree = s->max_fwd; out->max_back_degree = s->max_back;
+    out->kernel = s->kernel; out->n_tiles = s->n_tiles; out->max_tile_local = s->max_tile_local;
     return MS_OK;
 }
 

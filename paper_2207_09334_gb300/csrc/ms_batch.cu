@@ -1,0 +1,855 @@
+// ms_batch.cu -- batched voxel-robot populations: one persistent launch
+// advances thousands of independent robots of uneven size.
+//
+// Each robot is small (at most 4096 masses), so its whole state lives in
+// shared memory for the length of the run: positions+inverse mass, velocity
+// and the force accumulator, 48 bytes per mass.  Spring records stay in
+// global memory (the same sliced-ELL layout as the single-system step, with
+// robot-local mass indices) and are re-read every step from L2.  A step is
+// two phases separated by a barrier: every mass gathers its spring forces
+// from the shared-memory state at t_n (Jacobi, like the paper's grid-wide
+// synchronisation in Algorithm 1), then every mass integrates in place.
+//
+// Two schedules share one kernel:
+//   block-per-robot  all 256 threads of a CTA work on one robot (__syncthreads);
+//   warp-per-robot   each warp of a CTA owns a small robot (__syncwarp only).
+// The CTAs are persistent: they pull work items (a robot, or a group of up to
+// eight small robots) from a queue ordered by decreasing cost, and the
+// choice of schedule per robot-size bucket is made by timing both
+// (msb_autotune).  At the end of its item a CTA reduces the robot's centre of
+// mass with warp shuffles and writes the x-travel.
+#include "ms_voxel.h"
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <numeric>
+#include <vector>
+
+namespace ms {
+namespace {
+
+constexpr int kBatchThreads = 256;
+constexpr int kWarpsPerCta = kBatchThreads / 32;
+constexpr int kWarpModeMax = 256;   // robots up to this many masses may run warp-per-robot
+
+struct BatchArgs {
+    const RobotDev *robots;
+    const int4 *items;     // (x, count, mode, cost): mode 0 = block (x = robot),
+                           // mode 1 = warp (robots wlist[x .. x+count))
+    const int *wlist;
+    int n_items;
+    int *queue;            // next item (zeroed before each launch)
+    float4 *st;            // population state, 2 float4 per mass
+    Records rec;
+    Env env;
+    const float2 *sc;      // (sin, cos)(2 pi f t_n) per step of this run
+    int nsteps;
+    int warp_cap;          // masses per warp region in warp mode
+    float *travel;         // per robot
+    int *err;
+};
+
+__global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchArgs a)
+{
+    extern __shared__ float4 smem[];
+    __shared__ int item_sh;
+    __shared__ float red_sh[2][kWarpsPerCta];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    for (;;) {
+        if (tid == 0) item_sh = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int it = item_sh;
+        __syncthreads();
+        if (it >= a.n_items) break;
+        const int4 item = a.items[it];
+
+        if (item.z == 0) {
+            // ---------------- block-per-robot ----------------
+            const RobotDev R = a.robots[item.x];
+            const int n = R.n;
+            float4 *xs = smem, *vs = smem + n, *fs = smem + 2 * n;
+            const float4 *g = a.st + 2 * R.mass_base;
+            for (int i = tid; i < n; i += kBatchThreads) { xs[i] = g[2 * i]; vs[i] = g[2 * i + 1]; }
+            __syncthreads();
+            for (int step = 0; step < a.nsteps; ++step) {
+                const float2 sc = __ldg(&a.sc[step]);
+                for (int i = tid; i < n; i += kBatchThreads) fs[i] = robot_force(a.rec, R.slice_base, i, xs, vs, sc.x, sc.y);
+                __syncthreads();
+                for (int i = tid; i < n; i += kBatchThreads) {
+                    float4 x = xs[i], v = vs[i];
+                    robot_integrate(a.env, x, v, fs[i]);
+                    xs[i] = x; vs[i] = v;
+                }
+                __syncthreads();
+            }
+            float mx = 0.f, m = 0.f;
+            bool bad = false;
+            for (int i = tid; i < n; i += kBatchThreads) {
+                const float4 x = xs[i], v = vs[i];
+                float4 *gw = a.st + 2 * R.mass_base;
+                gw[2 * i] = x; gw[2 * i + 1] = v;
+                if (x.w > 0.f) { const float mi = 1.0f / x.w; mx += mi * x.x; m += mi; }
+                bad |= !isfinite(x.x + x.y + x.z + v.x + v.y + v.z);
+            }
+            if (__syncthreads_or(bad) && tid == 0) atomicOr(a.err, kErrNonFinite);
+            mx = warp_sum(mx); m = warp_sum(m);
+            if (lane == 0) { red_sh[0][warp] = mx; red_sh[1][warp] = m; }
+            __syncthreads();
+            if (tid == 0) {
+                float smx = 0.f, sm = 0.f;
+                for (int w = 0; w < kWarpsPerCta; ++w) { smx += red_sh[0][w]; sm += red_sh[1][w]; }
+                a.travel[item.x] = smx / sm - R.com0_x;
+            }
+            __syncthreads();
+        } else {
+            // ---------------- warp-per-robot ----------------
+            if (warp < item.y) {
+                const int r = a.wlist[item.x + warp];
+                const RobotDev R = a.robots[r];
+                const int n = R.n;
+                float4 *xs = smem + (size_t)warp * 3 * a.warp_cap, *vs = xs + a.warp_cap, *fs = vs + a.warp_cap;
+                const float4 *g = a.st + 2 * R.mass_base;
+                for (int i = lane; i < n; i += 32) { xs[i] = g[2 * i]; vs[i] = g[2 * i + 1]; }
+                __syncwarp();
+                for (int step = 0; step < a.nsteps; ++step) {
+                    const float2 sc = __ldg(&a.sc[step]);
+                    for (int i = lane; i < n; i += 32) fs[i] = robot_force(a.rec, R.slice_base, i, xs, vs, sc.x, sc.y);
+                    __syncwarp();
+                    for (int i = lane; i < n; i += 32) {
+                        float4 x = xs[i], v = vs[i];
+                        robot_integrate(a.env, x, v, fs[i]);
+                        xs[i] = x; vs[i] = v;
+                    }
+                    __syncwarp();
+                }
+                float mx = 0.f, m = 0.f;
+                bool bad = false;
+                for (int i = lane; i < n; i += 32) {
+                    const float4 x = xs[i], v = vs[i];
+                    float4 *gw = a.st + 2 * R.mass_base;
+                    gw[2 * i] = x; gw[2 * i + 1] = v;
+                    if (x.w > 0.f) { const float mi = 1.0f / x.w; mx += mi * x.x; m += mi; }
+                    bad |= !isfinite(x.x + x.y + x.z + v.x + v.y + v.z);
+                }
+                if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, kErrNonFinite);
+                mx = warp_sum(mx); m = warp_sum(m);
+                if (lane == 0) a.travel[r] = mx / m - R.com0_x;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// (sin, cos)(2 pi f t_n) for the steps of one run, t_n = (counter + n) dt,
+// evaluated in double precision.
+__global__ void k_sc_table(const long long *counter, int nsteps, double dt, double two_pi_f, float2 *out)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nsteps) return;
+    const double t = (double)(*counter + n) * dt;
+    double s, c;
+    sincos(two_pi_f * t, &s, &c);
+    out[n] = make_float2((float)s, (float)c);
+}
+
+__global__ void k_advance(long long *counter, int nsteps) { *counter += nsteps; }
+
+// Centre-of-mass x travel of every robot from the global state (one CTA per robot).
+__global__ void k_com_travel(const RobotDev *robots, const float4 *st, float *travel)
+{
+    __shared__ float red[2][kWarpsPerCta];
+    const RobotDev R = robots[blockIdx.x];
+    float mx = 0.f, m = 0.f;
+    for (int i = threadIdx.x; i < R.n; i += blockDim.x) {
+        const float4 x = st[2 * (R.mass_base + i)];
+        if (x.w > 0.f) { const float mi = 1.0f / x.w; mx += mi * x.x; m += mi; }
+    }
+    mx = warp_sum(mx); m = warp_sum(m);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { red[0][warp] = mx; red[1][warp] = m; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float smx = 0.f, sm = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { smx += red[0][w]; sm += red[1][w]; }
+        travel[blockIdx.x] = smx / sm - R.com0_x;
+    }
+}
+
+}  // namespace
+}  // namespace ms
+
+using namespace ms;
+
+struct msb_batch {
+    ms_params p{};
+    msb_voxel_spec spec{};
+    double freq = 0.0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    ms_allocator alloc{};
+    bool custom_alloc = false;
+    std::vector<std::pair<void *, size_t>> allocs;
+    int64_t device_bytes = 0;
+
+    int n_robots = 0;
+    int64_t n_masses = 0, n_records = 0, n_slots = 0, n_back = 0;
+    int n_slices = 0;
+    int max_n = 0;
+    std::vector<RobotDev> h_robots;
+    std::vector<float4> h_st0;                 // initial state (for reset)
+
+    RobotDev *robots = nullptr;
+    float4 *st = nullptr, *st2 = nullptr;
+    uint4 *slice = nullptr;
+    int32_t *f_nbr = nullptr;
+    float2 *f_kl = nullptr, *f_ab = nullptr;
+    float *f_c = nullptr;
+    uint32_t *b_ent = nullptr;
+    float *travel = nullptr;
+    int *err = nullptr;
+    int *queue = nullptr;
+    long long *counter = nullptr;
+    float2 *sc = nullptr;
+    int sc_cap = 0;
+    int4 *items = nullptr;
+    int items_cap = 0;
+    std::vector<int4> h_items;
+    int *wlist = nullptr;
+    int wlist_cap = 0;
+    std::vector<int> h_wlist;
+    std::vector<uint8_t> warp_mode;           // per robot: 1 = warp-per-robot
+    int warp_cap = 32;
+    size_t smem_bytes = 0;
+    int grid = 0;
+    int64_t step_count = 0;
+    std::map<int, cudaGraphExec_t> graphs;
+
+    void *dev_alloc(size_t bytes)
+    {
+        if (bytes == 0) bytes = 16;
+        void *ptr = nullptr;
+        if (custom_alloc) ptr = alloc.alloc(bytes, stream, alloc.ctx);
+        else if (cudaMalloc(&ptr, bytes) != cudaSuccess) { cudaGetLastError(); ptr = nullptr; }
+        if (ptr) { allocs.push_back({ptr, bytes}); device_bytes += (int64_t)bytes; }
+        return ptr;
+    }
+    void drop_graphs()
+    {
+        for (auto &g : graphs) cudaGraphExecDestroy(g.second);
+        graphs.clear();
+    }
+    void release()
+    {
+        if (stream) cudaStreamSynchronize(stream); else cudaDeviceSynchronize();
+        drop_graphs();
+        for (auto &a : allocs) {
+            if (custom_alloc) alloc.free(a.first, a.second, stream, alloc.ctx);
+            else cudaFree(a.first);
+        }
+        allocs.clear();
+        if (cap_stream) { cudaStreamDestroy(cap_stream); cap_stream = nullptr; }
+    }
+};
+
+namespace {
+
+#define MSB_CUDA_TRY(expr)                                                                     \
+    do {                                                                                       \
+        cudaError_t _e = (expr);                                                               \
+        if (_e != cudaSuccess)                                                                 \
+            return fail(MS_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));     \
+    } while (0)
+
+template <class T>
+ms_status bupload(msb_batch *b, T **dst, const T *src, size_t count)
+{
+    *dst = (T *)b->dev_alloc(sizeof(T) * count);
+    if (!*dst) return fail(MS_ERR_OOM, "device allocation failed");
+    if (src && count) {
+        cudaError_t e = cudaMemcpyAsync(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice, b->stream);
+        if (e != cudaSuccess) return fail(MS_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+    }
+    return MS_OK;
+}
+
+// The 13 forward neighbour directions (dx, dy, dz) of the 26-neighbourhood:
+// (dz, dy, dx) lexicographically positive, so the partner is later in
+// raster (x fastest) order.
+struct Dir { int dx, dy, dz; };
+std::vector<Dir> forward_dirs()
+{
+    std::vector<Dir> d;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx)
+                if (dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)))) d.push_back({dx, dy, dz});
+    return d;
+}
+
+int dir_index(int dx, int dy, int dz)
+{
+    static const std::vector<Dir> d = forward_dirs();
+    for (int q = 0; q < (int)d.size(); ++q)
+        if (d[q].dx == dx && d[q].dy == dy && d[q].dz == dz) return q;
+    return -1;
+}
+
+// Build the schedule items from per-robot modes: block items one per robot,
+// warp items groups of up to 8 robots of similar size; ordered by
+// decreasing cost so the persistent CTAs balance (longest item first).
+void set_items(msb_batch *b, const std::vector<int> &block_robots, std::vector<int> warp_robots)
+{
+    b->h_items.clear();
+    b->h_wlist.clear();
+    int cap = 32;
+    for (int r : block_robots) b->h_items.push_back(make_int4(r, 1, 0, b->h_robots[r].n));
+    std::stable_sort(warp_robots.begin(), warp_robots.end(),
+                     [&](int x, int y) { return b->h_robots[x].n > b->h_robots[y].n; });
+    for (size_t q = 0; q < warp_robots.size(); q += kWarpsPerCta) {
+        const int cnt = (int)std::min<size_t>(kWarpsPerCta, warp_robots.size() - q);
+        int cost = 0;
+        for (int u = 0; u < cnt; ++u) {
+            const int r = warp_robots[q + u];
+            b->h_wlist.push_back(r);
+            cost = std::max(cost, b->h_robots[r].n);
+            cap = std::max(cap, b->h_robots[r].n);
+        }
+        b->h_items.push_back(make_int4((int)q, cnt, 1, cost));
+    }
+    b->warp_cap = (cap + 31) / 32 * 32;
+    std::stable_sort(b->h_items.begin(), b->h_items.end(), [](const int4 &x, const int4 &y) {
+        // a warp robot advances with 1/8 of the CTA's threads
+        const long long cx = (long long)x.w * (x.z == 0 ? 1 : 8), cy = (long long)y.w * (y.z == 0 ? 1 : 8);
+        return cx > cy;
+    });
+    size_t blk = 0;
+    for (auto &it : b->h_items) if (it.z == 0) blk = std::max(blk, (size_t)b->h_robots[it.x].n);
+    const size_t warp_bytes = b->h_wlist.empty() ? 0 : (size_t)kWarpsPerCta * 3 * b->warp_cap * sizeof(float4);
+    b->smem_bytes = std::max<size_t>(std::max(blk * 3 * sizeof(float4), warp_bytes), 16);
+}
+
+void build_items(msb_batch *b)
+{
+    std::vector<int> blk, wrp;
+    for (int r = 0; r < b->n_robots; ++r) (b->warp_mode[r] ? wrp : blk).push_back(r);
+    set_items(b, blk, wrp);
+}
+
+ms_status upload_items(msb_batch *b)
+{
+    const int n = (int)b->h_items.size();
+    if (n > b->items_cap) {
+        ms_status st = bupload<int4>(b, &b->items, nullptr, n);
+        if (st != MS_OK) return st;
+        b->items_cap = n;
+    }
+    MSB_CUDA_TRY(cudaMemcpyAsync(b->items, b->h_items.data(), sizeof(int4) * n, cudaMemcpyHostToDevice, b->stream));
+    const int nw = (int)b->h_wlist.size();
+    if (nw > b->wlist_cap || !b->wlist) {
+        ms_status st = bupload<int>(b, &b->wlist, nullptr, std::max(nw, 1));
+        if (st != MS_OK) return st;
+        b->wlist_cap = std::max(nw, 1);
+    }
+    if (nw) MSB_CUDA_TRY(cudaMemcpyAsync(b->wlist, b->h_wlist.data(), sizeof(int) * nw, cudaMemcpyHostToDevice, b->stream));
+    MSB_CUDA_TRY(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_bytes));
+    int dev = 0, sms = 0, per_sm = 0;
+    MSB_CUDA_TRY(cudaGetDevice(&dev));
+    MSB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    MSB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kBatchThreads, b->smem_bytes));
+    if (per_sm < 1) return fail(MS_ERR_ARG, "a robot does not fit in one CTA's shared memory");
+    b->grid = std::max(1, std::min(n, sms * per_sm));
+    MSB_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    b->drop_graphs();
+    return MS_OK;
+}
+
+ms_status ensure_sc(msb_batch *b, int nsteps)
+{
+    if (nsteps <= b->sc_cap) return MS_OK;
+    b->drop_graphs();                          // graphs hold the old table pointer
+    ms_status st = bupload<float2>(b, &b->sc, nullptr, std::max(nsteps, 1));
+    if (st != MS_OK) return st;
+    b->sc_cap = nsteps;
+    return MS_OK;
+}
+
+BatchArgs batch_args(msb_batch *b, int nsteps)
+{
+    BatchArgs a{};
+    a.robots = b->robots; a.items = b->items; a.wlist = b->wlist; a.n_items = (int)b->h_items.size(); a.queue = b->queue;
+    a.st = b->st;
+    a.rec = Records{b->slice, b->f_nbr, b->f_kl, b->f_c, b->f_ab, b->b_ent};
+    a.env = make_env(b->p);
+    a.sc = b->sc; a.nsteps = nsteps;
+    a.warp_cap = b->warp_cap; a.travel = b->travel; a.err = b->err;
+    return a;
+}
+
+// Enqueue one run (table, persistent kernel, clock advance) on stream s.
+ms_status enqueue_run(msb_batch *b, int nsteps, cudaStream_t s)
+{
+    MSB_CUDA_TRY(cudaMemsetAsync(b->queue, 0, sizeof(int), s));
+    const double two_pi_f = 2.0 * M_PI * b->freq;
+    k_sc_table<<<(nsteps + 255) / 256, 256, 0, s>>>(b->counter, nsteps, (double)b->p.dt, two_pi_f, b->sc);
+    MSB_CUDA_TRY(cudaGetLastError());
+    k_batch<<<b->grid, kBatchThreads, b->smem_bytes, s>>>(batch_args(b, nsteps));
+    MSB_CUDA_TRY(cudaGetLastError());
+    k_advance<<<1, 1, 0, s>>>(b->counter, nsteps);
+    MSB_CUDA_TRY(cudaGetLastError());
+    return MS_OK;
+}
+
+}  // namespace
+
+namespace ms {
+void launch_sc_table(const long long *counter, int nsteps, double dt, double two_pi_f, float2 *out, cudaStream_t s)
+{
+    if (nsteps > 0) k_sc_table<<<(nsteps + 255) / 256, 256, 0, s>>>(counter, nsteps, dt, two_pi_f, out);
+}
+
+ms_status build_voxels(const msb_voxel_spec *spec, int n_robots, const int32_t *dims, const uint8_t *materials,
+                       const float *phase, const float *logk, bool adjoint_maps, VoxelBuild &out)
+{
+    out = VoxelBuild();
+    std::vector<uint4> &h_slice = out.slice;
+    std::vector<int32_t> &h_nbr = out.nbr;
+    std::vector<float2> &h_kl = out.kl, &h_ab = out.ab;
+    std::vector<float> &h_c = out.c;
+    std::vector<uint32_t> &h_b = out.bent;
+    const std::vector<Dir> dirs = forward_dirs();
+    const double a = spec->voxel_edge;
+    float L0dir[13];
+    for (int d = 0; d < 13; ++d)
+        L0dir[d] = (float)(a * std::sqrt((double)(dirs[d].dx * dirs[d].dx + dirs[d].dy * dirs[d].dy + dirs[d].dz * dirs[d].dz)));
+
+    out.robots.resize(n_robots);
+    int64_t vox_off = 0;
+    for (int r = 0; r < n_robots; ++r) {
+        const int nx = dims[3 * r], ny = dims[3 * r + 1], nz = dims[3 * r + 2];
+        if (nx < 1 || ny < 1 || nz < 1 || (int64_t)nx * ny * nz > (1 << 20)) return fail(MS_ERR_ARG, "bad dims for robot " + std::to_string(r));
+        const int cx = nx + 1, cy = ny + 1, cz = nz + 1;
+        const int64_t nvox = (int64_t)nx * ny * nz;
+        const uint8_t *mat = materials + vox_off;
+        const float *ph = phase ? phase + vox_off : nullptr;
+        const float *lk = logk ? logk + vox_off : nullptr;
+        std::vector<int32_t> cmap((size_t)cx * cy * cz, -1);
+        std::vector<double> cmass((size_t)cx * cy * cz, 0.0);
+        int nonempty = 0;
+        for (int64_t v = 0; v < nvox; ++v) {
+            if (mat[v] >= spec->n_materials) return fail(MS_ERR_ARG, "material id out of range in robot " + std::to_string(r));
+            if (mat[v] == 0) continue;
+            if (ph && !std::isfinite(ph[v])) return fail(MS_ERR_ARG, "non-finite phase in robot " + std::to_string(r));
+            if (lk && !std::isfinite(lk[v])) return fail(MS_ERR_ARG, "non-finite logk in robot " + std::to_string(r));
+            ++nonempty;
+            const int ix = (int)(v % nx), iy = (int)((v / nx) % ny), iz = (int)(v / ((int64_t)nx * ny));
+            for (int c8 = 0; c8 < 8; ++c8) {
+                const int q = (ix + (c8 & 1)) + cx * ((iy + ((c8 >> 1) & 1)) + cy * (iz + (c8 >> 2)));
+                cmap[q] = 1;
+                cmass[q] += spec->voxel_mass / 8.0;
+            }
+        }
+        if (!nonempty) return fail(MS_ERR_ARG, "robot " + std::to_string(r) + " has no non-empty voxel");
+        int n = 0;
+        for (size_t q = 0; q < cmap.size(); ++q) if (cmap[q] > 0) cmap[q] = n++;
+        if (n > kMaxRobotMasses) return fail(MS_ERR_ARG, "robot " + std::to_string(r) + " has " + std::to_string(n) + " masses; at most 4096 are supported");
+        // merged springs per (owner corner, forward direction)
+        std::vector<double> K((size_t)n * 13, 0.0), Cc((size_t)n * 13, 0.0), SA((size_t)n * 13, 0.0), SB((size_t)n * 13, 0.0);
+        std::vector<uint8_t> has((size_t)n * 13, 0);
+        std::vector<short4> key_vox;                 // adjoint: voxels sharing each merged spring
+        std::vector<uint32_t> vkey;                  // adjoint: key of each voxel's 28 corner pairs
+        if (adjoint_maps) {
+            if (nvox > 32767) return fail(MS_ERR_ARG, "robot " + std::to_string(r) + " has too many voxels for the adjoint maps");
+            key_vox.assign((size_t)n * 13, make_short4(-1, -1, -1, -1));
+            vkey.assign((size_t)nvox * 28, UINT32_MAX);
+        }
+        for (int64_t v = 0; v < nvox; ++v) {
+            if (mat[v] == 0) continue;
+            const int ix = (int)(v % nx), iy = (int)((v / nx) % ny), iz = (int)(v / ((int64_t)nx * ny));
+            const double kv = lk ? std::exp((double)lk[v]) : (double)spec->mat_k[mat[v]];
+            const double cv = spec->mat_c[mat[v]], av = spec->mat_amp[mat[v]];
+            const double phv = ph ? (double)ph[v] : 0.0;
+            for (int p8 = 0; p8 < 8; ++p8)
+                for (int q8 = p8 + 1; q8 < 8; ++q8) {
+                    // corner offsets inside the voxel; q8 > p8 means q is later in raster order
+                    const int px = p8 & 1, py = (p8 >> 1) & 1, pz = p8 >> 2;
+                    const int qx = q8 & 1, qy = (q8 >> 1) & 1, qz = q8 >> 2;
+                    const int d = dir_index(qx - px, qy - py, qz - pz);
+                    const int owner = cmap[(ix + px) + cx * ((iy + py) + cy * (iz + pz))];
+                    const size_t key = (size_t)owner * 13 + d;
+                    K[key] += kv; Cc[key] += cv;
+                    SA[key] += kv * av * std::cos(phv); SB[key] += kv * av * std::sin(phv);
+                    has[key] = 1;
+                    if (adjoint_maps) {
+                        short4 &kvx = key_vox[key];
+                        if (kvx.x < 0) kvx.x = (short)v; else if (kvx.y < 0) kvx.y = (short)v;
+                        else if (kvx.z < 0) kvx.z = (short)v; else kvx.w = (short)v;
+                        int pair = 0;
+                        for (int a8 = 0; a8 < p8; ++a8) pair += 7 - a8;
+                        pair += q8 - p8 - 1;
+                        vkey[(size_t)v * 28 + pair] = (uint32_t)key;
+                    }
+                }
+        }
+        // corner positions, masses
+        RobotDev &R = out.robots[r];
+        R.mass_base = out.n_masses; R.n = n; R.slice_base = out.n_slices;
+        double M = 0, MX = 0;
+        std::vector<int> pos_of(n);
+        for (size_t q = 0; q < cmap.size(); ++q) {
+            if (cmap[q] < 0) continue;
+            const int qx = (int)(q % cx), qy = (int)((q / cx) % cy), qz = (int)(q / ((size_t)cx * cy));
+            const double m = cmass[q];
+            const float w = (float)(1.0 / m);
+            out.st0.push_back(make_float4((float)(qx * a), (float)(qy * a), (float)(qz * a), w));
+            out.st0.push_back(make_float4(0.f, 0.f, 0.f, 0.f));
+            M += m; MX += m * (double)(float)(qx * a);
+            pos_of[cmap[q]] = (int)q;
+        }
+        R.com0_x = (float)(MX / M);
+        R.inv_mass = (float)(1.0 / M);
+        R.vox_base = (int)vox_off;
+        R.n_vox = (int)nvox;
+        // forward degrees and sliced-ELL rows
+        std::vector<int> deg(n, 0), bdeg(n, 0);
+        for (int o = 0; o < n; ++o)
+            for (int d = 0; d < 13; ++d) if (has[(size_t)o * 13 + d]) deg[o]++;
+        const int ns = (n + 31) / 32;
+        const size_t slice0 = h_slice.size();
+        for (int s_ = 0; s_ < ns; ++s_) {
+            int mx = 0;
+            for (int l = 0; l < 32 && 32 * s_ + l < n; ++l) mx = std::max(mx, deg[32 * s_ + l]);
+            h_slice.push_back(make_uint4((uint32_t)h_nbr.size(), 0u, (uint32_t)mx, 0u));
+            h_nbr.resize(h_nbr.size() + 32 * (size_t)mx, -1);
+        }
+        h_kl.resize(h_nbr.size(), make_float2(0.f, 0.f));
+        h_ab.resize(h_nbr.size(), make_float2(0.f, 0.f));
+        h_c.resize(h_nbr.size(), 0.f);
+        std::vector<uint32_t> key_slot;
+        if (adjoint_maps) {
+            out.slot_vox.resize(h_nbr.size(), make_short4(-1, -1, -1, -1));
+            key_slot.assign((size_t)n * 13, UINT32_MAX);
+        }
+        for (int o = 0; o < n; ++o) {
+            const int q = pos_of[o];
+            const int ox = q % cx, oy = (q / cx) % cy, oz = q / (cx * cy);
+            int slot = 0;
+            for (int d = 0; d < 13; ++d) {
+                const size_t key = (size_t)o * 13 + d;
+                if (!has[key]) continue;
+                const int j = cmap[(ox + dirs[d].dx) + cx * ((oy + dirs[d].dy) + cy * (oz + dirs[d].dz))];
+                const uint32_t rr = h_slice[slice0 + (o >> 5)].x + 32u * slot + (uint32_t)(o & 31);
+                h_nbr[rr] = j;
+                h_kl[rr] = make_float2((float)K[key], L0dir[d]);
+                h_c[rr] = (float)Cc[key];
+                h_ab[rr] = K[key] > 0 ? make_float2((float)(SA[key] / K[key]), (float)(SB[key] / K[key])) : make_float2(0.f, 0.f);
+                if (adjoint_maps) { out.slot_vox[rr] = key_vox[key]; key_slot[key] = rr; }
+                bdeg[j]++;
+                ++slot;
+                ++out.n_records;
+            }
+        }
+        // back references
+        const size_t b0 = h_b.size();
+        for (int s_ = 0; s_ < ns; ++s_) {
+            int mx = 0;
+            for (int l = 0; l < 32 && 32 * s_ + l < n; ++l) mx = std::max(mx, bdeg[32 * s_ + l]);
+            h_slice[slice0 + s_].y = (uint32_t)h_b.size();
+            h_slice[slice0 + s_].z |= (uint32_t)mx << 16;
+            h_b.resize(h_b.size() + 32 * (size_t)mx, kBackPad);
+        }
+        (void)b0;
+        std::vector<int> bfill(n, 0);
+        for (int o = 0; o < n; ++o) {
+            const uint32_t base = h_slice[slice0 + (o >> 5)].x + (uint32_t)(o & 31);
+            for (int s_ = 0; s_ < deg[o]; ++s_) {
+                const int j = h_nbr[base + 32u * s_];
+                const int t = bfill[j]++;
+                h_b[h_slice[slice0 + (j >> 5)].y + 32u * t + (uint32_t)(j & 31)] = (uint32_t)o | ((uint32_t)s_ << kOwnerBits);
+            }
+        }
+        if (adjoint_maps) {
+            for (int64_t v = 0; v < nvox; ++v) {
+                for (int pr = 0; pr < 28; ++pr) {
+                    const uint32_t key = vkey[(size_t)v * 28 + pr];
+                    out.vox_slots.push_back(key == UINT32_MAX ? UINT32_MAX : key_slot[key]);
+                }
+                out.vox_amp.push_back(mat[v] ? spec->mat_amp[mat[v]] : 0.f);
+            }
+        }
+        out.n_slices += ns;
+        out.n_masses += n;
+        out.max_n = std::max(out.max_n, n);
+        vox_off += nvox;
+        if (h_nbr.size() >= (size_t)UINT32_MAX / 2 || h_b.size() >= (size_t)UINT32_MAX / 2)
+            return fail(MS_ERR_ARG, "population too large for 32-bit record offsets");
+    }
+
+    return MS_OK;
+}
+
+}  // namespace ms
+
+extern "C" {
+
+ms_status msb_create(const ms_params *p, const msb_voxel_spec *spec, int32_t n_robots, const int32_t *dims,
+                     const uint8_t *materials, const float *phase, const float *logk,
+                     const ms_allocator *alloc, void *stream, msb_batch **out)
+{
+    if (!out) return fail(MS_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!p || !spec || !dims || !materials) return fail(MS_ERR_ARG, "p, spec, dims and materials are required");
+    if (n_robots < 1) return fail(MS_ERR_ARG, "n_robots must be >= 1");
+    if (!(p->dt > 0.f) || !std::isfinite(p->dt)) return fail(MS_ERR_ARG, "dt must be positive and finite");
+    if (p->integrator != 0) return fail(MS_ERR_ARG, "the GPU path implements integrator 0 (symplectic Euler) only");
+    if (!(p->vel_damping >= 0.f && p->vel_damping < 1.f)) return fail(MS_ERR_ARG, "vel_damping must be in [0, 1)");
+    if (spec->n_materials < 1 || !spec->mat_k || !spec->mat_c || !spec->mat_amp) return fail(MS_ERR_ARG, "material table incomplete");
+    if (!(spec->voxel_edge > 0.f) || !(spec->voxel_mass > 0.f) || !std::isfinite(spec->freq)) return fail(MS_ERR_ARG, "voxel_edge and voxel_mass must be > 0");
+    for (int m = 0; m < spec->n_materials; ++m)
+        if (!(spec->mat_k[m] >= 0.f) || !(spec->mat_c[m] >= 0.f) || !std::isfinite(spec->mat_amp[m]) || !std::isfinite(spec->mat_k[m]) || !std::isfinite(spec->mat_c[m]))
+            return fail(MS_ERR_ARG, "material " + std::to_string(m) + " has a negative or non-finite entry");
+    if (alloc && (!alloc->alloc || !alloc->free)) return fail(MS_ERR_ARG, "allocator needs alloc and free");
+
+    msb_batch *b = new (std::nothrow) msb_batch();
+    if (!b) return fail(MS_ERR_OOM, "host allocation failed");
+    struct Guard { msb_batch *b; ~Guard() { if (b) { b->release(); delete b; } } } guard{b};
+    b->p = *p; b->spec = *spec; b->freq = spec->freq;
+    b->stream = (cudaStream_t)stream;
+    if (alloc) { b->alloc = *alloc; b->custom_alloc = true; }
+    b->n_robots = n_robots;
+
+    VoxelBuild vb;
+    ms_status st = build_voxels(spec, n_robots, dims, materials, phase, logk, false, vb);
+    if (st != MS_OK) return st;
+    b->h_robots = vb.robots;
+    b->h_st0 = vb.st0;
+    b->n_masses = vb.n_masses; b->n_records = vb.n_records; b->n_slices = vb.n_slices; b->max_n = vb.max_n;
+    b->n_slots = (int64_t)vb.nbr.size();
+    b->n_back = (int64_t)vb.bent.size();
+    std::vector<uint4> &h_slice = vb.slice;
+    std::vector<int32_t> &h_nbr = vb.nbr;
+    std::vector<float2> &h_kl = vb.kl, &h_ab = vb.ab;
+    std::vector<float> &h_c = vb.c;
+    std::vector<uint32_t> &h_b = vb.bent;
+
+    if ((st = bupload(b, &b->robots, b->h_robots.data(), n_robots)) != MS_OK) return st;
+    if ((st = bupload(b, &b->st, b->h_st0.data(), b->h_st0.size())) != MS_OK) return st;
+    if ((st = bupload<float4>(b, &b->st2, nullptr, b->h_st0.size())) != MS_OK) return st;
+    if ((st = bupload(b, &b->slice, h_slice.data(), h_slice.size())) != MS_OK) return st;
+    if ((st = bupload(b, &b->f_nbr, h_nbr.data(), h_nbr.size())) != MS_OK) return st;
+    if ((st = bupload(b, &b->f_kl, h_kl.data(), h_kl.size())) != MS_OK) return st;
+    if ((st = bupload(b, &b->f_ab, h_ab.data(), h_ab.size())) != MS_OK) return st;
+    if ((st = bupload(b, &b->f_c, h_c.data(), h_c.size())) != MS_OK) return st;
+    if ((st = bupload(b, &b->b_ent, h_b.data(), h_b.size())) != MS_OK) return st;
+    if ((st = bupload<float>(b, &b->travel, nullptr, n_robots)) != MS_OK) return st;
+    if ((st = bupload<int>(b, &b->err, nullptr, 1)) != MS_OK) return st;
+    if ((st = bupload<int>(b, &b->queue, nullptr, 1)) != MS_OK) return st;
+    if ((st = bupload<long long>(b, &b->counter, nullptr, 1)) != MS_OK) return st;
+    MSB_CUDA_TRY(cudaMemsetAsync(b->err, 0, sizeof(int), b->stream));
+    MSB_CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(long long), b->stream));
+    MSB_CUDA_TRY(cudaMemsetAsync(b->travel, 0, sizeof(float) * n_robots, b->stream));
+    MSB_CUDA_TRY(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    b->warp_mode.assign(n_robots, 0);
+    for (int r = 0; r < n_robots; ++r) b->warp_mode[r] = b->h_robots[r].n <= 64 ? 1 : 0;
+    build_items(b);
+    if ((st = upload_items(b)) != MS_OK) return st;
+    MSB_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    guard.b = nullptr;
+    *out = b;
+    return MS_OK;
+}
+
+ms_status msb_run(msb_batch *b, int32_t nsteps)
+{
+    if (!b) return fail(MS_ERR_ARG, "batch is NULL");
+    if (nsteps < 0) return fail(MS_ERR_ARG, "nsteps must be >= 0");
+    if (nsteps == 0) return MS_OK;
+    ms_status st = ensure_sc(b, nsteps);
+    if (st != MS_OK) return st;
+    auto it = b->graphs.find(nsteps);
+    if (it == b->graphs.end()) {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        MSB_CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+        st = enqueue_run(b, nsteps, b->cap_stream);
+        cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+        if (st != MS_OK) { if (g) cudaGraphDestroy(g); return st; }
+        if (e != cudaSuccess) return fail(MS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(MS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        it = b->graphs.emplace(nsteps, ge).first;
+    }
+    MSB_CUDA_TRY(cudaGraphLaunch(it->second, b->stream));
+    b->step_count += nsteps;
+    return MS_OK;
+}
+
+ms_status msb_run_loop(msb_batch *b, int32_t nsteps)
+{
+    if (!b) return fail(MS_ERR_ARG, "batch is NULL");
+    if (nsteps < 0) return fail(MS_ERR_ARG, "nsteps must be >= 0");
+    StepArgs a{};
+    a.f_nbr = b->f_nbr; a.f_kl = b->f_kl; a.f_c = b->f_c; a.f_ab = b->f_ab; a.b_ent = b->b_ent;
+    a.err = b->err; a.dt = b->p.dt; a.gx = b->p.g[0]; a.gy = b->p.g[1]; a.gz = b->p.g[2];
+    a.k_c = b->p.k_c; a.mu = b->p.mu; a.keep = 1.0f - b->p.vel_damping; a.contact = b->p.contact_on;
+    const double two_pi_f = 2.0 * M_PI * b->freq;
+    float4 *cur = b->st, *nxt = b->st2;
+    for (int n = 0; n < nsteps; ++n) {
+        const double t = (double)(b->step_count + n) * (double)b->p.dt;
+        a.s_n = (float)std::sin(two_pi_f * t);
+        a.c_n = (float)std::cos(two_pi_f * t);
+        for (int r = 0; r < b->n_robots; ++r) {
+            const RobotDev &R = b->h_robots[r];
+            a.N = R.n;
+            a.slice = b->slice + R.slice_base;
+            a.st = cur + 2 * R.mass_base;
+            a.sto = nxt + 2 * R.mass_base;
+            MSB_CUDA_TRY(launch_step(a, b->stream));
+        }
+        std::swap(cur, nxt);
+    }
+    if (cur != b->st)
+        MSB_CUDA_TRY(cudaMemcpyAsync(b->st, cur, sizeof(float4) * 2 * b->n_masses, cudaMemcpyDeviceToDevice, b->stream));
+    // keep the batched kernel's clock in step with this one
+    if (nsteps > 0) {
+        k_advance<<<1, 1, 0, b->stream>>>(b->counter, nsteps);
+        MSB_CUDA_TRY(cudaGetLastError());
+    }
+    k_com_travel<<<b->n_robots, 256, 0, b->stream>>>(b->robots, b->st, b->travel);
+    MSB_CUDA_TRY(cudaGetLastError());
+    b->step_count += nsteps;
+    return MS_OK;
+}
+
+ms_status msb_autotune(msb_batch *b, int32_t sample_steps, int32_t policy)
+{
+    if (!b) return fail(MS_ERR_ARG, "batch is NULL");
+    if (policy < 0 || policy > 2) return fail(MS_ERR_ARG, "policy must be 0, 1 or 2");
+    const size_t smem_limit = 200 * 1024;
+    auto warp_ok = [&](int n) { return n <= kWarpModeMax && (size_t)kWarpsPerCta * 3 * ((n + 31) / 32 * 32) * sizeof(float4) <= smem_limit; };
+    if (policy == 1) { std::fill(b->warp_mode.begin(), b->warp_mode.end(), 0); }
+    else if (policy == 2) { for (int r = 0; r < b->n_robots; ++r) b->warp_mode[r] = warp_ok(b->h_robots[r].n) ? 1 : 0; }
+    else {
+        if (sample_steps < 1) return fail(MS_ERR_ARG, "sample_steps must be >= 1");
+        // save the state: the timing runs advance the sampled robots
+        MSB_CUDA_TRY(cudaMemcpyAsync(b->st2, b->st, sizeof(float4) * 2 * b->n_masses, cudaMemcpyDeviceToDevice, b->stream));
+        ms_status st = ensure_sc(b, sample_steps);
+        if (st != MS_OK) return st;
+        // size buckets by mass count: (0,32], (32,64], (64,128], (128,256]
+        const int edges[] = {0, 32, 64, 128, 256};
+        cudaEvent_t e0, e1;
+        MSB_CUDA_TRY(cudaEventCreate(&e0));
+        MSB_CUDA_TRY(cudaEventCreate(&e1));
+        std::vector<uint8_t> choice(5, 0);
+        for (int bk = 1; bk < 5; ++bk) {
+            std::vector<int> members;
+            for (int r = 0; r < b->n_robots; ++r)
+                if (b->h_robots[r].n > edges[bk - 1] && b->h_robots[r].n <= edges[bk] && warp_ok(b->h_robots[r].n)) members.push_back(r);
+            if (members.empty()) continue;
+            if (members.size() > 256) members.resize(256);
+            float t_mode[2] = {0.f, 0.f};
+            for (int mode = 0; mode < 2; ++mode) {
+                // items for the sample only
+                if (mode == 0) set_items(b, members, {});
+                else set_items(b, {}, members);
+                if ((st = upload_items(b)) != MS_OK) return st;
+                for (int rep = 0; rep < 2; ++rep) {           // first run warms up
+                    MSB_CUDA_TRY(cudaEventRecord(e0, b->stream));
+                    if ((st = enqueue_run(b, sample_steps, b->stream)) != MS_OK) return st;
+                    MSB_CUDA_TRY(cudaEventRecord(e1, b->stream));
+                    MSB_CUDA_TRY(cudaEventSynchronize(e1));
+                }
+                MSB_CUDA_TRY(cudaEventElapsedTime(&t_mode[mode], e0, e1));
+            }
+            choice[bk] = t_mode[1] < t_mode[0] ? 1 : 0;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        for (int r = 0; r < b->n_robots; ++r) {
+            const int n = b->h_robots[r].n;
+            int bk = 0;
+            for (int q = 1; q < 5; ++q) if (n > edges[q - 1] && n <= edges[q]) bk = q;
+            b->warp_mode[r] = (bk > 0 && warp_ok(n)) ? choice[bk] : 0;
+        }
+        // restore the state, the clock and the travel record
+        MSB_CUDA_TRY(cudaMemcpyAsync(b->st, b->st2, sizeof(float4) * 2 * b->n_masses, cudaMemcpyDeviceToDevice, b->stream));
+        k_com_travel<<<b->n_robots, 256, 0, b->stream>>>(b->robots, b->st, b->travel);
+        MSB_CUDA_TRY(cudaGetLastError());
+        const long long sc_now = b->step_count;
+        MSB_CUDA_TRY(cudaMemcpyAsync(b->counter, &sc_now, sizeof(long long), cudaMemcpyHostToDevice, b->stream));
+        MSB_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    }
+    build_items(b);
+    return upload_items(b);
+}
+
+ms_status msb_com_travel(msb_batch *b, float *out, int32_t on_device)
+{
+    if (!b || !out) return fail(MS_ERR_ARG, "batch and out are required");
+    if (on_device) {
+        MSB_CUDA_TRY(cudaMemcpyAsync(out, b->travel, sizeof(float) * b->n_robots, cudaMemcpyDeviceToDevice, b->stream));
+        return MS_OK;
+    }
+    MSB_CUDA_TRY(cudaMemcpyAsync(out, b->travel, sizeof(float) * b->n_robots, cudaMemcpyDeviceToHost, b->stream));
+    MSB_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    int flag = 0;
+    MSB_CUDA_TRY(cudaMemcpy(&flag, b->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) return fail(MS_ERR_NONFINITE, "a robot reached a non-finite position or velocity");
+    return MS_OK;
+}
+
+ms_status msb_robot_info(const msb_batch *b, int32_t robot, int32_t *n_masses, int64_t *first_mass)
+{
+    if (!b || robot < 0 || robot >= b->n_robots) return fail(MS_ERR_ARG, "bad batch or robot index");
+    if (n_masses) *n_masses = b->h_robots[robot].n;
+    if (first_mass) *first_mass = b->h_robots[robot].mass_base;
+    return MS_OK;
+}
+
+ms_status msb_get_state(msb_batch *b, float *x, float *v)
+{
+    if (!b) return fail(MS_ERR_ARG, "batch is NULL");
+    std::vector<float4> h(2 * (size_t)b->n_masses);
+    MSB_CUDA_TRY(cudaMemcpyAsync(h.data(), b->st, sizeof(float4) * h.size(), cudaMemcpyDeviceToHost, b->stream));
+    MSB_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    for (int64_t i = 0; i < b->n_masses; ++i) {
+        if (x) { x[3 * i] = h[2 * i].x; x[3 * i + 1] = h[2 * i].y; x[3 * i + 2] = h[2 * i].z; }
+        if (v) { v[3 * i] = h[2 * i + 1].x; v[3 * i + 1] = h[2 * i + 1].y; v[3 * i + 2] = h[2 * i + 1].z; }
+    }
+    return MS_OK;
+}
+
+ms_status msb_reset(msb_batch *b)
+{
+    if (!b) return fail(MS_ERR_ARG, "batch is NULL");
+    MSB_CUDA_TRY(cudaMemcpyAsync(b->st, b->h_st0.data(), sizeof(float4) * b->h_st0.size(), cudaMemcpyHostToDevice, b->stream));
+    MSB_CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(long long), b->stream));
+    MSB_CUDA_TRY(cudaMemsetAsync(b->travel, 0, sizeof(float) * b->n_robots, b->stream));
+    MSB_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    b->step_count = 0;
+    return MS_OK;
+}
+
+ms_status msb_get_info(const msb_batch *b, msb_info_t *out)
+{
+    if (!b || !out) return fail(MS_ERR_ARG, "batch or out is NULL");
+    out->n_robots = b->n_robots; out->n_masses = b->n_masses; out->n_records = b->n_records;
+    out->max_robot_masses = b->max_n;
+    int nb = 0, nw = 0;
+    for (int r = 0; r < b->n_robots; ++r) (b->warp_mode[r] ? nw : nb)++;
+    out->n_block_items = nb; out->n_warp_items = nw;
+    out->device_bytes = b->device_bytes; out->step_count = b->step_count;
+    return MS_OK;
+}
+
+ms_status msb_destroy(msb_batch *b)
+{
+    if (!b) return MS_OK;
+    b->release();
+    delete b;
+    return MS_OK;
+}
+
+}  // extern "C"

@@ -4,20 +4,28 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
+#include "cronos_ms.h"
+
 namespace ms {
+
+// Records msg as the calling thread's last error and returns st (ms_api.cu).
+ms_status fail(ms_status st, const std::string &msg);
 
 // Device layout of one simulation (all pointers are device memory).
 //
-// Masses are stored in the library's internal order as two float4 streams,
-// double buffered (the step reads buffer `cur` and writes `cur ^ 1`):
-//   x4[i] = (x, y, z, w)   w = 1/m for a free mass, -1 for an anchored mass
-//   v4[i] = (vx, vy, vz, 0)
+// Masses are stored in the library's internal order, double buffered (the
+// step reads buffer `cur` and writes `cur ^ 1`), one 32-byte sector per mass
+// so that a neighbour's whole state is one sector:
+//   st[2i]   = (x, y, z, w)   w = 1/m for a free mass, -1 for an anchored mass
+//   st[2i+1] = (vx, vy, vz, 0)
 //
 // Springs are stored once, in the row of their lower-indexed endpoint (the
 // "owner"), in a sliced-ELL layout with slices of 32 masses (one warp):
 //   record (owner o, slot s) lives at  slice[o/32].fwd_off + 32*s + o%32
-// with arrays f_nbr (partner index, -1 = padding), f_k, f_L0 and optionally
-// f_c (per-record damping) and f_al/f_be (actuation coefficients).
+// with arrays f_nbr (partner index, -1 = padding), f_kl = (k, L0) and
+// optionally f_c (per-record damping) and f_ab = (alpha, beta) (actuation).
 // The partner reaches the same record through a back reference stored in
 // its own row, also sliced-ELL:
 //   b_ent[slice[j/32].bwd_off + 32*t + j%32] = o | (s << 27)  (0xffffffff = padding)
@@ -34,20 +42,37 @@ constexpr uint32_t kOwnerMask = (1u << kOwnerBits) - 1u;
 constexpr uint32_t kBackPad = 0xffffffffu;
 constexpr int kMaxFwdDegree = 31;
 
+// Kernels of the single-system step.
+constexpr int kKernelGather = 1;   // one thread per mass, sliced-ELL rows + back references
+constexpr int kKernelTiled = 2;    // CTA per tile of masses, state + halo in shared memory
+constexpr int kTileMasses = 512;   // masses per tile (= threads per CTA)
+constexpr int kTileMaxLocal = 2048; // tile members + halo that fit the CTA's shared memory (24 B each)
+constexpr int kTileGroup = 2;      // spring slots per pipeline stage (one bulk copy per array)
+constexpr int kTileStages = 2;     // pipeline depth
+constexpr int kErrNonFinite = 1;   // bits of the device error flag
+constexpr int kErrTimeout = 2;
+
 struct StepArgs {
-    const float4 *x;     // state at t_n
-    const float4 *v;
-    float4 *xo;          // state at t_{n+1}
-    float4 *vo;
+    const float4 *st;    // state at t_n (2 float4 per mass)
+    float4 *sto;         // state at t_{n+1}
     const float4 *fext;  // or nullptr
     const uint4 *slice;
     const int32_t *f_nbr;
-    const float *f_k;
-    const float *f_L0;
+    const float2 *f_kl;  // (k, L0)
     const float *f_c;    // or nullptr (then c_uniform)
-    const float *f_al;   // or nullptr (passive)
-    const float *f_be;
+    const float2 *f_ab;  // (alpha, beta), or nullptr (passive)
     const uint32_t *b_ent;
+    // tiled layout: tiles[2t] = (first mass, members, halo offset, halo count),
+    // tiles[2t+1] = (first record slot, slots per member, 0, 0); slot s of
+    // member m of tile t is record rec + s*kTileMasses + m (slot-major, so
+    // a group of slots for the whole tile is one contiguous range);
+    // t_nbr = tile-local partner index (0xffff = padding)
+    const uint16_t *t_nbr;
+    const int4 *tiles;
+    const int32_t *halo;
+    int n_tiles;
+    int tile_local;      // max members + halo over the tiles (shared-memory entries)
+    int tiled;
     int *err;            // non-finite flag (sticky)
     int N;
     float c_uniform;
@@ -59,9 +84,9 @@ struct StepArgs {
 
 // Launchers (ms_step.cu).
 cudaError_t launch_step(const StepArgs &a, cudaStream_t st);
-cudaError_t launch_gather_state(const float4 *x4, const float4 *v4, const int32_t *perm, int N,
-                                float *x_out, float *v_out, cudaStream_t st);
-cudaError_t launch_scatter_state(float4 *x4, float4 *v4, const int32_t *perm, int N,
-                                 const float *x_in, const float *v_in, cudaStream_t st);
+cudaError_t launch_gather_state(const float4 *st, const int32_t *perm, int N,
+                                float *x_out, float *v_out, cudaStream_t stream);
+cudaError_t launch_scatter_state(float4 *st, const int32_t *perm, int N,
+                                 const float *x_in, const float *v_in, cudaStream_t stream);
 
 }  // namespace ms

@@ -24,20 +24,71 @@
 
 namespace ms {
 
+// Hooke term of eq. 2 plus the axial dashpot, added to (fx, fy, fz) for the
+// mass at xi with partner xj (d = xj - xi):
+//   f = (k (l - L) + c (vj - vi).d / l) d / l.
+// One reciprocal square root serves both l and the unit vector.  The result
+// is an exact negation when the endpoints are swapped, and a spring of zero
+// length (or a padding slot pointing at the mass itself) adds nothing.
 __device__ __forceinline__ void spring_term(const float4 xi, const float4 vi, const float4 xj,
                                             const float4 vj, float k, float L, float c,
                                             float &fx, float &fy, float &fz)
 {
     const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-    const float l2 = dx * dx + dy * dy + dz * dz;
-    if (l2 > 0.0f) {                       // a zero-length spring exerts no force
-        const float l = sqrtf(l2);
-        const float il = 1.0f / l;
-        const float ux = dx * il, uy = dy * il, uz = dz * il;
-        const float rv = (vj.x - vi.x) * ux + (vj.y - vi.y) * uy + (vj.z - vi.z) * uz;
-        const float fs = k * (l - L) + c * rv;
-        fx += fs * ux; fy += fs * uy; fz += fs * uz;
+    const float l2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float il = rsqrtf(l2);
+    const float l = l2 * il;
+    const float rv = fmaf(vj.x - vi.x, dx, fmaf(vj.y - vi.y, dy, (vj.z - vi.z) * dz)) * il;
+    float fs = fmaf(k, l - L, c * rv) * il;     // force magnitude / l
+    fs = (l2 > 0.0f) ? fs : 0.0f;
+    fx = fmaf(fs, dx, fx); fy = fmaf(fs, dy, fy); fz = fmaf(fs, dz, fz);
+}
+
+// The same term with the partner's state packed as (x, y, z, vx), (vy, vz).
+__device__ __forceinline__ void spring_term_packed(const float4 xi, const float4 vi, const float4 pa,
+                                                   const float2 pb, float k, float L, float c,
+                                                   float &fx, float &fy, float &fz)
+{
+    const float dx = pa.x - xi.x, dy = pa.y - xi.y, dz = pa.z - xi.z;
+    const float l2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float il = rsqrtf(l2);
+    const float l = l2 * il;
+    const float rv = fmaf(pa.w - vi.x, dx, fmaf(pb.x - vi.y, dy, (pb.y - vi.z) * dz)) * il;
+    float fs = fmaf(k, l - L, c * rv) * il;
+    fs = (l2 > 0.0f) ? fs : 0.0f;
+    fx = fmaf(fs, dx, fx); fy = fmaf(fs, dy, fy); fz = fmaf(fs, dz, fz);
+}
+
+// Gravity, external force, ground contact (penalty normal force, Coulomb
+// impulse clamp), global damping and the symplectic Euler update of mass i.
+template <bool HAS_FEXT>
+__device__ __forceinline__ void integrate_mass(const StepArgs &a, int i, const float4 xi, const float4 vi,
+                                               float fx, float fy, float fz, float4 &xn, float4 &vn)
+{
+    xn = xi;
+    vn = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float w = xi.w;                  // 1/m, or -1 for an anchored mass
+    if (w < 0.0f) return;
+    if (HAS_FEXT) {
+        const float4 fe = __ldg(&a.fext[i]);
+        fx += fe.x; fy += fe.y; fz += fe.z;
     }
+    const bool pen = a.contact && xi.z < 0.0f;
+    float Fn = 0.f;
+    if (pen) { Fn = -a.k_c * xi.z; fz += Fn; }
+    float vx = vi.x + a.dt * (fx * w + a.gx);
+    float vy = vi.y + a.dt * (fy * w + a.gy);
+    float vz = vi.z + a.dt * (fz * w + a.gz);
+    if (pen && a.mu > 0.0f) {              // Coulomb impulse clamp on (vx, vy)
+        const float D = a.mu * Fn * a.dt * w;
+        const float vt = sqrtf(vx * vx + vy * vy);
+        if (vt <= D) { vx = 0.f; vy = 0.f; }
+        else { const float sc = 1.0f - D / vt; vx *= sc; vy *= sc; }
+    }
+    vx *= a.keep; vy *= a.keep; vz *= a.keep;
+    vn = make_float4(vx, vy, vz, 0.f);
+    xn = make_float4(xi.x + a.dt * vx, xi.y + a.dt * vy, xi.z + a.dt * vz, w);
+    if (!isfinite(xn.x + xn.y + xn.z + vx + vy + vz)) atomicOr(a.err, kErrNonFinite);
 }
 
 template <bool HAS_C, bool HAS_ACT, bool HAS_FEXT>
@@ -47,8 +98,8 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a)
     if (i >= a.N) return;
     const unsigned lane = (unsigned)i & 31u;
     const uint4 meta = __ldg(&a.slice[i >> 5]);
-    const float4 xi = __ldg(&a.x[i]);
-    const float4 vi = __ldg(&a.v[i]);
+    const float4 xi = __ldg(&a.st[2 * i]);
+    const float4 vi = __ldg(&a.st[2 * i + 1]);
     float fx = 0.f, fy = 0.f, fz = 0.f;
 
     // springs owned by this mass
@@ -58,11 +109,11 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a)
     for (unsigned s = 0; s < flen; ++s, r += 32u) {
         int j = __ldg(&a.f_nbr[r]);
         j = (j < 0) ? i : j;               // padding slot: self, zero length
-        const float k = __ldg(&a.f_k[r]);
-        float L = __ldg(&a.f_L0[r]);
+        const float2 kl = __ldg(&a.f_kl[r]);
+        float L = kl.y;
         const float c = HAS_C ? __ldg(&a.f_c[r]) : a.c_uniform;
-        if (HAS_ACT) L = L * (1.0f + (__ldg(&a.f_al[r]) * a.s_n + __ldg(&a.f_be[r]) * a.c_n));
-        spring_term(xi, vi, __ldg(&a.x[j]), __ldg(&a.v[j]), k, L, c, fx, fy, fz);
+        if (HAS_ACT) { const float2 ab = __ldg(&a.f_ab[r]); L = L * (1.0f + (ab.x * a.s_n + ab.y * a.c_n)); }
+        spring_term(xi, vi, __ldg(&a.st[2 * j]), __ldg(&a.st[2 * j + 1]), kl.x, L, c, fx, fy, fz);
     }
     // springs owned by partners, reached through back references
     unsigned q = meta.y + lane;
@@ -75,47 +126,228 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a)
             o = (int)(e & kOwnerMask);
             rr = __ldg(&a.slice[o >> 5].x) + (e >> kOwnerBits) * 32u + ((unsigned)o & 31u);
         }
-        const float k = __ldg(&a.f_k[rr]);
-        float L = __ldg(&a.f_L0[rr]);
+        const float2 kl = __ldg(&a.f_kl[rr]);
+        float L = kl.y;
         const float c = HAS_C ? __ldg(&a.f_c[rr]) : a.c_uniform;
-        if (HAS_ACT) L = L * (1.0f + (__ldg(&a.f_al[rr]) * a.s_n + __ldg(&a.f_be[rr]) * a.c_n));
-        spring_term(xi, vi, __ldg(&a.x[o]), __ldg(&a.v[o]), k, L, c, fx, fy, fz);
+        if (HAS_ACT) { const float2 ab = __ldg(&a.f_ab[rr]); L = L * (1.0f + (ab.x * a.s_n + ab.y * a.c_n)); }
+        spring_term(xi, vi, __ldg(&a.st[2 * o]), __ldg(&a.st[2 * o + 1]), kl.x, L, c, fx, fy, fz);
     }
 
-    float4 xn = xi, vn = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float w = xi.w;                  // 1/m, or -1 for an anchored mass
-    if (w >= 0.0f) {
-        if (HAS_FEXT) {
-            const float4 fe = __ldg(&a.fext[i]);
-            fx += fe.x; fy += fe.y; fz += fe.z;
-        }
-        const bool pen = a.contact && xi.z < 0.0f;
-        float Fn = 0.f;
-        if (pen) { Fn = -a.k_c * xi.z; fz += Fn; }
-        float vx = vi.x + a.dt * (fx * w + a.gx);
-        float vy = vi.y + a.dt * (fy * w + a.gy);
-        float vz = vi.z + a.dt * (fz * w + a.gz);
-        if (pen && a.mu > 0.0f) {          // Coulomb impulse clamp on (vx, vy)
-            const float D = a.mu * Fn * a.dt * w;
-            const float vt = sqrtf(vx * vx + vy * vy);
-            if (vt <= D) { vx = 0.f; vy = 0.f; }
-            else { const float sc = 1.0f - D / vt; vx *= sc; vy *= sc; }
-        }
-        vx *= a.keep; vy *= a.keep; vz *= a.keep;
-        vn = make_float4(vx, vy, vz, 0.f);
-        xn = make_float4(xi.x + a.dt * vx, xi.y + a.dt * vy, xi.z + a.dt * vz, w);
-        if (!isfinite(xn.x + xn.y + xn.z + vx + vy + vz)) atomicOr(a.err, 1);
+    float4 xn, vn;
+    integrate_mass<HAS_FEXT>(a, i, xi, vi, fx, fy, fz, xn, vn);
+    a.sto[2 * i] = xn;
+    a.sto[2 * i + 1] = vn;
+}
+
+// ---------------------------------------------------------------------------
+// Tiled variant: one CTA per tile of kTileMasses consecutive masses (a
+// compact block in Morton order).
+//   * The CTA stages the state of its members and of their halo (every
+//     outside partner, listed per tile) in shared memory; every partner read
+//     is then a shared-memory read.
+//   * Each mass's row holds all of its springs, with the partner as a 16-bit
+//     tile-local index.  Rows are slot-major over the tile, so kTileGroup
+//     slots of the whole tile are one contiguous range per array; they are
+//     streamed into shared memory by TMA bulk copies (cp.async.bulk) through
+//     a kTileStages-deep mbarrier pipeline, so DRAM stays busy while the
+//     warps compute.  One elected thread issues the copies.
+//   * Every wait on an mbarrier is bounded: after kMaxSpins polls the CTA
+//     records kErrTimeout in the error flag and stops using the pipeline.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr unsigned kMaxSpins = 1u << 26;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+// global -> shared bulk copy completing on an mbarrier (sizes and both
+// addresses are multiples of 16 bytes by construction of the layout)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// bounded wait: true when the phase completed, false after kMaxSpins polls
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    for (unsigned n = 0; n < kMaxSpins; ++n)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+template <bool HAS_C, bool HAS_ACT>
+struct StageLayout {
+    static constexpr uint32_t nbr = kTileGroup * kTileMasses * 2;
+    static constexpr uint32_t kl = kTileGroup * kTileMasses * 8;
+    static constexpr uint32_t c = HAS_C ? kTileGroup * kTileMasses * 4 : 0;
+    static constexpr uint32_t ab = HAS_ACT ? kTileGroup * kTileMasses * 8 : 0;
+    static constexpr uint32_t bytes = nbr + kl + c + ab;
+};
+
+}  // namespace
+
+template <bool HAS_C, bool HAS_ACT, bool HAS_FEXT>
+__global__ void __launch_bounds__(kTileMasses) k_step_tiled(const StepArgs a)
+{
+    using SL = StageLayout<HAS_C, HAS_ACT>;
+    extern __shared__ __align__(128) unsigned char dyn[];
+    __shared__ __align__(8) uint64_t bar[kTileStages];
+    __shared__ int give_up;
+    const int tid = threadIdx.x;
+    const int4 T = __ldg(&a.tiles[2 * blockIdx.x]);
+    const int4 R = __ldg(&a.tiles[2 * blockIdx.x + 1]);
+    const int base = T.x, nb = T.y, hoff = T.z, nh = T.w;
+    const unsigned rec0 = (unsigned)R.x, nslots = (unsigned)R.y;
+    const unsigned ngroups = (nslots + kTileGroup - 1) / kTileGroup;
+    // shared partner state, packed: (x, y, z, vx) and (vy, vz) per tile-local mass
+    float4 *spa = reinterpret_cast<float4 *>(dyn);
+    float2 *spb = reinterpret_cast<float2 *>(spa + a.tile_local);
+    unsigned char *stage0 = dyn + (((size_t)a.tile_local * 24 + 127) & ~(size_t)127);
+
+    auto stage_ptr = [&](unsigned p) { return stage0 + (size_t)p * SL::bytes; };
+    auto issue = [&](unsigned g) {          // one thread: bulk-copy slot group g into its stage
+        const unsigned p = g % kTileStages;
+        const unsigned s0 = g * kTileGroup;
+        const unsigned ns = min((unsigned)kTileGroup, nslots - s0);
+        const size_t first = (size_t)rec0 + (size_t)s0 * kTileMasses;
+        const uint32_t cnt = ns * kTileMasses;
+        unsigned char *st = stage_ptr(p);
+        mbar_expect_tx(&bar[p], cnt * (2u + 8u + (HAS_C ? 4u : 0u) + (HAS_ACT ? 8u : 0u)));
+        bulk_g2s(st, a.t_nbr + first, cnt * 2u, &bar[p]);
+        bulk_g2s(st + SL::nbr, a.f_kl + first, cnt * 8u, &bar[p]);
+        if (HAS_C) bulk_g2s(st + SL::nbr + SL::kl, a.f_c + first, cnt * 4u, &bar[p]);
+        if (HAS_ACT) bulk_g2s(st + SL::nbr + SL::kl + SL::c, a.f_ab + first, cnt * 8u, &bar[p]);
+    };
+
+    if (tid == 0) {
+        give_up = 0;
+        for (int p = 0; p < kTileStages; ++p) mbar_init(&bar[p], 1);
+        mbar_fence_init();
     }
-    a.xo[i] = xn;
-    a.vo[i] = vn;
+    __syncthreads();
+    if (tid == 0)
+        for (unsigned g = 0; g < min(ngroups, (unsigned)kTileStages); ++g) issue(g);
+
+    // stage the state of the members and the halo while the first groups stream in
+    const bool active = tid < nb;
+    float4 xi = make_float4(0.f, 0.f, 0.f, 0.f), vi = xi;
+    if (active) {
+        xi = __ldg(&a.st[2 * (base + tid)]);
+        vi = __ldg(&a.st[2 * (base + tid) + 1]);
+        spa[tid] = make_float4(xi.x, xi.y, xi.z, vi.x);
+        spb[tid] = make_float2(vi.y, vi.z);
+    }
+    for (int h = tid; h < nh; h += kTileMasses) {
+        const int g = __ldg(&a.halo[hoff + h]);
+        const float4 hx = __ldg(&a.st[2 * g]), hv = __ldg(&a.st[2 * g + 1]);
+        spa[nb + h] = make_float4(hx.x, hx.y, hx.z, hv.x);
+        spb[nb + h] = make_float2(hv.y, hv.z);
+    }
+    __syncthreads();
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    for (unsigned g = 0; g < ngroups; ++g) {
+        const unsigned p = g % kTileStages;
+        if (!mbar_wait(&bar[p], (g / kTileStages) & 1u)) give_up = 1;
+        const unsigned char *st = stage_ptr(p);
+        const uint16_t *snbr = reinterpret_cast<const uint16_t *>(st);
+        const float2 *skl = reinterpret_cast<const float2 *>(st + SL::nbr);
+        const float *sc = reinterpret_cast<const float *>(st + SL::nbr + SL::kl);
+        const float2 *sab = reinterpret_cast<const float2 *>(st + SL::nbr + SL::kl + SL::c);
+        const unsigned ns = min((unsigned)kTileGroup, nslots - g * kTileGroup);
+        if (active) {
+#pragma unroll
+            for (unsigned u = 0; u < (unsigned)kTileGroup; ++u) {
+                if (u < ns) {
+                    const unsigned e = u * kTileMasses + tid;
+                    unsigned j = snbr[e];
+                    j = (j == 0xffffu) ? (unsigned)tid : j;
+                    const float2 kl = skl[e];
+                    float L = kl.y;
+                    const float c = HAS_C ? sc[e] : a.c_uniform;
+                    if (HAS_ACT) { const float2 ab = sab[e]; L = L * (1.0f + (ab.x * a.s_n + ab.y * a.c_n)); }
+                    spring_term_packed(xi, vi, spa[j], spb[j], kl.x, L, c, fx, fy, fz);
+                }
+            }
+        }
+        __syncthreads();                    // stage p fully consumed
+        if (give_up) break;
+        if (tid == 0 && g + kTileStages < ngroups) {
+            fence_proxy_async();
+            issue(g + kTileStages);
+        }
+    }
+    if (give_up) {
+        // a copy never completed: flag it, and give in-flight copies a bounded
+        // chance to land before the CTA's shared memory is released
+        if (tid == 0) {
+            atomicOr(a.err, kErrTimeout);
+            for (unsigned g = 0; g < ngroups && g < (unsigned)kTileStages; ++g) mbar_wait(&bar[g], 0);
+        }
+        return;
+    }
+    if (!active) return;
+    const int i = base + tid;
+    float4 xn, vn;
+    integrate_mass<HAS_FEXT>(a, i, xi, vi, fx, fy, fz, xn, vn);
+    a.sto[2 * i] = xn;
+    a.sto[2 * i + 1] = vn;
+}
+
+size_t tiled_smem_bytes(int tile_local, bool has_c, bool has_act)
+{
+    const size_t stage = (size_t)kTileGroup * kTileMasses * (2 + 8 + (has_c ? 4 : 0) + (has_act ? 8 : 0));
+    return ((((size_t)tile_local * 24 + 127) & ~(size_t)127)) + (size_t)kTileStages * stage;
 }
 
 cudaError_t launch_step(const StepArgs &a, cudaStream_t st)
 {
     if (a.N <= 0) return cudaSuccess;
+    const bool hc = a.f_c != nullptr, ha = a.f_ab != nullptr, hf = a.fext != nullptr;
+    if (a.tiled) {
+        const size_t smem = tiled_smem_bytes(a.tile_local, hc, ha);
+        const int grid = a.n_tiles;
+#define MS_LAUNCH_T(C, A, F)                                                                        \
+    do {                                                                                            \
+        cudaError_t e_ = cudaFuncSetAttribute(k_step_tiled<C, A, F>,                                \
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e_ != cudaSuccess) return e_;                                                           \
+        k_step_tiled<C, A, F><<<grid, kTileMasses, smem, st>>>(a);                                  \
+    } while (0)
+        if (hc) {
+            if (ha) { if (hf) MS_LAUNCH_T(true, true, true); else MS_LAUNCH_T(true, true, false); }
+            else    { if (hf) MS_LAUNCH_T(true, false, true); else MS_LAUNCH_T(true, false, false); }
+        } else {
+            if (ha) { if (hf) MS_LAUNCH_T(false, true, true); else MS_LAUNCH_T(false, true, false); }
+            else    { if (hf) MS_LAUNCH_T(false, false, true); else MS_LAUNCH_T(false, false, false); }
+        }
+#undef MS_LAUNCH_T
+        return cudaGetLastError();
+    }
     const int bs = 256;
     const int grid = (a.N + bs - 1) / bs;
-    const bool hc = a.f_c != nullptr, ha = a.f_al != nullptr, hf = a.fext != nullptr;
 #define MS_LAUNCH(C, A, F) k_step<C, A, F><<<grid, bs, 0, st>>>(a)
     if (hc) {
         if (ha) { if (hf) MS_LAUNCH(true, true, true); else MS_LAUNCH(true, true, false); }
@@ -128,45 +360,43 @@ cudaError_t launch_step(const StepArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-__global__ void k_gather_state(const float4 *__restrict__ x4, const float4 *__restrict__ v4,
-                               const int32_t *__restrict__ perm, int N, float *__restrict__ xo,
-                               float *__restrict__ vo)
+__global__ void k_gather_state(const float4 *__restrict__ st, const int32_t *__restrict__ perm, int N,
+                               float *__restrict__ xo, float *__restrict__ vo)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int c = perm ? perm[i] : i;
-    if (xo) { const float4 p = x4[i]; xo[3 * c] = p.x; xo[3 * c + 1] = p.y; xo[3 * c + 2] = p.z; }
-    if (vo) { const float4 p = v4[i]; vo[3 * c] = p.x; vo[3 * c + 1] = p.y; vo[3 * c + 2] = p.z; }
+    if (xo) { const float4 p = st[2 * i]; xo[3 * c] = p.x; xo[3 * c + 1] = p.y; xo[3 * c + 2] = p.z; }
+    if (vo) { const float4 p = st[2 * i + 1]; vo[3 * c] = p.x; vo[3 * c + 1] = p.y; vo[3 * c + 2] = p.z; }
 }
 
-__global__ void k_scatter_state(float4 *__restrict__ x4, float4 *__restrict__ v4,
-                                const int32_t *__restrict__ perm, int N, const float *__restrict__ xi,
-                                const float *__restrict__ vi)
+__global__ void k_scatter_state(float4 *__restrict__ st, const int32_t *__restrict__ perm, int N,
+                                const float *__restrict__ xi, const float *__restrict__ vi)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int c = perm ? perm[i] : i;
-    const float w = x4[i].w;
-    if (xi) x4[i] = make_float4(xi[3 * c], xi[3 * c + 1], xi[3 * c + 2], w);
+    const float w = st[2 * i].w;
+    if (xi) st[2 * i] = make_float4(xi[3 * c], xi[3 * c + 1], xi[3 * c + 2], w);
     if (vi) {
-        if (w < 0.0f) v4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        else v4[i] = make_float4(vi[3 * c], vi[3 * c + 1], vi[3 * c + 2], 0.f);
+        if (w < 0.0f) st[2 * i + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        else st[2 * i + 1] = make_float4(vi[3 * c], vi[3 * c + 1], vi[3 * c + 2], 0.f);
     }
 }
 
-cudaError_t launch_gather_state(const float4 *x4, const float4 *v4, const int32_t *perm, int N,
-                                float *x_out, float *v_out, cudaStream_t st)
+cudaError_t launch_gather_state(const float4 *st, const int32_t *perm, int N,
+                                float *x_out, float *v_out, cudaStream_t stream)
 {
     if (N <= 0) return cudaSuccess;
-    k_gather_state<<<(N + 255) / 256, 256, 0, st>>>(x4, v4, perm, N, x_out, v_out);
+    k_gather_state<<<(N + 255) / 256, 256, 0, stream>>>(st, perm, N, x_out, v_out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter_state(float4 *x4, float4 *v4, const int32_t *perm, int N,
-                                 const float *x_in, const float *v_in, cudaStream_t st)
+cudaError_t launch_scatter_state(float4 *st, const int32_t *perm, int N,
+                                 const float *x_in, const float *v_in, cudaStream_t stream)
 {
     if (N <= 0) return cudaSuccess;
-    k_scatter_state<<<(N + 255) / 256, 256, 0, st>>>(x4, v4, perm, N, x_in, v_in);
+    k_scatter_state<<<(N + 255) / 256, 256, 0, stream>>>(st, perm, N, x_in, v_in);
     return cudaGetLastError();
 }
 

@@ -17,7 +17,13 @@ from ._lib import MsAllocator, MsInfo, MsParams, check
 __all__ = ["Sim", "make_params", "torch_allocator"]
 
 
-def make_params(params: dict, reorder: bool = False, strict_stability: bool = False) -> MsParams:
+ORDERS = {None: 0, False: 0, "auto": 0, True: 1, "morton": 1, "caller": 2}
+KERNELS = {None: 0, "auto": 0, "gather": 1, "tiled": 2}
+
+
+def make_params(params: dict, reorder=None, strict_stability: bool = False, kernel=None) -> MsParams:
+    """reorder: None/False = library default, True/"morton", or "caller";
+    kernel: None/"auto", "gather" or "tiled"."""
     p = MsParams()
     p.dt = float(params["dt"])
     for a in range(3):
@@ -28,7 +34,8 @@ def make_params(params: dict, reorder: bool = False, strict_stability: bool = Fa
     p.contact_on = 1 if params.get("contact", False) else 0
     p.integrator = 0
     p.strict_stability = 1 if strict_stability else 0
-    p.reorder = 1 if reorder else 0
+    p.reorder = ORDERS[reorder]
+    p.kernel = KERNELS[kernel]
     return p
 
 
@@ -88,8 +95,8 @@ class Sim:
     c may be a scalar (uniform damping).  params: dt, g, k_c, mu, vel_damping, contact.
     """
 
-    def __init__(self, system: dict, params: dict, reorder: bool = False, stream=None,
-                 use_torch_allocator: bool = True, strict_stability: bool = False):
+    def __init__(self, system: dict, params: dict, reorder=None, stream=None,
+                 use_torch_allocator: bool = True, strict_stability: bool = False, kernel=None):
         lib = _lib.load()
         self._lib = lib
         x = _f32(system["x"], (-1, 3)); N = x.shape[0]
@@ -110,7 +117,7 @@ class Sim:
         L0 = system.get("L0")
         L0 = None if L0 is None else _f32(L0, (S,))
         self.N, self.S = N, S
-        self._params = make_params(params, reorder, strict_stability)
+        self._params = make_params(params, reorder, strict_stability, kernel)
         self._alloc = torch_allocator() if use_torch_allocator else None
         self.stream = _stream_handle(stream)
         handle = C.c_void_p()

@@ -50,10 +50,11 @@ def test_binding_names_match_header():
         assert n in declared, f"binding declares {n}, header does not"
 
 
-def _create(lib, N=2, x=None, mass=None, ij=None, k=None, dt=1e-3, strict=0, kc=0.0):
+def _create(lib, N=2, x=None, mass=None, ij=None, k=None, dt=1e-3, strict=0, kc=0.0, kernel=0):
     from paper_2207_09334_gb300._lib import MsParams
     p = MsParams(); p.dt = dt; p.g[2] = -9.81; p.k_c = kc; p.contact_on = 1 if kc else 0
     p.strict_stability = strict
+    p.kernel = kernel
     x = np.array(x if x is not None else [[0, 0, 0], [1, 0, 0]], np.float32)
     v = np.zeros_like(x)
     m = np.array(mass if mass is not None else [1.0] * len(x), np.float32)
@@ -85,11 +86,25 @@ def test_create_rejects_unstable_in_strict_mode(lib):
     assert "stability" in lib.ms_last_error().decode()
 
 
-def test_create_rejects_too_many_partners(lib):
-    # mass 0 owns 40 distinct partners
+def test_gather_kernel_rejects_too_many_partners(lib):
+    # mass 0 owns 40 distinct partners: beyond the gather layout's 31
     x = [[0, 0, 0]] + [[1 + i, 0, 0] for i in range(40)]
-    rc, _ = _create(lib, x=x, ij=[[0, i + 1] for i in range(40)])
+    rc, _ = _create(lib, x=x, ij=[[0, i + 1] for i in range(40)], kernel=1)
     assert rc == 1 and "31" in lib.ms_last_error().decode()
+
+
+def test_tiled_kernel_rejects_tiles_that_overflow_shared_memory(lib):
+    # a hub joined to 5000 far-away masses: the tile holding the hub needs
+    # more halo entries than a CTA's shared memory holds
+    n = 5001
+    x = [[float(i), 0.0, 0.0] for i in range(n)]
+    rc, _ = _create(lib, x=x, ij=[[0, i] for i in range(1, n)], kernel=2)
+    assert rc == 1 and "shared-memory" in lib.ms_last_error().decode()
+
+
+def test_bad_kernel_choice(lib):
+    rc, _ = _create(lib, kernel=7)
+    assert rc == 1 and "kernel" in lib.ms_last_error().decode()
 
 
 def test_null_handles_are_errors(lib):

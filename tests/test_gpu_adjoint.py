@@ -1,0 +1,165 @@
+"""Hand-written adjoint of voxel-robot rollouts vs central finite differences
+of the FP64 oracle.
+
+The oracle builds each robot voxel by voxel (28 springs per voxel, k =
+exp(logk_v), rest length L0 (1 + A sin(2 pi f t + phase_v))) and the
+gradient is (L(p + e) - L(p - e)) / 2e per parameter.  Where the rollout
+crosses a contact or friction branch between p - e and p + e the FD is not
+a derivative; such components are recognised by their FD changing with e
+(1e-5, 1e-6, 1e-7) and are reported, not gated.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ms():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2207_09334_gb300 as ms
+    ms.load()
+    return ms
+
+
+def f32p(p):
+    q = dict(p)
+    for key in ("dt", "k_c", "mu", "vel_damping"):
+        q[key] = float(np.float32(q[key]))
+    q["g"] = tuple(float(np.float32(g)) for g in p["g"])
+    return q
+
+
+def oracle_loss(ora, mat, phase, logk, params, nsteps, seed=None):
+    s = ora.voxel_system(mat, phase, synth.VOXEL_MATERIALS, synth.VOXEL_FREQ, synth.VOXEL_EDGE,
+                         synth.VOXEL_MASS, logk=logk)
+    x, _ = ora.run(s, f32p(params), nsteps)
+    if seed is not None:
+        return float(np.sum(seed * x))
+    m = s["m"]
+    return float(ora.centre_of_mass(m, x)[0] - ora.centre_of_mass(m, s["x"])[0])
+
+
+def fd_grad(ora, mat, phase, logk, params, nsteps, eps, seed=None):
+    gp = np.zeros(phase.size); gk = np.zeros(logk.size)
+    occ = mat.ravel() > 0
+    for v in np.flatnonzero(occ):
+        for arr, out in ((phase, gp), (logk, gk)):
+            a = arr.astype(np.float64).ravel().copy()
+            a[v] += eps
+            lp = oracle_loss(ora, mat, phase if arr is logk else a.reshape(arr.shape),
+                             logk if arr is phase else a.reshape(arr.shape), params, nsteps, seed)
+            a[v] -= 2 * eps
+            lm = oracle_loss(ora, mat, phase if arr is logk else a.reshape(arr.shape),
+                             logk if arr is phase else a.reshape(arr.shape), params, nsteps, seed)
+            out[v] = (lp - lm) / (2 * eps)
+    return gp, gk
+
+
+def base_logk(mat):
+    k = synth.VOXEL_MATERIALS[:, 0]
+    return np.where(mat > 0, np.log(np.maximum(k[mat], 1.0)), 0.0).astype(np.float32)
+
+
+def test_smooth_loss_gradient_matches_fd(ms, ora):
+    """No contact, no gravity, loss = sum_i w_i . x_i(T): a smooth function of
+    every parameter; every component must match the FD within 1e-3."""
+    rng = np.random.default_rng(31)
+    mat = rng.integers(1, 4, size=(2, 2, 2)).astype(np.uint8)
+    phase = rng.uniform(0, 2 * np.pi, size=mat.shape).astype(np.float32)
+    logk = (base_logk(mat) + rng.normal(0, 0.1, size=mat.shape)).astype(np.float32)
+    params = synth.voxel_params(contact=False, mu=0.0, g=(0.0, 0.0, 0.0))
+    n = 27
+    seed = rng.standard_normal((n, 3)).astype(np.float32)
+    nsteps = 400
+    with ms.Adjoint([mat], synth.VOXEL_MATERIALS, synth.VOXEL_FREQ, synth.VOXEL_EDGE, synth.VOXEL_MASS,
+                    params, checkpoint_every=100, max_steps=nsteps) as adj:
+        assert adj.n_masses == n
+        loss, gp, gk = adj.gradients(nsteps, phase, logk, seed_x=seed)
+    lo = oracle_loss(ora, mat, phase.astype(np.float64), logk.astype(np.float64), params, nsteps, seed)
+    assert abs(loss[0] - lo) <= 1e-5 * max(1.0, abs(lo))
+    fp, fk = fd_grad(ora, mat, phase.astype(np.float64), logk.astype(np.float64), params, nsteps, 1e-6, seed)
+    for g, f, name in ((gp, fp, "phase"), (gk, fk, "logk")):
+        scale = np.abs(f).max()
+        err = np.abs(g - f)
+        assert np.all(err <= 1e-3 * np.maximum(np.abs(f), 1e-2 * scale)), (name, g, f)
+
+
+def _contact_check(ms, ora, mat, phase, logk, nsteps):
+    params = synth.voxel_params()
+    with ms.Adjoint([mat], synth.VOXEL_MATERIALS, synth.VOXEL_FREQ, synth.VOXEL_EDGE, synth.VOXEL_MASS,
+                    params, checkpoint_every=100, max_steps=nsteps) as adj:
+        loss, gp, gk = adj.gradients(nsteps, phase, logk)
+    p64, k64 = phase.astype(np.float64), logk.astype(np.float64)
+    fds = [fd_grad(ora, mat, p64, k64, params, nsteps, eps) for eps in (1e-5, 1e-6, 1e-7)]
+    occ = mat.ravel() > 0
+    report = []
+    smooth = ok = 0
+    for which, g in ((0, gp), (1, gk)):
+        f5, f6, f7 = (fd[which] for fd in fds)
+        scale = np.abs(f6[occ]).max()
+        for v in np.flatnonzero(occ):
+            den = max(abs(f6[v]), 1e-2 * scale)
+            consistent = abs(f5[v] - f6[v]) <= 1e-3 * den and abs(f7[v] - f6[v]) <= 1e-3 * den
+            rel = abs(g[v] - f6[v]) / den
+            smooth += consistent
+            ok += consistent and rel <= 1e-3
+            report.append((which, int(v), bool(consistent), float(g[v]), float(f6[v]), rel))
+    return loss, smooth, ok, report
+
+
+def test_contact_gradient_200_steps(ms, ora):
+    """With ground contact and friction: every FD-consistent component
+    matches within 1e-3, and most components are FD-consistent."""
+    rng = np.random.default_rng(33)
+    mat, phase = synth.random_voxel_design(rng, (3, 3, 3))
+    logk = base_logk(mat)
+    loss, smooth, ok, report = _contact_check(ms, ora, mat, phase, logk, 200)
+    assert smooth >= len(report) // 2, report
+    assert ok == smooth, [r for r in report if r[2] and r[5] > 1e-3]
+
+
+@pytest.mark.slow
+def test_contact_gradient_2000_steps_3x3x3(ms, ora):
+    """The differentiable-batch check: a 3x3x3 robot, 2000 steps, loss =
+    centre-of-mass x-travel, central FD of the FP64 oracle at eps = 1e-6.
+    Components whose FD is consistent across eps must match within 1e-3."""
+    rng = np.random.default_rng(3)
+    mat, phase = synth.random_voxel_design(rng, (3, 3, 3))
+    logk = base_logk(mat)
+    loss, smooth, ok, report = _contact_check(ms, ora, mat, phase, logk, 2000)
+    print("\nFD-consistent components:", smooth, "of", len(report), "; matching within 1e-3:", ok)
+    for r in report:
+        print("  %-5s voxel %2d consistent=%d adjoint=% .6e fd=% .6e rel=%.2e" %
+              ("phase" if r[0] == 0 else "logk", r[1], r[2], r[3], r[4], r[5]))
+    assert ok == smooth, [r for r in report if r[2] and r[5] > 1e-3]
+
+
+def test_autograd_function_and_batch_forward(ms):
+    """RolloutLoss (torch.autograd.Function) returns the batched simulator's
+    travel and back-propagates the adjoint's gradients, weighted per robot."""
+    import torch
+    rng = np.random.default_rng(35)
+    designs = [synth.random_voxel_design(rng, (3, 2, 2)) for _ in range(3)]
+    mats = [m for m, _ in designs]
+    params = synth.voxel_params()
+    phase = torch.tensor(np.concatenate([p.ravel() for _, p in designs]), device="cuda", requires_grad=True)
+    logk = torch.tensor(np.concatenate([base_logk(m).ravel() for m in mats]), device="cuda", requires_grad=True)
+    with ms.Adjoint(mats, synth.VOXEL_MATERIALS, synth.VOXEL_FREQ, synth.VOXEL_EDGE, synth.VOXEL_MASS,
+                    params, checkpoint_every=50, max_steps=300) as adj:
+        loss = ms.RolloutLoss.apply(phase, logk, adj, 300)
+        wts = torch.tensor([1.0, -2.0, 0.5], device="cuda")
+        (loss * wts).sum().backward()
+        _, gp, gk = adj.gradients(300, phase.detach(), logk.detach())
+    vr = torch.as_tensor(adj.voxel_robot, device="cuda")
+    torch.testing.assert_close(phase.grad, wts[vr] * gp)
+    torch.testing.assert_close(logk.grad, wts[vr] * gk)
+    with ms.Population(designs, synth.VOXEL_MATERIALS, synth.VOXEL_FREQ, synth.VOXEL_EDGE, synth.VOXEL_MASS,
+                       params) as pop:
+        pop.run(300)
+        travel = pop.com_travel()
+    np.testing.assert_allclose(loss.detach().cpu().numpy(), travel, rtol=0, atol=2e-6)

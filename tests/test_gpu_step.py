@@ -42,8 +42,11 @@ def body_size(s):
     return float(np.ptp(np.asarray(s["x"], np.float64), axis=0).max())
 
 
-def gpu_run(ms, s, p, n, reorder=False, chunks=1):
-    with ms.Sim(s, p, reorder=reorder) as sim:
+KERNELS = ["gather", "tiled"]
+
+
+def gpu_run(ms, s, p, n, reorder=None, chunks=1, kernel=None):
+    with ms.Sim(s, p, reorder=reorder, kernel=kernel) as sim:
         done = 0
         for q in range(chunks):
             todo = n * (q + 1) // chunks - done
@@ -69,23 +72,24 @@ def test_hand_worked_steps_on_gpu(ms):
         np.testing.assert_allclose(v, case["v_out"], rtol=2e-6, atol=1e-6, err_msg=case["name"])
 
 
-@pytest.mark.parametrize("reorder", [False, True])
-def test_soft_cube_contact_free_1000_steps(ms, ora, reorder):
+@pytest.mark.parametrize("kernel,reorder", [("gather", "caller"), ("gather", "morton"), ("tiled", "morton"), ("tiled", "caller")])
+def test_soft_cube_contact_free_1000_steps(ms, ora, kernel, reorder):
     s = synth.soft_cube()
     p = synth.soft_cube_params(contact=False)
-    xg, vg = gpu_run(ms, s, p, 1000, reorder=reorder, chunks=4)
+    xg, vg = gpu_run(ms, s, p, 1000, reorder=reorder, chunks=4, kernel=kernel)
     xo, vo = ora.run(s, f32p(p), 1000)
     err = np.abs(xg - xo).max()
     assert err <= 1e-5 * body_size(s), (err, 1e-5 * body_size(s))
 
 
-def test_soft_cube_contact_200_steps(ms, ora):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_soft_cube_contact_200_steps(ms, ora, kernel):
     """Cube 1 mm above the ground, thrown down and sideways: contact and
     friction are active within the 200 steps."""
     s = synth.soft_cube(z0=0.001)
     s["v"][:] = np.array([0.3, -0.2, -0.6], np.float32)
     p = synth.soft_cube_params(contact=True)
-    xg, _ = gpu_run(ms, s, p, 200)
+    xg, _ = gpu_run(ms, s, p, 200, kernel=kernel)
     xo, vo = s["x"], s["v"]
     zmin = np.inf
     for c in range(20):
@@ -104,25 +108,33 @@ def test_soft_cube_contact_200_steps(ms, ora):
 def test_soft_cube_full_drop_com_travel(ms, ora):
     """The dropped-cube workload: 0.05 m drop onto the ground, 10,000 steps.
     The vertical centre-of-mass travel agrees within 1 %.  The sideways drift
-    of this symmetric, bouncing drop is chaotic (perturbing the FP64 start
-    positions by 1e-9 m moves it from 5e-5 m to 2e-4 m), so only its size is
-    bounded: below 5 % of the travel."""
+    of this symmetric, bouncing drop is chaotic, so it is gated against the
+    oracle's own sensitivity: within three times the largest deviation of
+    four FP64 runs whose start positions are perturbed by 1e-9 m (or 1e-4 m)."""
     s = synth.soft_cube()
     p = synth.soft_cube_params(contact=True)
     xg, _ = gpu_run(ms, s, p, 10000, chunks=10)
     xo, _ = ora.run(s, f32p(p), 10000)
     m = s["m"].astype(np.float64)
-    d_o = ora.centre_of_mass(m, xo) - ora.centre_of_mass(m, s["x"])
-    d_g = ora.centre_of_mass(m, xg) - ora.centre_of_mass(m, s["x"])
+    c0 = ora.centre_of_mass(m, s["x"])
+    d_o = ora.centre_of_mass(m, xo) - c0
+    d_g = ora.centre_of_mass(m, xg) - c0
     assert abs(d_g[2] - d_o[2]) <= 0.01 * abs(d_o[2])
-    assert np.linalg.norm(d_g[:2]) <= 0.05 * np.linalg.norm(d_o)
+    spread = 0.0
+    ar = ora._Arrays(s)
+    for q in range(4):
+        xp = s["x"].astype(np.float64) + 1e-9 * np.random.default_rng(200 + q).standard_normal(s["x"].shape)
+        x1, _ = ora.run(s, f32p(p), 10000, x=xp, arrays=ar)
+        spread = max(spread, float(np.linalg.norm((ora.centre_of_mass(m, x1) - c0 - d_o)[:2])))
+    assert np.linalg.norm(d_g[:2] - d_o[:2]) <= max(3 * spread, 1e-4), (d_g, d_o, spread)
     assert xg[:, 2].min() > -1e-3                  # resting on the plane, not through it
 
 
-def test_cantilever_with_anchors_and_external_force(ms, ora):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_cantilever_with_anchors_and_external_force(ms, ora, kernel):
     s = synth.cantilever(40, 4, 4, c=0.1)
     p = synth.params(dt=1e-4, g=(0, 0, 0))
-    xg, vg = gpu_run(ms, s, p, 2000, chunks=2)
+    xg, vg = gpu_run(ms, s, p, 2000, chunks=2, kernel=kernel)
     xo, vo = ora.run(s, f32p(p), 2000)
     fixed = s["fixed"].astype(bool)
     assert np.all(xg[fixed] == s["x"][fixed]) and np.all(vg[fixed] == 0)
@@ -131,7 +143,8 @@ def test_cantilever_with_anchors_and_external_force(ms, ora):
     assert err <= 1e-5 * body_size(s), (err, 1e-5 * body_size(s))
 
 
-def test_actuated_heterogeneous_lattice(ms, ora):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_actuated_heterogeneous_lattice(ms, ora, kernel):
     x, ij, L0 = synth.box_lattice(7, 6, 5, 0.01, origin=(0, 0, 0.02))
     rng = np.random.default_rng(11)
     S = ij.shape[0]; N = x.shape[0]
@@ -141,7 +154,7 @@ def test_actuated_heterogeneous_lattice(ms, ora):
              L0=L0, A=rng.uniform(0, 0.2, S).astype(np.float32),
              phi=rng.uniform(0, 2 * np.pi, S).astype(np.float32), freq=5.0)
     p = synth.params(dt=1e-4, g=(0, 0, -9.81))
-    xg, _ = gpu_run(ms, s, p, 1000, chunks=3)
+    xg, _ = gpu_run(ms, s, p, 1000, chunks=3, kernel=kernel)
     xo, _ = ora.run(s, f32p(p), 1000)
     err = np.abs(xg - xo).max()
     assert err <= 1e-5 * body_size(s), (err, 1e-5 * body_size(s))
@@ -166,7 +179,8 @@ def test_parallel_springs_are_merged_exactly(ms, ora):
     assert err <= 1e-4 * body_size(s), (err, 1e-4 * body_size(s))
 
 
-def test_throughput_lattice_ragged(ms, ora):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_throughput_lattice_ragged(ms, ora, kernel):
     """Throughput-lattice parameters (k ~ U[5e3,5e4], c = 0.05, anchored
     bottom, v ~ N(0,1e-3), dt = 5e-5) on a 23x24x25 box: many slices and
     blocks and a ragged last block; 200 steps."""
@@ -179,32 +193,34 @@ def test_throughput_lattice_ragged(ms, ora):
     s = dict(x=x, v=v, m=np.full(N, 1e-3, np.float32), fixed=fixed, ij=ij,
              k=rk.uniform(5e3, 5e4, S).astype(np.float32), c=np.float32(0.05), L0=L0)
     p = synth.throughput_params()
-    xg, vg = gpu_run(ms, s, p, 200)
+    xg, vg = gpu_run(ms, s, p, 200, kernel=kernel)
     xo, vo = ora.run(s, f32p(p), 200)
     err = np.abs(xg - xo).max()
     assert err <= 1e-5 * body_size(s), (err, 1e-5 * body_size(s))
 
 
-def test_runs_are_bit_identical(ms):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_runs_are_bit_identical(ms, kernel):
     s = synth.soft_cube(z0=0.001)
     s["v"][:] = np.array([0.3, -0.2, -0.6], np.float32)
     p = synth.soft_cube_params(contact=True)
-    a, _ = gpu_run(ms, s, p, 300)
-    b, _ = gpu_run(ms, s, p, 300)
+    a, _ = gpu_run(ms, s, p, 300, kernel=kernel)
+    b, _ = gpu_run(ms, s, p, 300, kernel=kernel)
     assert np.array_equal(a, b)
 
 
-def test_state_round_trip_and_resume(ms):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_state_round_trip_and_resume(ms, kernel):
     """get_state / set_state checkpoint: 100 + 100 steps with a save/restore
     in between equals 200 straight steps (bit for bit)."""
     import torch
     s = synth.soft_cube(n=5, z0=0.001)
     s["v"][:] = np.array([0.1, 0.0, -0.4], np.float32)
     p = synth.soft_cube_params(contact=True)
-    with ms.Sim(s, p, reorder=True) as a:
+    with ms.Sim(s, p, reorder=True, kernel=kernel) as a:
         a.step(200)
         xa, va = a.get_state()
-    with ms.Sim(s, p, reorder=True) as b:
+    with ms.Sim(s, p, reorder=True, kernel=kernel) as b:
         b.step(100)
         xd = torch.empty((s["x"].shape[0], 3), device="cuda")
         vd = torch.empty_like(xd)
@@ -214,6 +230,16 @@ def test_state_round_trip_and_resume(ms):
         b.step(100)
         xb, vb = b.get_state()
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+
+
+def test_kernels_agree(ms):
+    """Gather and tiled kernels sum each mass's springs in different orders;
+    on a contact-free run they agree to rounding."""
+    s = synth.soft_cube(n=6)
+    p = synth.soft_cube_params(contact=False)
+    xa, _ = gpu_run(ms, s, p, 300, kernel="gather")
+    xb, _ = gpu_run(ms, s, p, 300, kernel="tiled")
+    np.testing.assert_allclose(xb, xa, rtol=0, atol=1e-7)
 
 
 def test_nonfinite_state_is_reported(ms):
@@ -228,13 +254,14 @@ def test_nonfinite_state_is_reported(ms):
         assert e.value.code == 5
 
 
-def test_empty_spring_set_is_free_fall(ms):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_empty_spring_set_is_free_fall(ms, kernel):
     s = dict(x=np.array([[0, 0, 1.0]], np.float32), v=np.array([[0.5, 0, 0]], np.float32),
              m=np.array([1e-3], np.float32), fixed=np.zeros(1, np.uint8),
              ij=np.zeros((0, 2), np.int32), k=np.zeros(0, np.float32), c=np.zeros(0, np.float32),
              L0=np.zeros(0, np.float32))
     p = synth.params(dt=1e-3)
-    x, v = gpu_run(ms, s, p, 100)
+    x, v = gpu_run(ms, s, p, 100, kernel=kernel)
     g = np.float32(-9.81); dt = np.float32(1e-3)
     assert abs(v[0, 2] - 100 * dt * g) < 1e-4
     assert abs(x[0, 0] - (0.0 + 100 * dt * 0.5)) < 1e-6
