@@ -329,6 +329,50 @@ ms_status msa_sizes(const msa_adjoint *a, int64_t *n_voxels, int64_t *n_masses);
 
 ms_status msa_destroy(msa_adjoint *a);
 
+/* ------------------------------------------------------------------------
+ * Design surrogate: an MLP n_in -> n_hidden -> n_hidden -> 1 with GELU,
+ * bf16 weights and activations, fp32 accumulation on the tensor cores
+ * (tcgen05 + TMEM, operands staged by TMA).  It predicts a voxel design's
+ * locomotion distance from its one-hot materials so that large candidate
+ * populations can be pre-screened before the simulator (above) judges the
+ * best.  The paper has no learned component; this serves the optimisation
+ * loop the paper motivates (Introduction: simulation for design and
+ * optimisation of soft robots).
+ *
+ * Parameters are one fp32 vector: W1 [n_hidden][n_in], b1 [n_hidden],
+ * W2 [n_hidden][n_hidden], b2 [n_hidden], w3 [n_hidden], b3 [1]
+ * (mlp_num_params entries).  Batches are multiples of 128 up to max_batch.
+ * Loss: 0.5 mean (y - target)^2.  All device-pointer arguments are
+ * stream-ordered on the model's stream.
+ * ---------------------------------------------------------------------- */
+typedef struct mlp_model mlp_model;
+
+/* n_in and n_hidden multiples of 128; weights uniform(+-1/sqrt(fan_in)) from seed, biases 0. */
+ms_status mlp_create(int32_t n_in, int32_t n_hidden, int32_t max_batch, uint64_t seed,
+                     const ms_allocator *alloc, void *stream, mlp_model **out);
+int64_t mlp_num_params(const mlp_model *m);
+/* host fp32 parameter vector in / out (grads: last computed gradient, may be NULL) */
+ms_status mlp_set_params(mlp_model *m, const float *params);
+ms_status mlp_get_params(mlp_model *m, float *params, float *grads);
+/* load a batch: one-hot encode device materials [B][n_in/4] (ids 0..3), or copy bf16 inputs [B][n_in] */
+ms_status mlp_encode(mlp_model *m, const uint8_t *materials, int32_t B);
+ms_status mlp_set_input(mlp_model *m, const uint16_t *x_bf16, int32_t B);
+/* predictions of the loaded batch into device y [B] (may be NULL) */
+ms_status mlp_forward(mlp_model *m, int32_t B, float *y);
+/* forward + backward of the loaded batch against device target [B]; gradients kept in the model;
+ * device loss [1] (may be NULL) */
+ms_status mlp_backward(mlp_model *m, const float *target, int32_t B, float *loss);
+/* one Adam step (bias-corrected) with the last gradients */
+ms_status mlp_adam(mlp_model *m, float lr, float beta1, float beta2, float eps);
+/* wait for the model's stream; MS_ERR_TIMEOUT if a bounded tensor-core wait gave up */
+ms_status mlp_sync(mlp_model *m);
+ms_status mlp_destroy(mlp_model *m);
+
+/* C[M][N] (fp32, device) = A[M][K] . B[N][K]^T with bf16 device inputs on the
+ * tensor cores; M, N multiples of 128, K a multiple of 64.  Synchronises. */
+ms_status mlp_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int32_t M, int32_t N, int32_t K,
+                        void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -9,5 +9,6 @@ from ._lib import MsError, library_path, load  # noqa: F401
 from .sim import Sim, make_params, torch_allocator  # noqa: F401
 from .batch import Population  # noqa: F401
 from .adjoint import Adjoint, RolloutLoss  # noqa: F401
+from .surrogate import Surrogate, gemm_bf16  # noqa: F401
 
 __version__ = "0.1.0"

@@ -86,6 +86,18 @@ SIGNATURES = {
     "msa_gradients": (C.c_int, [VP, I32, VP, VP, VP, VP, VP, VP, I32]),
     "msa_sizes": (C.c_int, [VP, C.POINTER(I64), C.POINTER(I64)]),
     "msa_destroy": (C.c_int, [VP]),
+    "mlp_create": (C.c_int, [I32, I32, I32, C.c_uint64, C.POINTER(MsAllocator), VP, C.POINTER(VP)]),
+    "mlp_num_params": (I64, [VP]),
+    "mlp_set_params": (C.c_int, [VP, VP]),
+    "mlp_get_params": (C.c_int, [VP, VP, VP]),
+    "mlp_encode": (C.c_int, [VP, VP, I32]),
+    "mlp_set_input": (C.c_int, [VP, VP, I32]),
+    "mlp_forward": (C.c_int, [VP, I32, VP]),
+    "mlp_backward": (C.c_int, [VP, VP, I32, VP]),
+    "mlp_adam": (C.c_int, [VP, F32, F32, F32, F32]),
+    "mlp_sync": (C.c_int, [VP]),
+    "mlp_destroy": (C.c_int, [VP]),
+    "mlp_gemm_bf16": (C.c_int, [VP, VP, VP, I32, I32, I32, VP]),
     "ms_version": (C.c_char_p, []),
 }
 

@@ -1,0 +1,108 @@
+"""Tensor-core (tcgen05) GEMM and the surrogate MLP vs the FP64 oracle."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ms():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2207_09334_gb300 as ms
+    ms.load()
+    return ms
+
+
+def bf16_round(a):
+    import torch
+    return torch.tensor(np.asarray(a, np.float32)).bfloat16().float().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 384, 320), (1024, 512, 2048), (512, 2048, 1024)])
+def test_gemm_matches_fp64(ms, M, N, K):
+    import torch
+    g = torch.Generator().manual_seed(M + N + K)
+    A = torch.randn(M, K, generator=g).bfloat16()
+    B = torch.randn(N, K, generator=g).bfloat16()
+    ref = A.double() @ B.double().T
+    out = ms.gemm_bf16(A.cuda(), B.cuda()).double().cpu()
+    err = (out - ref).abs().max().item()
+    bound = 1e-5 * (A.double().abs() @ B.double().abs().T).max().item()
+    assert err <= bound, (err, bound)
+
+
+def _mlp_case(ms, B=256, n_in=2048, h=512, seed=1):
+    import torch
+    rng = np.random.default_rng(seed)
+    mats = rng.integers(0, 4, size=(B, n_in // 4)).astype(np.uint8)
+    t = rng.normal(0, 1, B).astype(np.float32)
+    net = ms.Surrogate(n_in, h, max_batch=max(B, 128), seed=seed)
+    p = net.params().astype(np.float64)
+    # the kernels multiply with bf16 copies of W1 and W2: give the oracle the same weights
+    from oracle import mlp
+    W1, b1, W2, b2, w3, b3 = mlp.unpack(p, n_in, h)
+    pq = np.concatenate([bf16_round(W1).ravel(), b1, bf16_round(W2).ravel(), b2, w3, [b3]])
+    X = mlp.one_hot(mats)
+    dmats = torch.tensor(mats, device="cuda")
+    dt = torch.tensor(t, device="cuda")
+    return net, mlp, pq, X, t, dmats, dt
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def test_forward_and_gradients_match_oracle(ms):
+    net, mlp, pq, X, t, dmats, dt = _mlp_case(ms)
+    with net:
+        B = X.shape[0]
+        net.load_materials(dmats)
+        y = net.forward(B).cpu().numpy()
+        loss = float(net.backward(dt, B).item())
+        g = net.grads().astype(np.float64)
+    y_o, _ = mlp.forward(pq, X, 2048, 512)
+    loss_o, g_o = mlp.loss_and_grad(pq, X, t, 2048, 512)
+    assert rel_l2(y, y_o) < 2e-2
+    assert abs(loss - loss_o) <= 2e-2 * loss_o
+    W1, b1, W2, b2, w3, b3 = (np.asarray(a) for a in mlp.unpack(g, 2048, 512))
+    W1o, b1o, W2o, b2o, w3o, b3o = (np.asarray(a) for a in mlp.unpack(g_o, 2048, 512))
+    for name, a, b in (("W1", W1, W1o), ("b1", b1, b1o), ("W2", W2, W2o), ("b2", b2, b2o), ("w3", w3, w3o)):
+        assert rel_l2(a, b) < 3e-2, (name, rel_l2(a, b))
+    assert abs(b3 - b3o) <= 1e-3 * abs(b3o) + 1e-7
+
+
+def test_adam_step_matches_oracle(ms):
+    net, mlp, pq, X, t, dmats, dt = _mlp_case(ms, B=128)
+    with net:
+        p0 = net.params().astype(np.float64)
+        net.load_materials(dmats)
+        net.backward(dt, 128)
+        g = net.grads().astype(np.float64)
+        net.adam(1e-3)
+        p1 = net.params().astype(np.float64)
+    ref, _, _ = mlp.adam(p0, g, np.zeros_like(p0), np.zeros_like(p0), 1, lr=1e-3)
+    np.testing.assert_allclose(p1, ref, rtol=0, atol=1e-6)
+
+
+def test_training_fits_a_learnable_target(ms):
+    """A target that is a fixed function of the one-hot design: Adam on the
+    tensor-core kernels cuts the loss by 10x."""
+    import torch
+    rng = np.random.default_rng(5)
+    N, B = 4096, 512
+    mats = rng.integers(0, 4, size=(N, 512)).astype(np.uint8)
+    from oracle import mlp
+    wt = rng.normal(0, 1, 2048)
+    tt = mlp.one_hot(mats) @ wt
+    tt = ((tt - tt.mean()) / tt.std()).astype(np.float32)
+    dm = torch.tensor(mats, device="cuda"); dtt = torch.tensor(tt, device="cuda")
+    with ms.Surrogate(2048, 512, max_batch=B, seed=2) as net:
+        first = None
+        for it in range(400):
+            s = (it * B) % N
+            loss = float(net.train_step(dm[s:s + B], dtt[s:s + B], lr=1e-3).item())
+            first = first if first is not None else loss
+        net.sync()
+    assert loss < 0.1 * first, (first, loss)
