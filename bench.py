@@ -310,6 +310,141 @@ def run_ours(args, world, rank, local):
     return 0
 
 
+# ------------------------------------------------------------------ other workloads
+def run_population(args, world, rank, local):
+    """Batched voxel-robot population: robot-sim-seconds per second, batched
+    persistent launch vs the per-robot launch loop on the same GPU."""
+    import torch
+    import paper_2207_09334_gb300 as ms
+    torch.cuda.set_device(local)
+    ms.load()
+    designs = synth.voxel_population(args.robots, seed=2)
+    p = synth.voxel_params()
+    t0 = time.perf_counter()
+    pop = ms.Population(designs, synth.VOXEL_MATERIALS, synth.VOXEL_FREQ, synth.VOXEL_EDGE, synth.VOXEL_MASS, p)
+    pop.autotune(sample_steps=50)
+    inf = pop.info()
+    t_create = time.perf_counter() - t0
+    S = args.sim_steps_per_bench_step
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        pop.run(S)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            pop.run(S)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms_total = e0.elapsed_time(e1)
+    sim_s = args.robots * S * p["dt"] * args.steps
+    value = sim_s / (ms_total * 1e-3)
+    el_per_step = inf["n_masses"] + inf["n_records"]
+    # the plain per-robot loop on a short sample of steps
+    L = args.loop_steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pop.run_loop(L)
+    torch.cuda.synchronize()
+    loop_s = time.perf_counter() - t0
+    loop_value = args.robots * L * p["dt"] / loop_s
+    travel = pop.com_travel()
+    line = {"metric": "batched robot-sim-s/s", "value": value, "unit": "robot-sim-s/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded)",
+            "config": {"workload": f"population of {args.robots} voxel robots (sides U{{3..12}}, seed 2), "
+                                   f"one bench step = {S} simulated steps (dt = 1e-4) in one persistent launch",
+                       "n_masses": inf["n_masses"], "n_springs_merged": inf["n_records"],
+                       "block_robots": inf["n_block_items"], "warp_robots": inf["n_warp_items"],
+                       "setup_s": round(t_create, 1)},
+            "elements_per_s": el_per_step * S * args.steps / (ms_total * 1e-3),
+            "per_robot_loop": {"value": loop_value, "unit": "robot-sim-s/s", "sim_steps": L,
+                               "speedup_of_batched": value / loop_value},
+            "gpu_launches": 3 * args.steps, "clocks": clk.summary(),
+            "travel_mean_m": float(np.mean(travel))}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    pop.close()
+    return 0
+
+
+def run_surrogate(args, world, rank, local):
+    """Surrogate screening throughput: candidate designs scored per second by
+    the tensor-core MLP (one-hot encode + forward), against the simulator's
+    designs per second for the same 2 s rollouts."""
+    import torch
+    import paper_2207_09334_gb300 as ms
+    torch.cuda.set_device(local)
+    ms.load()
+    B = 1024
+    n_cand = args.candidates
+    rng = np.random.default_rng(4)
+    cand = torch.tensor(rng.integers(0, 4, size=(n_cand, 512)).astype(np.uint8), device="cuda")
+    net = ms.Surrogate(2048, 512, max_batch=B, seed=0)
+    out = torch.empty(n_cand, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def screen_once():
+        for s in range(0, n_cand, B):
+            net.load_materials(cand[s:s + B])
+            net.forward(B, out[s:s + B])
+    for _ in range(args.warmup):
+        screen_once()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            screen_once()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms_total = e0.elapsed_time(e1)
+    value = n_cand * args.steps / (ms_total * 1e-3)
+    flops = 2.0 * (2048 * 512 + 512 * 512 + 512) * n_cand * args.steps
+    # training step throughput (forward + backward + Adam, batch 1024)
+    tgt = torch.randn(B, device="cuda")
+    for _ in range(3):
+        net.train_step(cand[:B], tgt)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(20):
+        net.train_step(cand[:B], tgt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1) / 20
+    # the simulator's rate on the same kind of design (2 s rollout = 20000 steps), sampled
+    side = 8
+    nsim = args.sim_designs
+    designs = [(m.reshape(side, side, side), synth.surrogate_phase_field(side))
+               for m in rng.integers(0, 4, size=(nsim, 512)).astype(np.uint8)]
+    with ms.Population(designs, synth.VOXEL_MATERIALS, synth.VOXEL_FREQ, synth.VOXEL_EDGE, synth.VOXEL_MASS,
+                       synth.voxel_params()) as pop:
+        pop.autotune(sample_steps=50)
+        pop.run(200)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pop.run(2000)
+        torch.cuda.synchronize()
+        sim_rate = nsim / ((time.perf_counter() - t0) * 10.0)      # 2000 of the 20000 steps
+    line = {"metric": "designs screened/s", "value": value, "unit": "designs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)",
+            "data": "synthetic (seeded)",
+            "config": {"workload": f"MLP 2048->512->512->1 scoring {n_cand} one-hot 8^3 designs per bench step"},
+            "tensor_tflops": flops / (ms_total * 1e-3) / 1e12,
+            "train_step_ms_batch1024": train_ms,
+            "simulator_designs_per_s_2s_rollout": sim_rate,
+            "screen_speedup_vs_simulation": value / sim_rate,
+            "gpu_launches": args.steps * (2 * (n_cand // B) + 2 * (n_cand // B)),
+            "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    net.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -324,12 +459,22 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--ref-side", type=int, default=40)
+    ap.add_argument("--workload", default="lattice", choices=["lattice", "population", "surrogate"])
+    ap.add_argument("--robots", type=int, default=4096)
+    ap.add_argument("--sim-steps-per-bench-step", type=int, default=100)
+    ap.add_argument("--loop-steps", type=int, default=5)
+    ap.add_argument("--candidates", type=int, default=1 << 20)
+    ap.add_argument("--sim-designs", type=int, default=1024)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.workload == "population":
+        return run_population(args, world, rank, local)
+    if args.workload == "surrogate":
+        return run_surrogate(args, world, rank, local)
     return run_ours(args, world, rank, local)
 
 

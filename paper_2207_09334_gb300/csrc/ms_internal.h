@@ -47,7 +47,7 @@ constexpr int kKernelGather = 1;   // one thread per mass, sliced-ELL rows + bac
 constexpr int kKernelTiled = 2;    // CTA per tile of masses, state + halo in shared memory
 constexpr int kTileMasses = 512;   // masses per tile (= threads per CTA)
 constexpr int kTileMaxLocal = 2048; // tile members + halo that fit the CTA's shared memory (24 B each)
-constexpr int kTileGroup = 4;      // spring slots per pipeline stage (one bulk copy per array)
+constexpr int kTileGroup = 3;      // spring slots per pipeline stage (one bulk copy per array)
 constexpr int kTileStages = 2;     // pipeline depth
 constexpr int kErrNonFinite = 1;   // bits of the device error flag
 constexpr int kErrTimeout = 2;
