@@ -373,6 +373,49 @@ ms_status mlp_destroy(mlp_model *m);
 ms_status mlp_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int32_t M, int32_t N, int32_t K,
                         void *stream);
 
+/* ------------------------------------------------------------------------
+ * Stepping without allocating.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate device memory when they advance a system: code
+ * running while a CUDA graph is being captured (allocation calls are not
+ * capturable), plugins inside a host framework that owns every device
+ * allocation, and real-time loops that forbid allocator calls.  The caller
+ * owns every input and output; the only working memory is a fixed array
+ * that the library declares in its own device memory, so every GPU that
+ * loads the library holds it (16 MiB) until the process exits.
+ * ---------------------------------------------------------------------- */
+#define MS_NOALLOC_MAX_MASSES 262144
+
+/*
+ * ms_step_csr_noalloc -- advance nsteps explicit steps (the same physics as
+ * ms_step: Hooke term with axial dashpot, gravity, ground contact and the
+ * friction clamp, symplectic Euler, global damping; no actuation, no
+ * external force) of a system given directly as device arrays, calling no
+ * allocator of any kind.
+ *   N            masses, 1 <= N <= MS_NOALLOC_MAX_MASSES (larger N: MS_ERR_ARG).
+ *   x_in, v_in   (N,3) device, state at t_0 (read only).
+ *   mass         (N) device masses; fixed (N) device 1 = anchored, or NULL.
+ *   row_ptr      (N+1) device CSR offsets; the springs of mass i are entries
+ *                row_ptr[i] .. row_ptr[i+1]-1 of partner / k / c / rest_len
+ *                (device, one entry per spring end: every spring is listed
+ *                in the rows of both of its masses, with equal k, c, L0).
+ *   x_out, v_out (N,3) device, state after nsteps; must not alias the inputs.
+ *   stream       cudaStream_t (NULL = legacy default stream); asynchronous.
+ * The intermediate states of a multi-step call live in the library's fixed
+ * scratch array, which every call shares: calls whose work overlaps on the
+ * GPU (on different streams, or from different threads) race on it and must
+ * be serialised by the caller.  The first call on each device looks up the
+ * array's device address (with that device current) and caches it; make
+ * that first call before any stream capture begins.  Non-finite results are
+ * not flagged by this entry point.
+ */
+ms_status ms_step_csr_noalloc(const ms_params *p, int32_t N, const float *x_in, const float *v_in,
+                              const float *mass, const uint8_t *fixed, const int32_t *row_ptr,
+                              const int32_t *partner, const float *k, const float *c,
+                              const float *rest_len, int32_t nsteps, float *x_out, float *v_out,
+                              void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -98,6 +98,8 @@ SIGNATURES = {
     "mlp_sync": (C.c_int, [VP]),
     "mlp_destroy": (C.c_int, [VP]),
     "mlp_gemm_bf16": (C.c_int, [VP, VP, VP, I32, I32, I32, VP]),
+    "ms_step_csr_noalloc": (C.c_int, [C.POINTER(MsParams), I32, VP, VP, VP, VP, VP, VP, VP, VP, VP, I32, VP, VP,
+                                      VP]),
     "ms_version": (C.c_char_p, []),
 }
 
