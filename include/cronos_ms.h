@@ -58,13 +58,18 @@ typedef struct {
     float mu;               /* Coulomb friction coefficient on the ground (impulse clamp on tangential v) */
     float vel_damping;      /* global damping d: v' *= (1 - d) every step (0 = off) */
     int32_t contact_on;     /* 1 = ground contact active */
-    int32_t integrator;     /* 0 = symplectic Euler (only value supported by the GPU path) */
+    int32_t integrator;     /* 0 = symplectic Euler (default); 1 = forward Euler (eq. 4); 2 = position
+                               Verlet (eq. 5-6; no friction, no global damping; the dashpots see
+                               v_n = (x_n - x_{n-1})/dt).  ms_create only; populations and the
+                               adjoint take 0. */
     int32_t strict_stability; /* 1 = ms_create fails with MS_ERR_UNSTABLE if the bound below exceeds 4 */
     int32_t reorder;        /* mass order: 0 = library default (Morton for the tiled kernel, caller
                                order for the gather kernel), 1 = Morton order by initial position,
                                2 = caller order */
-    int32_t kernel;         /* 0 = library default (tiled, or gather when a tile's partners do not fit
-                               shared memory), 1 = gather, 2 = tiled (MS_ERR_ARG if a tile does not fit) */
+    int32_t kernel;         /* 0 = library default: tiled (gather when a tile's partners do not fit
+                               shared memory); 1 = gather, 2 = tiled (MS_ERR_ARG if a tile does not fit),
+                               3 = persistent (all steps of one ms_step call in one launch, the state in
+                               shared memory; MS_ERR_ARG beyond 4096 masses or with external force) */
 } ms_params;
 
 /* Optional device allocator (e.g. a framework's caching allocator).
@@ -89,7 +94,7 @@ typedef struct {
     double stability_bound;    /* dt^2 * max_i (2 sum_{springs at i} k + k_c) / m_i  (Gershgorin; stable if < 4) */
     int32_t max_fwd_degree;    /* gather: most springs owned by one mass; tiled: most springs of one mass */
     int32_t max_back_degree;
-    int32_t kernel;            /* 1 = gather, 2 = tiled */
+    int32_t kernel;            /* 1 = gather, 2 = tiled, 3 = persistent */
     int32_t n_tiles;
     int32_t max_tile_local;    /* tiled: largest members + halo of a tile */
 } ms_info_t;

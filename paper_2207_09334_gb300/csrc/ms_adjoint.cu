@@ -479,7 +479,7 @@ ms_status msa_gradients(msa_adjoint *b, int32_t nsteps, const float *phase, cons
     MSA_CUDA_TRY(cudaGetLastError());
     AdjArgs a{};
     a.robots = b->robots; a.slot_range = b->slot_range;
-    a.rec = Records{b->slice, b->f_nbr, b->f_kl, b->f_c, b->f_ab, b->b_ent};
+    a.rec = Records{b->slice, b->f_nbr, b->f_kl, b->f_c, b->f_ab, b->b_ent, 0.f};
     a.slot_vox = b->slot_vox; a.vox_slots = b->vox_slots; a.vox_amp = b->vox_amp;
     a.phase = b->phase; a.logk = b->logk; a.st0 = b->st0; a.seed = seed;
     a.ckpt = b->ckpt; a.seg = b->seg; a.scratch = b->scratch; a.sc = b->sc;

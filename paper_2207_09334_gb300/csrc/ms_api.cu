@@ -13,6 +13,7 @@
 // Everything is O(S) except the optional Morton sort (O(N log N)).
 #include "cronos_ms.h"
 #include "ms_internal.h"
+#include "ms_voxel.h"
 
 #include <algorithm>
 #include <cmath>
@@ -86,7 +87,10 @@ struct ms_sim {
     float *f_c = nullptr;
     uint32_t *b_ent = nullptr;
     // tiled layout
-    int kernel = 0;                     // ms::kKernelGather or ms::kKernelTiled
+    int kernel = 0;                     // ms::kKernelGather or ms::kKernelTiled (record layout)
+    bool persistent = false;            // gather layout stepped by one persistent CTA
+    float2 *sc = nullptr;               // (sin, cos) table of a persistent multi-step call
+    int sc_cap = 0;
     int n_tiles = 0, max_tile_local = 0;
     uint16_t *t_nbr = nullptr;
     int4 *tiles = nullptr;
@@ -175,7 +179,9 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
     if (N < 1 || N >= (1 << ms::kOwnerBits)) return fail(MS_ERR_ARG, "N must be in [1, 2^27)");
     if (S < 0 || (S > 0 && (!ij || !k))) return fail(MS_ERR_ARG, "S < 0, or ij / k missing");
     if (!(p->dt > 0.f) || !std::isfinite(p->dt)) return fail(MS_ERR_ARG, "dt must be positive and finite");
-    if (p->integrator != 0) return fail(MS_ERR_ARG, "the GPU path implements integrator 0 (symplectic Euler) only");
+    if (p->integrator < 0 || p->integrator > 2) return fail(MS_ERR_ARG, "integrator must be 0 (symplectic Euler), 1 (forward Euler) or 2 (Verlet)");
+    if (p->integrator == 2 && (p->mu > 0.f || p->vel_damping != 0.f))
+        return fail(MS_ERR_ARG, "the Verlet integrator takes no friction and no global damping");
     if (!(p->vel_damping >= 0.f && p->vel_damping < 1.f)) return fail(MS_ERR_ARG, "vel_damping must be in [0, 1)");
     if (p->contact_on && !(p->k_c >= 0.f && p->mu >= 0.f)) return fail(MS_ERR_ARG, "k_c and mu must be >= 0");
     if (!c && !(c_uniform >= 0.f && std::isfinite(c_uniform))) return fail(MS_ERR_ARG, "c_uniform must be >= 0");
@@ -196,8 +202,16 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
     if (alloc) { s->alloc = *alloc; s->custom_alloc = true; }
     s->c_uniform = c_uniform;
 
-    if (p->kernel < 0 || p->kernel > 2 || p->reorder < 0 || p->reorder > 2) return fail(MS_ERR_ARG, "kernel and reorder must be 0, 1 or 2");
-    s->kernel = p->kernel == 1 ? ms::kKernelGather : ms::kKernelTiled;
+    if (p->kernel < 0 || p->kernel > 3 || p->reorder < 0 || p->reorder > 2) return fail(MS_ERR_ARG, "kernel must be 0..3 and reorder 0..2");
+    const bool small = N <= ms::kMaxRobotMasses && !fext && p->integrator == 0;
+    if (p->kernel == 3 && !small)
+        return fail(MS_ERR_ARG, "the persistent kernel takes at most 4096 masses, no external force and symplectic Euler");
+    s->kernel = p->kernel == 1 ? ms::kKernelGather
+              : p->kernel == 2 ? ms::kKernelTiled
+              : p->kernel == 3 ? ms::kKernelPersistent
+              : ms::kKernelTiled;
+    const bool persistent = s->kernel == ms::kKernelPersistent;
+    if (persistent) s->kernel = ms::kKernelGather;     // same record layout; stepped by one persistent CTA
 
     // 1. mass order
     s->perm.resize(N); s->iperm.resize(N);
@@ -487,6 +501,7 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
             }
     }
     s->n_slots = n_slots;
+    s->persistent = persistent && s->kernel == ms::kKernelGather;
     s->rec_slot_a.swap(slot_a);
     s->rec_slot_b.swap(slot_b);
 
@@ -530,7 +545,7 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
         if ((st = upload(s, &s->f_nbr, h_nbr.data(), n_slots)) != MS_OK) return st;
         if ((st = upload(s, &s->b_ent, h_b.data(), h_b.size())) != MS_OK) return st;
     } else {
-        if ((st = upload(s, &s->t_nbr, h_nbr16.data(), n_slots)) != MS_OK) return st;
+        if ((st = upload(s, &s->t_nbr, h_nbr16.data(), h_nbr16.size())) != MS_OK) return st;
         if ((st = upload(s, &s->tiles, h_tiles.data(), h_tiles.size())) != MS_OK) return st;
         if ((st = upload(s, &s->halo, h_halo.data(), h_halo.size())) != MS_OK) return st;
     }
@@ -592,6 +607,25 @@ ms_status ms_step(ms_sim *s, int32_t nsteps)
 {
     if (!s) return fail(MS_ERR_ARG, "sim is NULL");
     if (nsteps < 0) return fail(MS_ERR_ARG, "nsteps must be >= 0");
+    const double two_pi_f = 2.0 * M_PI * s->freq;
+    if (s->persistent) {
+        if (nsteps == 0) return MS_OK;
+        const float2 *sc = nullptr;
+        if (s->actuated) {
+            if (nsteps > s->sc_cap) {
+                ms_status st = upload<float2>(s, &s->sc, nullptr, (size_t)nsteps);
+                if (st != MS_OK) return st;
+                s->sc_cap = nsteps;
+            }
+            ms::launch_sc_table_from(s->step_count, nsteps, (double)s->p.dt, two_pi_f, s->sc, s->stream);
+            MS_CUDA_TRY(cudaGetLastError());
+            sc = s->sc;
+        }
+        ms::Records rec{s->slice, s->f_nbr, s->f_kl, s->f_c, s->actuated ? s->f_ab : nullptr, s->b_ent, s->c_uniform};
+        MS_CUDA_TRY(ms::launch_persistent(rec, ms::make_env(s->p), s->st[s->cur], s->N, sc, nsteps, s->err, s->stream));
+        s->step_count += nsteps;
+        return MS_OK;
+    }
     ms::StepArgs a{};
     a.fext = s->fext; a.slice = s->slice; a.f_nbr = s->f_nbr; a.f_kl = s->f_kl;
     a.f_c = s->f_c; a.f_ab = s->actuated ? s->f_ab : nullptr;
@@ -600,8 +634,9 @@ ms_status ms_step(ms_sim *s, int32_t nsteps)
     a.tile_local = s->max_tile_local; a.tiled = s->kernel == ms::kKernelTiled;
     a.dt = s->p.dt; a.gx = s->p.g[0]; a.gy = s->p.g[1]; a.gz = s->p.g[2];
     a.k_c = s->p.k_c; a.mu = s->p.mu; a.keep = 1.0f - s->p.vel_damping; a.contact = s->p.contact_on;
-    const double two_pi_f = 2.0 * M_PI * s->freq;
+    a.integrator = s->p.integrator;
     for (int32_t n = 0; n < nsteps; ++n) {
+        a.first_step = (s->step_count + n == 0) ? 1 : 0;
         if (s->actuated) {
             const double t = (double)(s->step_count + n) * (double)s->p.dt;
             a.s_n = (float)std::sin(two_pi_f * t);
@@ -666,7 +701,8 @@ ms_status ms_get_info(const ms_sim *s, ms_info_t *out)
     out->n_slots = s->n_slots; out->n_back_slots = s->n_back_slots; out->device_bytes = s->device_bytes;
     out->step_count = s->step_count; out->stability_bound = s->stability;
     out->max_fwd_degree = s->max_fwd; out->max_back_degree = s->max_back;
-    out->kernel = s->kernel; out->n_tiles = s->n_tiles; out->max_tile_local = s->max_tile_local;
+    out->kernel = s->persistent ? ms::kKernelPersistent : s->kernel;
+    out->n_tiles = s->n_tiles; out->max_tile_local = s->max_tile_local;
     return MS_OK;
 }
 

@@ -156,6 +156,44 @@ __global__ void k_sc_table(const long long *counter, int nsteps, double dt, doub
 
 __global__ void k_advance(long long *counter, int nsteps) { *counter += nsteps; }
 
+__global__ void k_sc_table_from(long long n0, int nsteps, double dt, double two_pi_f, float2 *out)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nsteps) return;
+    double s, c;
+    sincos(two_pi_f * ((double)(n0 + n) * dt), &s, &c);
+    out[n] = make_float2((float)s, (float)c);
+}
+
+// All steps of one small system in one CTA (the robot step, block mode).
+__global__ void __launch_bounds__(kBatchThreads) k_persistent(const Records rec, const Env env, float4 *st, int n,
+                                                              const float2 *sc, int nsteps, int *err)
+{
+    extern __shared__ float4 smem[];
+    float4 *xs = smem, *vs = smem + n, *fs = smem + 2 * n;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < n; i += kBatchThreads) { xs[i] = st[2 * i]; vs[i] = st[2 * i + 1]; }
+    __syncthreads();
+    for (int step = 0; step < nsteps; ++step) {
+        const float2 t = sc ? __ldg(&sc[step]) : make_float2(0.f, 0.f);
+        for (int i = tid; i < n; i += kBatchThreads) fs[i] = robot_force(rec, 0, i, xs, vs, t.x, t.y);
+        __syncthreads();
+        for (int i = tid; i < n; i += kBatchThreads) {
+            float4 x = xs[i], v = vs[i];
+            robot_integrate(env, x, v, fs[i]);
+            xs[i] = x; vs[i] = v;
+        }
+        __syncthreads();
+    }
+    bool bad = false;
+    for (int i = tid; i < n; i += kBatchThreads) {
+        const float4 x = xs[i], v = vs[i];
+        st[2 * i] = x; st[2 * i + 1] = v;
+        bad |= !isfinite(x.x + x.y + x.z + v.x + v.y + v.z);
+    }
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(err, kErrNonFinite);
+}
+
 // Centre-of-mass x travel of every robot from the global state (one CTA per robot).
 __global__ void k_com_travel(const RobotDev *robots, const float4 *st, float *travel)
 {
@@ -380,7 +418,7 @@ BatchArgs batch_args(msb_batch *b, int nsteps)
     BatchArgs a{};
     a.robots = b->robots; a.items = b->items; a.wlist = b->wlist; a.n_items = (int)b->h_items.size(); a.queue = b->queue;
     a.st = b->st;
-    a.rec = Records{b->slice, b->f_nbr, b->f_kl, b->f_c, b->f_ab, b->b_ent};
+    a.rec = Records{b->slice, b->f_nbr, b->f_kl, b->f_c, b->f_ab, b->b_ent, 0.f};
     a.env = make_env(b->p);
     a.sc = b->sc; a.nsteps = nsteps;
     a.warp_cap = b->warp_cap; a.travel = b->travel; a.err = b->err;
@@ -407,6 +445,23 @@ namespace ms {
 void launch_sc_table(const long long *counter, int nsteps, double dt, double two_pi_f, float2 *out, cudaStream_t s)
 {
     if (nsteps > 0) k_sc_table<<<(nsteps + 255) / 256, 256, 0, s>>>(counter, nsteps, dt, two_pi_f, out);
+}
+
+void launch_sc_table_from(long long n0, int nsteps, double dt, double two_pi_f, float2 *out, cudaStream_t s)
+{
+    if (nsteps > 0) k_sc_table_from<<<(nsteps + 255) / 256, 256, 0, s>>>(n0, nsteps, dt, two_pi_f, out);
+}
+
+cudaError_t launch_persistent(const Records &rec, const Env &env, float4 *st, int n, const float2 *sc, int nsteps,
+                              int *err, cudaStream_t s)
+{
+    if (n <= 0 || nsteps <= 0) return cudaSuccess;
+    if (n > kMaxRobotMasses) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)n * 3 * sizeof(float4);
+    cudaError_t e = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_persistent<<<1, kBatchThreads, smem, s>>>(rec, env, st, n, sc, nsteps, err);
+    return cudaGetLastError();
 }
 
 ms_status build_voxels(const msb_voxel_spec *spec, int n_robots, const int32_t *dims, const uint8_t *materials,

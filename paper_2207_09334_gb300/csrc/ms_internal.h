@@ -45,6 +45,7 @@ constexpr int kMaxFwdDegree = 31;
 // Kernels of the single-system step.
 constexpr int kKernelGather = 1;   // one thread per mass, sliced-ELL rows + back references
 constexpr int kKernelTiled = 2;    // CTA per tile of masses, state + halo in shared memory
+constexpr int kKernelPersistent = 3; // small systems: all steps in one CTA, state in shared memory
 constexpr int kTileMasses = 512;   // masses per tile (= threads per CTA)
 constexpr int kTileMaxLocal = 2048; // tile members + halo that fit the CTA's shared memory (24 B each)
 constexpr int kTileGroup = 3;      // spring slots per pipeline stage (one bulk copy per array)
@@ -72,7 +73,7 @@ struct StepArgs {
     const int32_t *halo;
     int n_tiles;
     int tile_local;      // max members + halo over the tiles (shared-memory entries)
-    int tiled;
+    int tiled;           // 1: tiled layout
     int *err;            // non-finite flag (sticky)
     int N;
     float c_uniform;
@@ -80,6 +81,8 @@ struct StepArgs {
     float k_c, mu, keep; // keep = 1 - vel_damping
     float s_n, c_n;      // sin, cos of 2 pi f t_n
     int contact;
+    int integrator;      // 0 symplectic Euler, 1 forward Euler, 2 position Verlet
+    int first_step;      // 1 on the first step since creation (Verlet's eq. 5)
 };
 
 // Launchers (ms_step.cu).

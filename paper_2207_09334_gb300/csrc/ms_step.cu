@@ -60,7 +60,8 @@ __device__ __forceinline__ void spring_term_packed(const float4 xi, const float4
 }
 
 // Gravity, external force, ground contact (penalty normal force, Coulomb
-// impulse clamp), global damping and the symplectic Euler update of mass i.
+// impulse clamp), global damping and the update of mass i: symplectic Euler
+// (default), forward Euler (eq. 4) or position Verlet (eq. 5-6).
 template <bool HAS_FEXT>
 __device__ __forceinline__ void integrate_mass(const StepArgs &a, int i, const float4 xi, const float4 vi,
                                                float fx, float fy, float fz, float4 &xn, float4 &vn)
@@ -87,8 +88,24 @@ __device__ __forceinline__ void integrate_mass(const StepArgs &a, int i, const f
     }
     vx *= a.keep; vy *= a.keep; vz *= a.keep;
     vn = make_float4(vx, vy, vz, 0.f);
-    xn = make_float4(xi.x + a.dt * vx, xi.y + a.dt * vy, xi.z + a.dt * vz, w);
-    if (!isfinite(xn.x + xn.y + xn.z + vx + vy + vz)) atomicOr(a.err, kErrNonFinite);
+    if (a.integrator == 1) {
+        // forward Euler (eq. 4): the position moves with the velocity at t_n
+        xn = make_float4(xi.x + a.dt * vi.x, xi.y + a.dt * vi.y, xi.z + a.dt * vi.z, w);
+    } else if (a.integrator == 2) {
+        // position Verlet (eq. 5-6) in velocity form.  With v_n = (x_n - x_{n-1})/dt,
+        // eq. 6 is x_{n+1} = x_n + dt (v_n + dt f/m) and eq. 5 the same with dt/2
+        // in the inner product, so v_{n+1} = v_n + h dt f/m (h = 1/2 on the first
+        // step, 1 after) and x_{n+1} = x_n + dt v_{n+1}: no difference of
+        // positions is formed, so no precision is lost to cancellation.
+        const float h = a.first_step ? 0.5f : 1.0f;
+        const float ax = fx * w + a.gx, ay = fy * w + a.gy, az = fz * w + a.gz;
+        vn = make_float4(vi.x + h * a.dt * ax, vi.y + h * a.dt * ay, vi.z + h * a.dt * az, 0.f);
+        xn = make_float4(xi.x + a.dt * vn.x, xi.y + a.dt * vn.y, xi.z + a.dt * vn.z, w);
+    } else {
+        // symplectic Euler: the position moves with the updated velocity
+        xn = make_float4(xi.x + a.dt * vx, xi.y + a.dt * vy, xi.z + a.dt * vz, w);
+    }
+    if (!isfinite(xn.x + xn.y + xn.z + vn.x + vn.y + vn.z)) atomicOr(a.err, kErrNonFinite);
 }
 
 template <bool HAS_C, bool HAS_ACT, bool HAS_FEXT>
@@ -270,14 +287,15 @@ __global__ void __launch_bounds__(kTileMasses) k_step_tiled(const StepArgs a)
     float fx = 0.f, fy = 0.f, fz = 0.f;
     for (unsigned g = 0; g < ngroups; ++g) {
         const unsigned p = g % kTileStages;
-        if (!mbar_wait(&bar[p], (g / kTileStages) & 1u)) give_up = 1;
+        const bool late = !mbar_wait(&bar[p], (g / kTileStages) & 1u);
+        if (late) give_up = 1;              // the stage never landed: its contents are not used
         const unsigned char *st = stage_ptr(p);
         const uint16_t *snbr = reinterpret_cast<const uint16_t *>(st);
         const float2 *skl = reinterpret_cast<const float2 *>(st + SL::nbr);
         const float *sc = reinterpret_cast<const float *>(st + SL::nbr + SL::kl);
         const float2 *sab = reinterpret_cast<const float2 *>(st + SL::nbr + SL::kl + SL::c);
         const unsigned ns = min((unsigned)kTileGroup, nslots - g * kTileGroup);
-        if (active) {
+        if (active && !late) {
 #pragma unroll
             for (unsigned u = 0; u < (unsigned)kTileGroup; ++u) {
                 if (u < ns) {

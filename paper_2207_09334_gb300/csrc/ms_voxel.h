@@ -69,9 +69,10 @@ struct Records {
     const uint4 *slice;
     const int32_t *f_nbr;
     const float2 *f_kl;
-    const float *f_c;
-    const float2 *f_ab;
+    const float *f_c;      // or nullptr: every spring has c_uniform
+    const float2 *f_ab;    // or nullptr: passive springs
     const uint32_t *b_ent;
+    float c_uniform;
 };
 
 // Hooke + dashpot term (eq. 2), the same arithmetic as the single-system step.
@@ -102,9 +103,9 @@ __device__ __forceinline__ float4 robot_force(const Records &a, int slice_base, 
         int j = __ldg(&a.f_nbr[r]);
         j = (j < 0) ? i : j;
         const float2 kl = __ldg(&a.f_kl[r]);
-        const float2 ab = __ldg(&a.f_ab[r]);
+        const float2 ab = a.f_ab ? __ldg(&a.f_ab[r]) : make_float2(0.f, 0.f);
         const float L = kl.y * (1.0f + (ab.x * s_n + ab.y * c_n));
-        vox_spring(xi, vi, xs[j], vs[j], kl.x, L, __ldg(&a.f_c[r]), fx, fy, fz);
+        vox_spring(xi, vi, xs[j], vs[j], kl.x, L, a.f_c ? __ldg(&a.f_c[r]) : a.c_uniform, fx, fy, fz);
     }
     unsigned q = meta.y + lane;
     for (unsigned s = 0; s < blen; ++s, q += 32u) {
@@ -116,9 +117,9 @@ __device__ __forceinline__ float4 robot_force(const Records &a, int slice_base, 
             rr = __ldg(&a.slice[slice_base + (o >> 5)].x) + (e >> kOwnerBits) * 32u + ((unsigned)o & 31u);
         }
         const float2 kl = __ldg(&a.f_kl[rr]);
-        const float2 ab = __ldg(&a.f_ab[rr]);
+        const float2 ab = a.f_ab ? __ldg(&a.f_ab[rr]) : make_float2(0.f, 0.f);
         const float L = kl.y * (1.0f + (ab.x * s_n + ab.y * c_n));
-        vox_spring(xi, vi, xs[o], vs[o], kl.x, L, __ldg(&a.f_c[rr]), fx, fy, fz);
+        vox_spring(xi, vi, xs[o], vs[o], kl.x, L, a.f_c ? __ldg(&a.f_c[rr]) : a.c_uniform, fx, fy, fz);
     }
     return make_float4(fx, fy, fz, 0.f);
 }
@@ -156,5 +157,16 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 #endif  // __CUDACC__
+
+#ifdef __CUDACC__
+// Persistent single-system run (ms_batch.cu): all nsteps steps of one system
+// of at most kMaxRobotMasses masses in one CTA, state in shared memory,
+// read from and written back to st (2 float4 per mass).  sc holds (sin, cos)
+// of 2 pi f t_n for the nsteps steps, or is nullptr for passive springs.
+cudaError_t launch_persistent(const Records &rec, const Env &env, float4 *st, int n, const float2 *sc,
+                              int nsteps, int *err, cudaStream_t s);
+// (sin, cos)(two_pi_f * (n0 + n) * dt) for n < nsteps.
+void launch_sc_table_from(long long n0, int nsteps, double dt, double two_pi_f, float2 *out, cudaStream_t s);
+#endif
 
 }  // namespace ms

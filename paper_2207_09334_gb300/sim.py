@@ -18,12 +18,16 @@ __all__ = ["Sim", "make_params", "torch_allocator"]
 
 
 ORDERS = {None: 0, False: 0, "auto": 0, True: 1, "morton": 1, "caller": 2}
-KERNELS = {None: 0, "auto": 0, "gather": 1, "tiled": 2}
+KERNELS = {None: 0, "auto": 0, "gather": 1, "tiled": 2, "persistent": 3}
 
 
-def make_params(params: dict, reorder=None, strict_stability: bool = False, kernel=None) -> MsParams:
+INTEGRATORS = {"symplectic_euler": 0, "forward_euler": 1, "verlet": 2}
+
+
+def make_params(params: dict, reorder=None, strict_stability: bool = False, kernel=None,
+                integrator="symplectic_euler") -> MsParams:
     """reorder: None/False = library default, True/"morton", or "caller";
-    kernel: None/"auto", "gather" or "tiled"."""
+    kernel: None/"auto", "gather", "tiled" or "persistent"."""
     p = MsParams()
     p.dt = float(params["dt"])
     for a in range(3):
@@ -32,7 +36,7 @@ def make_params(params: dict, reorder=None, strict_stability: bool = False, kern
     p.mu = float(params.get("mu", 0.0))
     p.vel_damping = float(params.get("vel_damping", 0.0))
     p.contact_on = 1 if params.get("contact", False) else 0
-    p.integrator = 0
+    p.integrator = INTEGRATORS[integrator] if isinstance(integrator, str) else int(integrator)
     p.strict_stability = 1 if strict_stability else 0
     p.reorder = ORDERS[reorder]
     p.kernel = KERNELS[kernel]
@@ -96,7 +100,8 @@ class Sim:
     """
 
     def __init__(self, system: dict, params: dict, reorder=None, stream=None,
-                 use_torch_allocator: bool = True, strict_stability: bool = False, kernel=None):
+                 use_torch_allocator: bool = True, strict_stability: bool = False, kernel=None,
+                 integrator="symplectic_euler"):
         lib = _lib.load()
         self._lib = lib
         x = _f32(system["x"], (-1, 3)); N = x.shape[0]
@@ -117,7 +122,7 @@ class Sim:
         L0 = system.get("L0")
         L0 = None if L0 is None else _f32(L0, (S,))
         self.N, self.S = N, S
-        self._params = make_params(params, reorder, strict_stability, kernel)
+        self._params = make_params(params, reorder, strict_stability, kernel, integrator)
         self._alloc = torch_allocator() if use_torch_allocator else None
         self.stream = _stream_handle(stream)
         handle = C.c_void_p()

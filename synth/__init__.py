@@ -266,3 +266,51 @@ def surrogate_designs(n: int, seed: int = 4, side: int = 8):
         mat, _ = random_voxel_design(rng, (side, side, side))
         out[r] = mat
     return out
+
+
+# ---------------------------------------------------------------------------
+# Quasi-uniform lattice (Generating a Lattice: Mitchell's best-candidate
+# sampling -- each new vertex is the best of `candidates` random points, the
+# one whose k nearest existing vertices are farthest away)
+# ---------------------------------------------------------------------------
+
+def best_candidate_points(n: int, box=(1.0, 1.0, 1.0), candidates: int = 100, k_nearest: int = 1,
+                          seed: int = 0):
+    """n points in the box [0, box) by best-candidate sampling.  The score of
+    a candidate is the distance to its k-th nearest accepted point."""
+    rng = np.random.default_rng(seed)
+    box = np.asarray(box, np.float64)
+    pts = np.empty((n, 3))
+    pts[0] = rng.random(3) * box
+    for q in range(1, n):
+        cand = rng.random((candidates, 3)) * box
+        d = np.sqrt(((cand[:, None, :] - pts[None, :q, :]) ** 2).sum(axis=2))
+        kk = min(k_nearest, q)
+        score = np.partition(d, kk - 1, axis=1)[:, kk - 1]
+        pts[q] = cand[int(np.argmax(score))]
+    return pts
+
+
+def quasi_uniform_lattice(n: int = 2000, box=(0.1, 0.1, 0.1), cutoff_factor: float = 1.6,
+                          max_degree: int = 26, seed: int = 0, m: float = 1e-3, k: float = 1e4,
+                          c: float = 0.05, candidates: int = 100):
+    """Irregular spring network on best-candidate points: every pair closer than
+    cutoff_factor x (the mean nearest-neighbour distance) is linked, keeping at
+    most max_degree shortest springs per node.  Rest lengths are the initial
+    distances (rounded to float32)."""
+    pts = best_candidate_points(n, box, candidates=candidates, seed=seed)
+    d = np.sqrt(((pts[:, None, :] - pts[None, :, :]) ** 2).sum(axis=2))
+    np.fill_diagonal(d, np.inf)
+    nn = d.min(axis=1).mean()
+    cutoff = cutoff_factor * nn
+    keep = np.zeros_like(d, dtype=bool)
+    for i in range(n):
+        cand = np.flatnonzero(d[i] < cutoff)
+        cand = cand[np.argsort(d[i, cand])][:max_degree]
+        keep[i, cand] = True
+    keep &= keep.T                                   # mutual: both ends within their degree cap
+    iu, ju = np.nonzero(np.triu(keep, 1))
+    ij = np.stack([iu, ju], axis=1).astype(np.int32)
+    x = pts.astype(np.float32)
+    L0 = np.sqrt(((x[ij[:, 1]].astype(np.float64) - x[ij[:, 0]]) ** 2).sum(axis=1)).astype(np.float32)
+    return _system(x, ij, L0, m, k, c)

@@ -207,3 +207,66 @@ def test_autograd_function_and_batch_forward(ms):
         pop.run(300)
         travel = pop.com_travel()
     np.testing.assert_allclose(loss.detach().cpu().numpy(), travel, rtol=0, atol=2e-6)
+
+
+def _fd_components(ora, mat, phase, logk, params, nsteps, comps, eps=1e-6, seed=None):
+    out = []
+    for which, v in comps:
+        arr = (phase if which == 0 else logk).astype(np.float64).ravel().copy()
+        vals = []
+        for sgn in (1, -1):
+            a = arr.copy(); a[v] += sgn * eps
+            ph = a.reshape(mat.shape) if which == 0 else phase.astype(np.float64)
+            lk = a.reshape(mat.shape) if which == 1 else logk.astype(np.float64)
+            vals.append(oracle_loss(ora, mat, ph, lk, params, nsteps, seed))
+        out.append((vals[0] - vals[1]) / (2 * eps))
+    return np.array(out)
+
+
+def test_adjoint_on_a_robot_larger_than_the_block(ms, ora):
+    """A 6x6x6 robot (343 masses, more than the 256 threads of the CTA, so
+    each thread carries several masses and voxels): smooth loss (no contact,
+    no gravity) over 300 steps, FD on a sample of components within 1e-3."""
+    rng = np.random.default_rng(41)
+    mat = rng.integers(1, 4, size=(6, 6, 6)).astype(np.uint8)
+    phase = rng.uniform(0, 2 * np.pi, size=mat.shape).astype(np.float32)
+    logk = (base_logk(mat) + rng.normal(0, 0.1, size=mat.shape)).astype(np.float32)
+    params = synth.voxel_params(contact=False, mu=0.0, g=(0.0, 0.0, 0.0))
+    nsteps = 300
+    seed = rng.standard_normal((343, 3)).astype(np.float32)
+    with ms.Adjoint([mat], synth.VOXEL_MATERIALS, synth.VOXEL_FREQ, synth.VOXEL_EDGE, synth.VOXEL_MASS,
+                    params, checkpoint_every=64, max_steps=nsteps) as adj:
+        assert adj.n_masses == 343
+        loss, gp, gk = adj.gradients(nsteps, phase, logk, seed_x=seed)
+    occ = np.flatnonzero(mat.ravel() > 0)
+    pick = rng.choice(occ, size=8, replace=False)
+    comps = [(w, int(v)) for v in pick for w in (0, 1) if not (w == 0 and mat.ravel()[v] != 3)]
+    fd = _fd_components(ora, mat, phase, logk, params, nsteps, comps, seed=seed)
+    g = np.array([(gp if w == 0 else gk)[v] for w, v in comps])
+    scale = np.abs(fd).max()
+    assert np.all(np.abs(g - fd) <= 1e-3 * np.maximum(np.abs(fd), 1e-2 * scale)), list(zip(comps, g, fd))
+
+
+def test_adjoint_with_contact_on_a_larger_robot_200_steps(ms, ora):
+    """The same size with ground contact and friction over 200 steps: FD-
+    consistent components (FD unchanged between eps 1e-5 and 1e-6) match
+    within 1e-3."""
+    rng = np.random.default_rng(43)
+    mat, phase = synth.random_voxel_design(rng, (6, 6, 6))
+    logk = base_logk(mat)
+    params = synth.voxel_params()
+    with ms.Adjoint([mat], synth.VOXEL_MATERIALS, synth.VOXEL_FREQ, synth.VOXEL_EDGE, synth.VOXEL_MASS,
+                    params, checkpoint_every=50, max_steps=200) as adj:
+        loss, gp, gk = adj.gradients(200, phase, logk)
+    occ = np.flatnonzero(mat.ravel() > 0)
+    pick = rng.choice(occ, size=min(10, occ.size), replace=False)
+    comps = [(w, int(v)) for v in pick for w in (0, 1) if not (w == 0 and mat.ravel()[v] != 3)]
+    f6 = _fd_components(ora, mat, phase, logk, params, 200, comps, eps=1e-6)
+    f5 = _fd_components(ora, mat, phase, logk, params, 200, comps, eps=1e-5)
+    g = np.array([(gp if w == 0 else gk)[v] for w, v in comps])
+    scale = np.abs(f6).max()
+    den = np.maximum(np.abs(f6), 1e-2 * scale)
+    consistent = np.abs(f5 - f6) <= 1e-3 * den
+    assert consistent.sum() >= len(comps) // 2
+    bad = consistent & (np.abs(g - f6) > 1e-3 * den)
+    assert not bad.any(), list(zip(comps, g, f6, consistent))

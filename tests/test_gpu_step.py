@@ -42,10 +42,12 @@ def body_size(s):
     return float(np.ptp(np.asarray(s["x"], np.float64), axis=0).max())
 
 
-KERNELS = ["gather", "tiled"]
+KERNELS = ["gather", "tiled", "persistent"]
 
 
 def gpu_run(ms, s, p, n, reorder=None, chunks=1, kernel=None):
+    if kernel == "persistent" and (s["x"].shape[0] > 4096 or s.get("fext") is not None):
+        pytest.skip("the persistent kernel takes at most 4096 masses and no external force")
     with ms.Sim(s, p, reorder=reorder, kernel=kernel) as sim:
         done = 0
         for q in range(chunks):
@@ -72,7 +74,8 @@ def test_hand_worked_steps_on_gpu(ms):
         np.testing.assert_allclose(v, case["v_out"], rtol=2e-6, atol=1e-6, err_msg=case["name"])
 
 
-@pytest.mark.parametrize("kernel,reorder", [("gather", "caller"), ("gather", "morton"), ("tiled", "morton"), ("tiled", "caller")])
+@pytest.mark.parametrize("kernel,reorder", [("gather", "caller"), ("gather", "morton"), ("tiled", "morton"),
+                                            ("tiled", "caller"), ("persistent", None)])
 def test_soft_cube_contact_free_1000_steps(ms, ora, kernel, reorder):
     s = synth.soft_cube()
     p = synth.soft_cube_params(contact=False)
@@ -260,3 +263,36 @@ def test_empty_spring_set_is_free_fall(ms, kernel):
     g = np.float32(-9.81); dt = np.float32(1e-3)
     assert abs(v[0, 2] - 100 * dt * g) < 1e-4
     assert abs(x[0, 0] - (0.0 + 100 * dt * 0.5)) < 1e-6
+
+
+@pytest.mark.parametrize("kernel", ["gather", "tiled"])
+@pytest.mark.parametrize("integ", ["forward_euler", "verlet"])
+def test_other_integrators_match_oracle(ms, ora, kernel, integ):
+    """The paper's forward Euler (eq. 4) and position Verlet (eq. 5-6) on a
+    small soft lattice without contact.  Forward Euler amplifies every mode by
+    sqrt(1 + (omega dt)^2) per step, so the lattice is soft enough that the top
+    mode has omega dt ~ 0.05 (growth below 1.5x over the run)."""
+    s = synth.soft_cube(n=6, k=1e2, c=0.01)
+    rng = np.random.default_rng(9)
+    s["x"] += (2e-4 * rng.standard_normal(s["x"].shape)).astype(np.float32)
+    p = synth.params(dt=2e-5, g=(0, 0, -9.81))
+    with ms.Sim(s, p, kernel=kernel, integrator=integ) as sim:
+        sim.step(150); sim.step(150)
+        xg, _ = sim.get_state()
+    xo, _ = ora.run(s, f32p(p), 300, integrator=integ)
+    err = np.abs(xg - xo).max()
+    assert err <= 1e-5 * body_size(s), (err, 1e-5 * body_size(s))
+
+
+@pytest.mark.parametrize("kernel", ["gather", "tiled", "persistent"])
+def test_quasi_uniform_irregular_lattice(ms, ora, kernel):
+    """An irregular network (best-candidate points, degree 2..16, no lattice
+    directions): the general-graph path, dropped onto the ground."""
+    s = synth.quasi_uniform_lattice(1500, box=(0.1, 0.1, 0.1), seed=1)
+    s["x"][:, 2] += np.float32(0.002)
+    s["v"][:] = np.array([0.1, 0.0, -0.3], np.float32)
+    p = synth.soft_cube_params(contact=True)
+    xg, _ = gpu_run(ms, s, p, 200, kernel=kernel)
+    xo, _ = ora.run(s, f32p(p), 200)
+    err = np.abs(xg - xo).max()
+    assert err <= 1e-4 * body_size(s), (err, 1e-4 * body_size(s))

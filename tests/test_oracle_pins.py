@@ -396,3 +396,22 @@ def test_voxel_expansion_single_and_pair(ora):
     assert s2["x"].shape[0] == 12 and s2["ij"].shape[0] == 56
     assert abs(s2["m"].sum() - 0.06) < 1e-15
     assert s2["x"][:, 2].min() == 0.0
+
+
+def test_best_candidate_points_are_spread():
+    """Best-candidate sampling keeps points apart: its smallest nearest-neighbour
+    distance is several times that of uniform random points of the same count."""
+    n = 400
+    p = synth.best_candidate_points(n, seed=3)
+    r = np.random.default_rng(3).random((n, 3))
+    def min_nn(a):
+        d = np.sqrt(((a[:, None] - a[None]) ** 2).sum(-1)); np.fill_diagonal(d, np.inf)
+        return d.min()
+    assert min_nn(p) > 3 * min_nn(r)
+
+
+def test_quasi_uniform_lattice_shape():
+    s = synth.quasi_uniform_lattice(600, seed=2)
+    deg = np.bincount(s["ij"].ravel(), minlength=600)
+    assert deg.max() <= 26 and deg.min() >= 1
+    assert np.all(s["ij"][:, 0] < s["ij"][:, 1])
