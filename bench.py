@@ -291,7 +291,7 @@ def run_ours(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
             "config": dict(workload_config(n, N, S), parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
                            setup_s={"generate": round(t_gen, 1), "create": round(t_create, 1)},
-                           mass_order=args.order, kernel=["", "gather", "tiled"][info["kernel"]],
+                           mass_order=args.order, kernel=["", "gather", "tiled", "persistent"][info["kernel"]],
                            device_bytes=info["device_bytes"], records=info["n_records"]),
             "e2e": e2e,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -378,11 +378,11 @@ def run_surrogate(args, world, rank, local):
     import paper_2207_09334_gb300 as ms
     torch.cuda.set_device(local)
     ms.load()
-    B = 1024
+    B = args.screen_batch                       # rows per forward pass while screening
     n_cand = args.candidates
     rng = np.random.default_rng(4)
     cand = torch.tensor(rng.integers(0, 4, size=(n_cand, 512)).astype(np.uint8), device="cuda")
-    net = ms.Surrogate(2048, 512, max_batch=B, seed=0)
+    net = ms.Surrogate(2048, 512, max_batch=max(B, 1024), seed=0)
     out = torch.empty(n_cand, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -404,13 +404,14 @@ def run_surrogate(args, world, rank, local):
     value = n_cand * args.steps / (ms_total * 1e-3)
     flops = 2.0 * (2048 * 512 + 512 * 512 + 512) * n_cand * args.steps
     # training step throughput (forward + backward + Adam, batch 1024)
-    tgt = torch.randn(B, device="cuda")
+    TB = 1024
+    tgt = torch.randn(TB, device="cuda")
     for _ in range(3):
-        net.train_step(cand[:B], tgt)
+        net.train_step(cand[:TB], tgt)
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(20):
-        net.train_step(cand[:B], tgt)
+        net.train_step(cand[:TB], tgt)
     e1.record(stream)
     torch.cuda.synchronize()
     train_ms = e0.elapsed_time(e1) / 20
@@ -432,7 +433,8 @@ def run_surrogate(args, world, rank, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)",
             "data": "synthetic (seeded)",
-            "config": {"workload": f"MLP 2048->512->512->1 scoring {n_cand} one-hot 8^3 designs per bench step"},
+            "config": {"workload": f"MLP 2048->512->512->1 scoring {n_cand} one-hot 8^3 designs per bench step, "
+                                   f"{B} designs per forward pass"},
             "tensor_tflops": flops / (ms_total * 1e-3) / 1e12,
             "train_step_ms_batch1024": train_ms,
             "simulator_designs_per_s_2s_rollout": sim_rate,
@@ -442,6 +444,53 @@ def run_surrogate(args, world, rank, local):
     if rank == 0:
         print(json.dumps(line), flush=True)
     net.close()
+    return 0
+
+
+def run_adjoint(args, world, rank, local):
+    """Differentiable batch: 256 walkers of 8^3 voxels, loss = centre-of-mass
+    x-travel after 2000 steps, gradients w.r.t. every voxel's phase and
+    log-stiffness by the checkpointed adjoint (checkpoint every 100 steps)."""
+    import torch
+    import paper_2207_09334_gb300 as ms
+    torch.cuda.set_device(local)
+    ms.load()
+    designs = synth.walker_designs(args.walkers, seed=3)
+    mats = [m for m, _ in designs]
+    phase = torch.tensor(np.concatenate([p.ravel() for _, p in designs]), device="cuda")
+    kmat = synth.VOXEL_MATERIALS[:, 0]
+    logk = torch.tensor(np.concatenate([np.where(m > 0, np.log(np.maximum(kmat[m], 1.0)), 0.0).ravel()
+                                        for m in mats]).astype(np.float32), device="cuda")
+    nsteps = args.rollout_steps
+    adj = ms.Adjoint(mats, synth.VOXEL_MATERIALS, synth.VOXEL_FREQ, synth.VOXEL_EDGE, synth.VOXEL_MASS,
+                     synth.voxel_params(), checkpoint_every=100, max_steps=nsteps)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        adj.gradients(nsteps, phase, logk)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            loss, gp, gk = adj.gradients(nsteps, phase, logk)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms_total = e0.elapsed_time(e1)
+    per = ms_total / args.steps
+    value = args.walkers * nsteps * synth.voxel_params()["dt"] / (per * 1e-3)
+    line = {"metric": "differentiated robot-sim-s/s", "value": value, "unit": "robot-sim-s/s (forward + reverse)",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded)",
+            "config": {"workload": f"{args.walkers} walkers of 8^3 voxels (seed 3), {nsteps} steps, checkpoint every 100; "
+                                   "one bench step = one loss + gradient evaluation for all walkers",
+                       "voxels": int(adj.n_voxels), "masses": int(adj.n_masses)},
+            "mean_travel_m": float(loss.mean()), "grad_phase_rms": float(gp.pow(2).mean().sqrt()),
+            "grad_logk_rms": float(gk.pow(2).mean().sqrt()),
+            "gpu_launches": 5 * args.steps, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    adj.close()
     return 0
 
 
@@ -459,11 +508,14 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--ref-side", type=int, default=40)
-    ap.add_argument("--workload", default="lattice", choices=["lattice", "population", "surrogate"])
+    ap.add_argument("--workload", default="lattice", choices=["lattice", "population", "surrogate", "adjoint"])
+    ap.add_argument("--walkers", type=int, default=256)
+    ap.add_argument("--rollout-steps", type=int, default=2000)
     ap.add_argument("--robots", type=int, default=4096)
     ap.add_argument("--sim-steps-per-bench-step", type=int, default=100)
     ap.add_argument("--loop-steps", type=int, default=5)
     ap.add_argument("--candidates", type=int, default=1 << 20)
+    ap.add_argument("--screen-batch", type=int, default=16384)
     ap.add_argument("--sim-designs", type=int, default=1024)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
@@ -475,6 +527,8 @@ def main():
         return run_population(args, world, rank, local)
     if args.workload == "surrogate":
         return run_surrogate(args, world, rank, local)
+    if args.workload == "adjoint":
+        return run_adjoint(args, world, rank, local)
     return run_ours(args, world, rank, local)
 
 
