@@ -215,11 +215,14 @@ def run_ours(args, world, rank, local):
     n = args.n
     t0 = time.perf_counter()
     s, p = lattice_workload(n)
+    if args.integrator in ("verlet", "rk4"):
+        p = dict(p, mu=0.0, vel_damping=0.0)   # contact is off: the same physics
+    launches_per_step = 4 if args.integrator == "rk4" else 1
     N, S = s["x"].shape[0], s["ij"].shape[0]
     t_gen = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
-    sim = ms.Sim(s, p, reorder=args.order, kernel=args.kernel, stream=stream)
+    sim = ms.Sim(s, p, reorder=args.order, kernel=args.kernel, stream=stream, integrator=args.integrator)
     torch.cuda.synchronize()
     t_create = time.perf_counter() - t0
     info = sim.info()
@@ -276,10 +279,11 @@ def run_ours(args, world, rank, local):
 
     hbm, hbm_kind = peaks()
     alg_bytes = BYTES_PER_MASS * N + BYTES_PER_SPRING * S
-    kern_ms = statistics.mean(per)
+    kern_ms = statistics.mean(per) / launches_per_step
     achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
     kname = "k_step_tiled" if info["kernel"] == 2 else "k_step"
-    tr = kernel_traffic(os.path.join(ROOT, "paper_2207_09334_gb300", "csrc", "ms_step.cu"), kname)
+    tr = kernel_traffic(os.path.join(ROOT, "paper_2207_09334_gb300", "csrc", "ms_step.cu"), kname) \
+        if args.integrator == "symplectic_euler" else None      # the capture is of the default scheme
     traffic = None
     if tr is not None:
         traffic = tr["dram_bytes_per_launch_at_256"] * (N + S) / tr["elements_at_256"] if n != 256 else tr["dram_bytes_per_launch_at_256"]
@@ -292,13 +296,14 @@ def run_ours(args, world, rank, local):
             "config": dict(workload_config(n, N, S), parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
                            setup_s={"generate": round(t_gen, 1), "create": round(t_create, 1)},
                            mass_order=args.order, kernel=["", "gather", "tiled", "persistent"][info["kernel"]],
+                           integrator=args.integrator,
                            device_bytes=info["device_bytes"], records=info["n_records"]),
             "e2e": e2e,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
                          "kernel": kname, "peak_kind": f"{hbm_kind} (hbm_gbs)",
                          "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": kern_ms},
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * launches_per_step,
             "clocks": clocks}
     if cpu is not None:
         line["cpu_baseline"] = cpu
@@ -503,6 +508,9 @@ def main():
     ap.add_argument("--n", type=int, default=256, help="lattice side (256 = the benchmark workload)")
     ap.add_argument("--order", default="auto", choices=["auto", "morton", "caller"], help="internal mass order")
     ap.add_argument("--kernel", default="auto", choices=["auto", "gather", "tiled"])
+    ap.add_argument("--integrator", default="symplectic_euler",
+                    choices=["symplectic_euler", "forward_euler", "verlet", "rk4"],
+                    help="lattice workload: step scheme (rk4 = 4 stage launches per step)")
     ap.add_argument("--e2e-sim-steps", type=int, default=200)
     ap.add_argument("--e2e-iters", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -60,8 +60,11 @@ typedef struct {
     int32_t contact_on;     /* 1 = ground contact active */
     int32_t integrator;     /* 0 = symplectic Euler (default); 1 = forward Euler (eq. 4); 2 = position
                                Verlet (eq. 5-6; no friction, no global damping; the dashpots see
-                               v_n = (x_n - x_{n-1})/dt).  ms_create only; populations and the
-                               adjoint take 0. */
+                               v_n = (x_n - x_{n-1})/dt); 3 = classical RK4 (eq. 7-8 with the step
+                               size in every stage; no friction, no global damping; four force
+                               evaluations per step, stage q at t_n + c_q dt, c = 0, 1/2, 1/2, 1;
+                               3 x 32 B per mass of extra device memory).  ms_create only;
+                               populations and the adjoint take 0. */
     int32_t strict_stability; /* 1 = ms_create fails with MS_ERR_UNSTABLE if the bound below exceeds 4 */
     int32_t reorder;        /* mass order: 0 = library default (Morton for the tiled kernel, caller
                                order for the gather kernel), 1 = Morton order by initial position,
@@ -169,6 +172,41 @@ ms_status ms_set_state(ms_sim *sim, const float *x, const float *v, int32_t on_d
 /* ms_sync -- wait for the object's stream; returns MS_ERR_NONFINITE if a
  * step produced a non-finite value since creation (sticky), else MS_OK. */
 ms_status ms_sync(ms_sim *sim);
+
+/*
+ * ms_energy -- energy of the current state at t_n = step_count dt, reduced on
+ * the device (paper: Energy Conservation Tests; eq. 2's Hooke term):
+ *   out[0] kinetic        sum_i m_i |v_i|^2 / 2
+ *   out[1] elastic        sum_s k_s (l_s - L_s(t_n))^2 / 2, L_s actuated as in ms_set_actuation
+ *   out[2] gravitational  -sum_i m_i g . x_i           (anchored masses included)
+ *   out[3] ground         sum_i k_c z_i^2 / 2 over z_i < 0, when contact is on
+ * out: 4 doubles; on_device = 1: a device pointer (8-byte aligned), the call
+ * is asynchronous on the object's stream and copies nothing to the host, so
+ * a run can record the energy every few steps; 0: host pointer, the call
+ * synchronises.  The reduction order is fixed: the result is bit-identical
+ * between calls on the same state.  FP32 terms, FP32 warp sums, FP64 sums
+ * above.  Parallel springs merged into one record contribute that record's
+ * energy, which differs from the sum over the separate springs by
+ * sum_v k_v (L_v - L)^2 / 2 (L the merged rest length), a term independent
+ * of the positions.  The first call allocates a small reduction buffer
+ * (4 doubles per 512 masses).
+ */
+ms_status ms_energy(ms_sim *sim, double *out, int32_t on_device);
+
+/*
+ * ms_trace_set -- record the positions of n_masses chosen masses (caller
+ * indices) after every subsequent step, for at most `capacity` steps, into a
+ * device buffer of the object (e.g. a cantilever tip; paper: cantilever
+ * experiments).  Replaces any previous trace and restarts the count; n_masses
+ * = 0 switches tracing off and frees the buffer.  Steps beyond capacity are
+ * not recorded.  Not available with the persistent kernel (MS_ERR_ARG).
+ * Each recorded step adds one small kernel launch.
+ * ms_trace_get -- *n_steps (if not NULL) receives the number of recorded
+ * steps; out (if not NULL) receives n_steps x n_masses x 3 floats, step-major,
+ * masses in the order given to ms_trace_set.  on_device as for ms_get_state.
+ */
+ms_status ms_trace_set(ms_sim *sim, const int32_t *masses, int32_t n_masses, int32_t capacity);
+ms_status ms_trace_get(ms_sim *sim, float *out, int32_t *n_steps, int32_t on_device);
 
 /* ms_get_info -- sizes and diagnostics of the object. */
 ms_status ms_get_info(const ms_sim *sim, ms_info_t *out);

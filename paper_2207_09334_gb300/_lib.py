@@ -68,6 +68,9 @@ SIGNATURES = {
     "ms_set_state": (C.c_int, [VP, VP, VP, I32]),
     "ms_sync": (C.c_int, [VP]),
     "ms_get_info": (C.c_int, [VP, C.POINTER(MsInfo)]),
+    "ms_energy": (C.c_int, [VP, VP, I32]),
+    "ms_trace_set": (C.c_int, [VP, VP, I32, I32]),
+    "ms_trace_get": (C.c_int, [VP, VP, VP, I32]),
     "ms_destroy": (C.c_int, [VP]),
     "ms_last_error": (C.c_char_p, []),
     "msb_create": (C.c_int, [C.POINTER(MsParams), C.POINTER(MsbVoxelSpec), I32, VP, VP, VP, VP,

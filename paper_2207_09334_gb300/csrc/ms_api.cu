@@ -16,6 +16,7 @@
 #include "ms_voxel.h"
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -99,6 +100,14 @@ struct ms_sim {
     float *stage = nullptr;             // (N,3)*2 floats for host copies
     int *err = nullptr;
     float c_uniform = 0.f;
+    // instrumentation
+    double *e_partial = nullptr;        // 4 doubles per energy block, then the 4 results
+    int32_t *tr_idx = nullptr;          // traced masses (internal order)
+    float *tr_buf = nullptr;            // tr_cap steps x tr_n masses x 3
+    int tr_n = 0, tr_cap = 0, tr_count = 0;
+    // RK4: two stage states and the slope accumulator (2 float4 per mass each)
+    float4 *rk_y[2] = {nullptr, nullptr};
+    float4 *rk_acc = nullptr;
 
     double freq = 0.0;
     bool actuated = false;
@@ -120,6 +129,18 @@ struct ms_sim {
             device_bytes += (int64_t)bytes;
         }
         return ptr;
+    }
+    void dev_free(void *ptr)
+    {
+        for (size_t q = 0; q < allocs.size(); ++q)
+            if (allocs[q].ptr == ptr) {
+                if (stream) cudaStreamSynchronize(stream); else cudaDeviceSynchronize();
+                if (custom_alloc) alloc.free(ptr, allocs[q].bytes, stream, alloc.ctx);
+                else cudaFree(ptr);
+                device_bytes -= (int64_t)allocs[q].bytes;
+                allocs.erase(allocs.begin() + (long)q);
+                return;
+            }
     }
     void release()
     {
@@ -179,9 +200,10 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
     if (N < 1 || N >= (1 << ms::kOwnerBits)) return fail(MS_ERR_ARG, "N must be in [1, 2^27)");
     if (S < 0 || (S > 0 && (!ij || !k))) return fail(MS_ERR_ARG, "S < 0, or ij / k missing");
     if (!(p->dt > 0.f) || !std::isfinite(p->dt)) return fail(MS_ERR_ARG, "dt must be positive and finite");
-    if (p->integrator < 0 || p->integrator > 2) return fail(MS_ERR_ARG, "integrator must be 0 (symplectic Euler), 1 (forward Euler) or 2 (Verlet)");
-    if (p->integrator == 2 && (p->mu > 0.f || p->vel_damping != 0.f))
-        return fail(MS_ERR_ARG, "the Verlet integrator takes no friction and no global damping");
+    if (p->integrator < 0 || p->integrator > 3)
+        return fail(MS_ERR_ARG, "integrator must be 0 (symplectic Euler), 1 (forward Euler), 2 (Verlet) or 3 (RK4)");
+    if (p->integrator >= 2 && (p->mu > 0.f || p->vel_damping != 0.f))
+        return fail(MS_ERR_ARG, "the Verlet and RK4 integrators take no friction and no global damping");
     if (!(p->vel_damping >= 0.f && p->vel_damping < 1.f)) return fail(MS_ERR_ARG, "vel_damping must be in [0, 1)");
     if (p->contact_on && !(p->k_c >= 0.f && p->mu >= 0.f)) return fail(MS_ERR_ARG, "k_c and mu must be >= 0");
     if (!c && !(c_uniform >= 0.f && std::isfinite(c_uniform))) return fail(MS_ERR_ARG, "c_uniform must be >= 0");
@@ -512,7 +534,10 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
     for (int32_t i = 0; i < N; ++i) {
         const int32_t cidx = s->perm[i];
         const bool anchored = fixed && fixed[cidx];
-        const float w = anchored ? -1.0f : (float)(1.0 / (double)mass[cidx]);
+        // free: 1/m; anchored: -m (a mass of zero or less is stored as the
+        // smallest negative normal, so the sign still marks the anchor)
+        const float w = !anchored ? (float)(1.0 / (double)mass[cidx])
+                        : (mass[cidx] > 0.f && std::isfinite(mass[cidx])) ? -mass[cidx] : -FLT_MIN;
         hs[2 * (size_t)i] = make_float4(x0[3 * cidx], x0[3 * cidx + 1], x0[3 * cidx + 2], w);
         hs[2 * (size_t)i + 1] = anchored ? make_float4(0.f, 0.f, 0.f, 0.f)
                                          : make_float4(v0[3 * cidx], v0[3 * cidx + 1], v0[3 * cidx + 2], 0.f);
@@ -551,6 +576,11 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
     }
     if (s->permuted && (st = upload(s, &s->d_perm, s->perm.data(), N)) != MS_OK) return st;
     if ((st = upload<float>(s, &s->stage, nullptr, (size_t)N * 6)) != MS_OK) return st;
+    if (p->integrator == 3) {
+        if ((st = upload<float4>(s, &s->rk_y[0], nullptr, 2 * (size_t)N)) != MS_OK) return st;
+        if ((st = upload<float4>(s, &s->rk_y[1], nullptr, 2 * (size_t)N)) != MS_OK) return st;
+        if ((st = upload<float4>(s, &s->rk_acc, nullptr, 2 * (size_t)N)) != MS_OK) return st;
+    }
     if ((st = upload<int>(s, &s->err, nullptr, 1)) != MS_OK) return st;
     MS_CUDA_TRY(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
     // host arrays must outlive the asynchronous copies
@@ -635,17 +665,41 @@ ms_status ms_step(ms_sim *s, int32_t nsteps)
     a.dt = s->p.dt; a.gx = s->p.g[0]; a.gy = s->p.g[1]; a.gz = s->p.g[2];
     a.k_c = s->p.k_c; a.mu = s->p.mu; a.keep = 1.0f - s->p.vel_damping; a.contact = s->p.contact_on;
     a.integrator = s->p.integrator;
+    a.rk_acc = s->rk_acc;
     for (int32_t n = 0; n < nsteps; ++n) {
         a.first_step = (s->step_count + n == 0) ? 1 : 0;
-        if (s->actuated) {
-            const double t = (double)(s->step_count + n) * (double)s->p.dt;
-            a.s_n = (float)std::sin(two_pi_f * t);
-            a.c_n = (float)std::cos(two_pi_f * t);
+        const double t = (double)(s->step_count + n) * (double)s->p.dt;
+        if (s->p.integrator == 3) {
+            // four stage launches: Y_0 = Y_n -> rk_y[0] -> rk_y[1] -> rk_y[0] -> Y_{n+1};
+            // stage q sees the actuation at t_n + c_q dt, c = 0, 1/2, 1/2, 1
+            static const double c_stage[4] = {0.0, 0.5, 0.5, 1.0};
+            a.rk_base = s->st[s->cur];
+            for (int q = 0; q < 4; ++q) {
+                if (s->actuated) {
+                    const double tq = t + c_stage[q] * (double)s->p.dt;
+                    a.s_n = (float)std::sin(two_pi_f * tq);
+                    a.c_n = (float)std::cos(two_pi_f * tq);
+                }
+                a.rk_stage = q;
+                a.st = q == 0 ? s->st[s->cur] : s->rk_y[(q - 1) & 1];
+                a.sto = q == 3 ? s->st[s->cur ^ 1] : s->rk_y[q & 1];
+                MS_CUDA_TRY(ms::launch_step(a, s->stream));
+            }
+        } else {
+            if (s->actuated) {
+                a.s_n = (float)std::sin(two_pi_f * t);
+                a.c_n = (float)std::cos(two_pi_f * t);
+            }
+            a.st = s->st[s->cur];
+            a.sto = s->st[s->cur ^ 1];
+            MS_CUDA_TRY(ms::launch_step(a, s->stream));
         }
-        a.st = s->st[s->cur];
-        a.sto = s->st[s->cur ^ 1];
-        MS_CUDA_TRY(ms::launch_step(a, s->stream));
         s->cur ^= 1;
+        if (s->tr_n > 0 && s->tr_count < s->tr_cap) {
+            MS_CUDA_TRY(ms::launch_trace(s->st[s->cur], s->tr_idx, s->tr_n,
+                                         s->tr_buf + (size_t)s->tr_count * s->tr_n * 3, s->stream));
+            ++s->tr_count;
+        }
     }
     s->step_count += nsteps;
     return MS_OK;
@@ -691,6 +745,68 @@ ms_status ms_sync(ms_sim *s)
     MS_CUDA_TRY(cudaMemcpy(&flag, s->err, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag & ms::kErrTimeout) return fail(MS_ERR_TIMEOUT, "a bounded device-side wait gave up (bulk copy never completed)");
     if (flag & ms::kErrNonFinite) return fail(MS_ERR_NONFINITE, "a step produced a non-finite position or velocity");
+    return MS_OK;
+}
+
+ms_status ms_energy(ms_sim *s, double *out, int32_t on_device)
+{
+    if (!s || !out) return fail(MS_ERR_ARG, "sim or out is NULL");
+    ms::EnergyArgs a{};
+    a.st = s->st[s->cur]; a.slice = s->slice; a.f_nbr = s->f_nbr; a.t_nbr = s->t_nbr;
+    a.tiles = s->tiles; a.halo = s->halo; a.f_kl = s->f_kl; a.f_ab = s->actuated ? s->f_ab : nullptr;
+    a.N = s->N; a.n_tiles = s->n_tiles; a.tiled = s->kernel == ms::kKernelTiled;
+    if (s->actuated) {
+        const double t = (double)s->step_count * (double)s->p.dt;
+        a.s_n = (float)std::sin(2.0 * M_PI * s->freq * t);
+        a.c_n = (float)std::cos(2.0 * M_PI * s->freq * t);
+    }
+    a.gx = s->p.g[0]; a.gy = s->p.g[1]; a.gz = s->p.g[2]; a.k_c = s->p.k_c; a.contact = s->p.contact_on;
+    if (!s->e_partial) {
+        ms_status st = upload<double>(s, &s->e_partial, nullptr, 4 * (size_t)ms::energy_blocks(a) + 4);
+        if (st != MS_OK) return st;
+    }
+    a.partial = s->e_partial;
+    double *res = s->e_partial + 4 * (size_t)ms::energy_blocks(a);
+    MS_CUDA_TRY(ms::launch_energy(a, on_device ? out : res, s->stream));
+    if (on_device) return MS_OK;
+    MS_CUDA_TRY(cudaMemcpyAsync(out, res, 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    MS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return MS_OK;
+}
+
+ms_status ms_trace_set(ms_sim *s, const int32_t *masses, int32_t n_masses, int32_t capacity)
+{
+    if (!s) return fail(MS_ERR_ARG, "sim is NULL");
+    if (n_masses < 0 || capacity < 0 || (n_masses > 0 && (!masses || capacity < 1)))
+        return fail(MS_ERR_ARG, "need n_masses >= 0, and masses and capacity >= 1 when n_masses > 0");
+    if (n_masses > 0 && s->persistent) return fail(MS_ERR_ARG, "the persistent kernel records no per-step trace");
+    if ((int64_t)n_masses * capacity * 3 >= ((int64_t)1 << 40)) return fail(MS_ERR_ARG, "trace too large");
+    std::vector<int32_t> idx(n_masses);
+    for (int32_t q = 0; q < n_masses; ++q) {
+        if (masses[q] < 0 || masses[q] >= s->N) return fail(MS_ERR_ARG, "trace mass index out of range");
+        idx[q] = s->iperm[masses[q]];
+    }
+    if (s->tr_idx) { s->dev_free(s->tr_idx); s->tr_idx = nullptr; }
+    if (s->tr_buf) { s->dev_free(s->tr_buf); s->tr_buf = nullptr; }
+    s->tr_n = 0; s->tr_cap = 0; s->tr_count = 0;
+    if (n_masses == 0) return MS_OK;
+    ms_status st = upload(s, &s->tr_idx, idx.data(), (size_t)n_masses);
+    if (st != MS_OK) return st;
+    if ((st = upload<float>(s, &s->tr_buf, nullptr, (size_t)n_masses * capacity * 3)) != MS_OK) return st;
+    MS_CUDA_TRY(cudaStreamSynchronize(s->stream));      // idx is a host temporary
+    s->tr_n = n_masses; s->tr_cap = capacity;
+    return MS_OK;
+}
+
+ms_status ms_trace_get(ms_sim *s, float *out, int32_t *n_steps, int32_t on_device)
+{
+    if (!s) return fail(MS_ERR_ARG, "sim is NULL");
+    if (n_steps) *n_steps = s->tr_count;
+    if (!out || s->tr_count == 0) return MS_OK;
+    const size_t bytes = sizeof(float) * 3 * (size_t)s->tr_n * s->tr_count;
+    MS_CUDA_TRY(cudaMemcpyAsync(out, s->tr_buf, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                s->stream));
+    if (!on_device) MS_CUDA_TRY(cudaStreamSynchronize(s->stream));
     return MS_OK;
 }
 

@@ -81,9 +81,34 @@ struct StepArgs {
     float k_c, mu, keep; // keep = 1 - vel_damping
     float s_n, c_n;      // sin, cos of 2 pi f t_n
     int contact;
-    int integrator;      // 0 symplectic Euler, 1 forward Euler, 2 position Verlet
+    int integrator;      // 0 symplectic Euler, 1 forward Euler, 2 position Verlet, 3 RK4
     int first_step;      // 1 on the first step since creation (Verlet's eq. 5)
+    const float4 *rk_base;   // RK4: the state Y_n of the step (2 float4 per mass)
+    float4 *rk_acc;          // RK4: weighted sum of the stage slopes (2 float4 per mass)
+    int rk_stage;            // RK4: stage 0..3
 };
+
+// Energy reduction (ms_instr.cu) over either record layout.
+struct EnergyArgs {
+    const float4 *st;
+    const uint4 *slice;      // gather layout
+    const int32_t *f_nbr;
+    const uint16_t *t_nbr;   // tiled layout
+    const int4 *tiles;
+    const int32_t *halo;
+    const float2 *f_kl;
+    const float2 *f_ab;      // or nullptr (passive)
+    double *partial;         // 4 doubles per block (energy_blocks)
+    int N, n_tiles, tiled;
+    float s_n, c_n;          // sin, cos of 2 pi f t_n
+    float gx, gy, gz, k_c;
+    int contact;
+};
+int energy_blocks(const EnergyArgs &a);
+// out (device): kinetic, elastic, gravitational, ground-penalty energy (FP64)
+cudaError_t launch_energy(const EnergyArgs &a, double *out, cudaStream_t s);
+// out[3 q + c] = x[idx[q]][c] for q < n
+cudaError_t launch_trace(const float4 *st, const int32_t *idx, int n, float *out, cudaStream_t s);
 
 // Launchers (ms_step.cu).
 cudaError_t launch_step(const StepArgs &a, cudaStream_t st);

@@ -61,14 +61,15 @@ __device__ __forceinline__ void spring_term_packed(const float4 xi, const float4
 
 // Gravity, external force, ground contact (penalty normal force, Coulomb
 // impulse clamp), global damping and the update of mass i: symplectic Euler
-// (default), forward Euler (eq. 4) or position Verlet (eq. 5-6).
-template <bool HAS_FEXT>
+// (default), forward Euler (eq. 4), position Verlet (eq. 5-6) or one stage
+// of classical RK4 (eq. 7-8).
+template <bool HAS_FEXT, bool RK4>
 __device__ __forceinline__ void integrate_mass(const StepArgs &a, int i, const float4 xi, const float4 vi,
                                                float fx, float fy, float fz, float4 &xn, float4 &vn)
 {
     xn = xi;
     vn = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float w = xi.w;                  // 1/m, or -1 for an anchored mass
+    const float w = xi.w;                  // 1/m, or -m for an anchored mass
     if (w < 0.0f) return;
     if (HAS_FEXT) {
         const float4 fe = __ldg(&a.fext[i]);
@@ -77,6 +78,36 @@ __device__ __forceinline__ void integrate_mass(const StepArgs &a, int i, const f
     const bool pen = a.contact && xi.z < 0.0f;
     float Fn = 0.f;
     if (pen) { Fn = -a.k_c * xi.z; fz += Fn; }
+    if (RK4) {
+        // RK4 stage q on d/dt (x, v) = (v, f/m): (xi, vi) is the stage state
+        // Y_q, its slope is K_q = (vi, f/m).  The slopes are summed with
+        // weights 1, 2, 2, 1 into rk_acc; stages 0-2 write the next stage
+        // state Y_n + c h K_q (c = 1/2, 1/2, 1), stage 3 writes
+        // Y_{n+1} = Y_n + h/6 (K_0 + 2 K_1 + 2 K_2 + K_3).
+        const int q = a.rk_stage;
+        const float ax = fx * w + a.gx, ay = fy * w + a.gy, az = fz * w + a.gz;
+        const float4 bx = __ldg(&a.rk_base[2 * i]), bv = __ldg(&a.rk_base[2 * i + 1]);
+        float4 sx = make_float4(vi.x, vi.y, vi.z, 0.f), sv = make_float4(ax, ay, az, 0.f);
+        if (q > 0) {
+            const float wq = q == 3 ? 1.0f : 2.0f;
+            const float4 px = a.rk_acc[2 * i], pv = a.rk_acc[2 * i + 1];
+            sx = make_float4(fmaf(wq, sx.x, px.x), fmaf(wq, sx.y, px.y), fmaf(wq, sx.z, px.z), 0.f);
+            sv = make_float4(fmaf(wq, sv.x, pv.x), fmaf(wq, sv.y, pv.y), fmaf(wq, sv.z, pv.z), 0.f);
+        }
+        if (q < 3) {
+            a.rk_acc[2 * i] = sx;
+            a.rk_acc[2 * i + 1] = sv;
+            const float c = q == 2 ? a.dt : 0.5f * a.dt;
+            xn = make_float4(fmaf(c, vi.x, bx.x), fmaf(c, vi.y, bx.y), fmaf(c, vi.z, bx.z), w);
+            vn = make_float4(fmaf(c, ax, bv.x), fmaf(c, ay, bv.y), fmaf(c, az, bv.z), 0.f);
+        } else {
+            const float h6 = a.dt / 6.0f;
+            xn = make_float4(fmaf(h6, sx.x, bx.x), fmaf(h6, sx.y, bx.y), fmaf(h6, sx.z, bx.z), w);
+            vn = make_float4(fmaf(h6, sv.x, bv.x), fmaf(h6, sv.y, bv.y), fmaf(h6, sv.z, bv.z), 0.f);
+        }
+        if (!isfinite(xn.x + xn.y + xn.z + vn.x + vn.y + vn.z)) atomicOr(a.err, kErrNonFinite);
+        return;
+    }
     float vx = vi.x + a.dt * (fx * w + a.gx);
     float vy = vi.y + a.dt * (fy * w + a.gy);
     float vz = vi.z + a.dt * (fz * w + a.gz);
@@ -108,7 +139,7 @@ __device__ __forceinline__ void integrate_mass(const StepArgs &a, int i, const f
     if (!isfinite(xn.x + xn.y + xn.z + vn.x + vn.y + vn.z)) atomicOr(a.err, kErrNonFinite);
 }
 
-template <bool HAS_C, bool HAS_ACT, bool HAS_FEXT>
+template <bool HAS_C, bool HAS_ACT, bool HAS_FEXT, bool RK4>
 __global__ void __launch_bounds__(256) k_step(const StepArgs a)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -151,7 +182,7 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a)
     }
 
     float4 xn, vn;
-    integrate_mass<HAS_FEXT>(a, i, xi, vi, fx, fy, fz, xn, vn);
+    integrate_mass<HAS_FEXT, RK4>(a, i, xi, vi, fx, fy, fz, xn, vn);
     a.sto[2 * i] = xn;
     a.sto[2 * i + 1] = vn;
 }
@@ -226,7 +257,7 @@ struct StageLayout {
 
 }  // namespace
 
-template <bool HAS_C, bool HAS_ACT, bool HAS_FEXT>
+template <bool HAS_C, bool HAS_ACT, bool HAS_FEXT, bool RK4>
 __global__ void __launch_bounds__(kTileMasses) k_step_tiled(const StepArgs a)
 {
     using SL = StageLayout<HAS_C, HAS_ACT>;
@@ -329,7 +360,7 @@ __global__ void __launch_bounds__(kTileMasses) k_step_tiled(const StepArgs a)
     if (!active) return;
     const int i = base + tid;
     float4 xn, vn;
-    integrate_mass<HAS_FEXT>(a, i, xi, vi, fx, fy, fz, xn, vn);
+    integrate_mass<HAS_FEXT, RK4>(a, i, xi, vi, fx, fy, fz, xn, vn);
     a.sto[2 * i] = xn;
     a.sto[2 * i + 1] = vn;
 }
@@ -340,19 +371,19 @@ size_t tiled_smem_bytes(int tile_local, bool has_c, bool has_act)
     return ((((size_t)tile_local * 24 + 127) & ~(size_t)127)) + (size_t)kTileStages * stage;
 }
 
-cudaError_t launch_step(const StepArgs &a, cudaStream_t st)
+template <bool RK4>
+cudaError_t launch_step_t(const StepArgs &a, cudaStream_t st)
 {
-    if (a.N <= 0) return cudaSuccess;
     const bool hc = a.f_c != nullptr, ha = a.f_ab != nullptr, hf = a.fext != nullptr;
     if (a.tiled) {
         const size_t smem = tiled_smem_bytes(a.tile_local, hc, ha);
         const int grid = a.n_tiles;
 #define MS_LAUNCH_T(C, A, F)                                                                        \
     do {                                                                                            \
-        cudaError_t e_ = cudaFuncSetAttribute(k_step_tiled<C, A, F>,                                \
+        cudaError_t e_ = cudaFuncSetAttribute(k_step_tiled<C, A, F, RK4>,                           \
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e_ != cudaSuccess) return e_;                                                           \
-        k_step_tiled<C, A, F><<<grid, kTileMasses, smem, st>>>(a);                                  \
+        k_step_tiled<C, A, F, RK4><<<grid, kTileMasses, smem, st>>>(a);                             \
     } while (0)
         if (hc) {
             if (ha) { if (hf) MS_LAUNCH_T(true, true, true); else MS_LAUNCH_T(true, true, false); }
@@ -366,7 +397,7 @@ cudaError_t launch_step(const StepArgs &a, cudaStream_t st)
     }
     const int bs = 256;
     const int grid = (a.N + bs - 1) / bs;
-#define MS_LAUNCH(C, A, F) k_step<C, A, F><<<grid, bs, 0, st>>>(a)
+#define MS_LAUNCH(C, A, F) k_step<C, A, F, RK4><<<grid, bs, 0, st>>>(a)
     if (hc) {
         if (ha) { if (hf) MS_LAUNCH(true, true, true); else MS_LAUNCH(true, true, false); }
         else    { if (hf) MS_LAUNCH(true, false, true); else MS_LAUNCH(true, false, false); }
@@ -376,6 +407,14 @@ cudaError_t launch_step(const StepArgs &a, cudaStream_t st)
     }
 #undef MS_LAUNCH
     return cudaGetLastError();
+}
+
+// RK4 stages run their own instantiations, so the other schemes' kernels
+// keep the register budget of the plain update.
+cudaError_t launch_step(const StepArgs &a, cudaStream_t st)
+{
+    if (a.N <= 0) return cudaSuccess;
+    return a.integrator == 3 ? launch_step_t<true>(a, st) : launch_step_t<false>(a, st);
 }
 
 __global__ void k_gather_state(const float4 *__restrict__ st, const int32_t *__restrict__ perm, int N,

@@ -21,7 +21,7 @@ ORDERS = {None: 0, False: 0, "auto": 0, True: 1, "morton": 1, "caller": 2}
 KERNELS = {None: 0, "auto": 0, "gather": 1, "tiled": 2, "persistent": 3}
 
 
-INTEGRATORS = {"symplectic_euler": 0, "forward_euler": 1, "verlet": 2}
+INTEGRATORS = {"symplectic_euler": 0, "forward_euler": 1, "verlet": 2, "rk4": 3}
 
 
 def make_params(params: dict, reorder=None, strict_stability: bool = False, kernel=None,
@@ -79,6 +79,11 @@ def torch_allocator() -> _TorchAllocator:
 def _f32(a, shape=None):
     a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
     return a if shape is None else a.reshape(shape)
+
+
+def _torch():
+    import torch
+    return torch
 
 
 def _ptr(a):
@@ -175,6 +180,37 @@ class Sim:
 
     def sync(self):
         check(self._lib.ms_sync(self.h))
+
+    def energy(self, out=None):
+        """(kinetic, elastic, gravitational, ground) energy of the current
+        state, reduced on the device.  With a CUDA float64 tensor `out` of 4
+        elements (e.g. a row of a preallocated trace) the result is written
+        there without a host copy or synchronisation; otherwise a tuple."""
+        if out is not None:
+            if not (hasattr(out, "is_cuda") and out.is_cuda and out.dtype == _torch().float64 and out.numel() >= 4
+                    and out.is_contiguous()):
+                raise ValueError("out must be a contiguous CUDA float64 tensor of at least 4 elements")
+            check(self._lib.ms_energy(self.h, C.c_void_p(out.data_ptr()), 1))
+            return out
+        e = np.empty(4, np.float64)
+        check(self._lib.ms_energy(self.h, _ptr(e), 0))
+        return tuple(float(q) for q in e)
+
+    def trace(self, masses, capacity: int):
+        """Record the positions of `masses` (caller indices) after each of the
+        next `capacity` steps; an empty list switches tracing off."""
+        idx = np.ascontiguousarray(np.asarray(masses, np.int32).ravel())
+        self._trace_n = int(idx.size)
+        check(self._lib.ms_trace_set(self.h, _ptr(idx) if idx.size else None, int(idx.size), int(capacity)))
+
+    def get_trace(self):
+        """(steps, len(masses), 3) float32 positions recorded since trace()."""
+        n = C.c_int32(0)
+        check(self._lib.ms_trace_get(self.h, None, C.byref(n), 0))
+        out = np.empty((n.value, getattr(self, "_trace_n", 0), 3), np.float32)
+        if n.value:
+            check(self._lib.ms_trace_get(self.h, _ptr(out), C.byref(n), 0))
+        return out
 
     def info(self) -> dict:
         inf = MsInfo()

@@ -266,7 +266,7 @@ def test_empty_spring_set_is_free_fall(ms, kernel):
 
 
 @pytest.mark.parametrize("kernel", ["gather", "tiled"])
-@pytest.mark.parametrize("integ", ["forward_euler", "verlet"])
+@pytest.mark.parametrize("integ", ["forward_euler", "verlet", "rk4"])
 def test_other_integrators_match_oracle(ms, ora, kernel, integ):
     """The paper's forward Euler (eq. 4) and position Verlet (eq. 5-6) on a
     small soft lattice without contact.  Forward Euler amplifies every mode by
@@ -296,3 +296,25 @@ def test_quasi_uniform_irregular_lattice(ms, ora, kernel):
     xo, _ = ora.run(s, f32p(p), 200)
     err = np.abs(xg - xo).max()
     assert err <= 1e-4 * body_size(s), (err, 1e-4 * body_size(s))
+
+
+@pytest.mark.parametrize("kernel", ["gather", "tiled"])
+def test_rk4_with_actuation_anchors_and_ground_contact(ms, ora, kernel):
+    """RK4 stages see the actuation at t_n + c dt and the penalty contact
+    (friction off, as RK4 takes no impulse clamp): actuated lattice with an
+    anchored layer, started partly below the ground."""
+    x, ij, L0 = synth.box_lattice(6, 5, 4, 0.01, origin=(0, 0, -0.002))
+    rng = np.random.default_rng(21)
+    S = ij.shape[0]; N = x.shape[0]
+    s = dict(x=x, v=(0.01 * rng.standard_normal((N, 3))).astype(np.float32),
+             m=rng.uniform(1e-3, 4e-3, N).astype(np.float32), fixed=(np.arange(N) < 6).astype(np.uint8), ij=ij,
+             k=rng.uniform(1e3, 1e4, S).astype(np.float32), c=rng.uniform(0, 0.1, S).astype(np.float32),
+             L0=L0, A=rng.uniform(0, 0.2, S).astype(np.float32),
+             phi=rng.uniform(0, 2 * np.pi, S).astype(np.float32), freq=5.0)
+    p = synth.params(dt=1e-4, g=(0, 0, -9.81), contact=True, k_c=1e4, mu=0.0)
+    with ms.Sim(s, p, kernel=kernel, integrator="rk4") as sim:
+        sim.step(300); sim.step(200)
+        xg, _ = sim.get_state()
+    xo, _ = ora.run(s, f32p(p), 500, integrator="rk4")
+    err = np.abs(xg - xo).max()
+    assert err <= 1e-5 * body_size(s), (err, 1e-5 * body_size(s))
