@@ -400,7 +400,9 @@ ms_status mlp_get_params(mlp_model *m, float *params, float *grads);
 /* load a batch: one-hot encode device materials [B][n_in/4] (ids 0..3), or copy bf16 inputs [B][n_in] */
 ms_status mlp_encode(mlp_model *m, const uint8_t *materials, int32_t B);
 ms_status mlp_set_input(mlp_model *m, const uint16_t *x_bf16, int32_t B);
-/* predictions of the loaded batch into device y [B] (may be NULL) */
+/* predictions of the loaded batch into device y [B] (may be NULL); inference only: the
+ * pre-activations and transposed activations that training needs are not stored
+ * (mlp_backward runs its own forward pass) */
 ms_status mlp_forward(mlp_model *m, int32_t B, float *y);
 /* forward + backward of the loaded batch against device target [B]; gradients kept in the model;
  * device loss [1] (may be NULL) */

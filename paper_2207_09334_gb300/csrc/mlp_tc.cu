@@ -3,15 +3,22 @@
 //
 // Every matrix product is C = A . B^T with A [M x K] and B [N x K] both
 // row-major bf16 (K-major), accumulated in fp32 in tensor memory:
-//   * TMA (cp.async.bulk.tensor, 128-byte swizzle) streams 128 x 64 tiles of
-//     A and B into a kStages-deep shared-memory ring guarded by mbarriers;
-//   * one thread issues tcgen05.mma (cta_group::1, kind::f16, M = 128,
-//     N = 128, K = 16 per instruction) into a 128 x 128 fp32 accumulator in
-//     TMEM and releases each stage with tcgen05.commit;
-//   * the four warps read the accumulator back with tcgen05.ld (warp w owns
-//     TMEM lanes 32w..32w+31 = rows) and apply the fused epilogue: plain fp32
-//     store, bias + GELU (forward), or GELU' (backward), writing row-major
-//     and transposed bf16 copies as the next product needs.
+//   * one CTA computes a 128 x BN tile of C (BN = 256 when N allows, else
+//     128) with four warps, specialised while the K loop runs:
+//       - a producer thread (warp 0) streams 128 x 64 tiles of A and BN x 64
+//         tiles of B by TMA (cp.async.bulk.tensor, 128-byte swizzle) into a
+//         kStages-deep shared-memory ring, refilling a stage as soon as its
+//         "empty" mbarrier says the MMAs that read it are done;
+//       - an MMA thread (warp 1) waits on each stage's "full" mbarrier and
+//         issues tcgen05.mma (cta_group::1, kind::f16, M = 128, N = BN,
+//         K = 16 per instruction) into a 128 x BN fp32 accumulator in TMEM,
+//         then tcgen05.commit to the stage's "empty" mbarrier;
+//     so loads run kStages tiles ahead and the MMAs are issued back to back;
+//   * the eight warps read the accumulator back with tcgen05.ld (warp w owns
+//     TMEM lanes 32(w mod 4)..+31 = rows, and half w / 4 of the columns) and
+//     apply the fused epilogue: plain fp32 store, bias + GELU (forward), or
+//     GELU' (backward), writing row-major and transposed bf16 copies as the
+//     next product needs.
 // Every wait is bounded by %globaltimer; on expiry the kernel records a
 // timeout in the error flag, stops issuing work and returns.
 #include <cuda.h>
@@ -30,10 +37,10 @@
 namespace ms {
 namespace {
 
-constexpr int kBM = 128, kBN = 128, kBK = 64;
+constexpr int kBM = 128, kBK = 64;
 constexpr int kStages = 4;
-constexpr int kGemmThreads = 128;
-constexpr uint32_t kTileBytes = kBM * kBK * 2;                  // 16 KB per operand tile
+constexpr int kGemmThreads = 256;                                // 8 warps: two per TMEM lane quarter
+constexpr uint32_t kTileBytes = kBM * kBK * 2;                  // 16 KB: one 128 x 64 bf16 box
 constexpr uint64_t kWaitNs = 2000000000ull;                       // 2 s
 
 enum Epi { EPI_F32 = 0, EPI_BIAS_GELU = 1, EPI_DGELU = 2 };
@@ -43,7 +50,7 @@ struct GemmArgs {
     int epi;
     float *C;                 // EPI_F32: [M][N] fp32
     const float *bias;        // EPI_BIAS_GELU: [N]
-    __nv_bfloat16 *Z;         // EPI_BIAS_GELU: pre-activation out [M][N]; EPI_DGELU: pre-activation in
+    __nv_bfloat16 *Z;         // EPI_BIAS_GELU: pre-activation out [M][N] (or nullptr); EPI_DGELU: pre-activation in
     __nv_bfloat16 *H;         // row-major out [M][N] (GELU(z) or dz)
     __nv_bfloat16 *Ht;        // transposed out [N][M] (or nullptr)
     int *err;
@@ -106,14 +113,16 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr)
     return d;
 }
 
-// instruction descriptor: D f32, A and B bf16, both K-major, M = 128, N = 128
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+// instruction descriptor: D f32, A and B bf16, both K-major, M = 128, N = BN
+template <int BN>
+__host__ __device__ constexpr uint32_t idesc() { return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24); }
 
+template <int BN>
 __device__ __forceinline__ void umma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate)
 {
     asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
-                 ::"r"(tmem), "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate) : "memory");
+                 ::"r"(tmem), "l"(a), "l"(b), "r"(idesc<BN>()), "r"(accumulate) : "memory");
 }
 
 __device__ __forceinline__ void umma_commit(uint64_t *bar)
@@ -128,21 +137,23 @@ __device__ __forceinline__ float gelu_grad(float z)
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.3989422804014327f * expf(-0.5f * z * z);
 }
 
+template <int BN>
 __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(const __grid_constant__ CUtensorMap mapA,
                                                           const __grid_constant__ CUtensorMap mapB, const GemmArgs g)
 {
+    constexpr uint32_t kStageBytes = kTileBytes * (1 + BN / kBM);   // A tile + BN/128 B boxes
     extern __shared__ __align__(1024) unsigned char dyn[];
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
     __shared__ uint32_t tmem_base;
     __shared__ int give_up;
-    // 1024-byte aligned ring of stages: A tile then B tile
+    // 1024-byte aligned ring of stages: A tile then the B tile (BN rows)
     unsigned char *ring = reinterpret_cast<unsigned char *>(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
     const int KT = g.K / kBK;
 
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_base)), "r"(kBN) : "memory");
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_base)), "r"(BN) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 32) {
@@ -157,29 +168,33 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(const __grid_constant_
     const uint32_t tmem = tmem_base;
 
     if (tid == 0) {
-        // producer and MMA issuer
-        auto load = [&](int kt) {
+        // producer: stage s is refilled once the MMAs of k-tile kt - kStages released it
+        for (int kt = 0; kt < KT; ++kt) {
             const int s = kt % kStages;
-            unsigned char *a = ring + (size_t)s * 2 * kTileBytes, *b = a + kTileBytes;
-            mbar_expect_tx(&full[s], 2 * kTileBytes);
+            if (kt >= kStages && !mbar_wait(&empty[s], ((kt / kStages) - 1) & 1)) {
+                give_up = 1;
+                atomicOr(g.err, kErrTimeout);
+                break;
+            }
+            unsigned char *a = ring + (size_t)s * kStageBytes;
+            mbar_expect_tx(&full[s], kStageBytes);
             tma_load_2d(a, &mapA, kt * kBK, m0, &full[s]);
-            tma_load_2d(b, &mapB, kt * kBK, n0, &full[s]);
-        };
-        for (int kt = 0; kt < KT && kt < kStages; ++kt) load(kt);
+#pragma unroll
+            for (int q = 0; q < BN / kBM; ++q)
+                tma_load_2d(a + kTileBytes * (1 + q), &mapB, kt * kBK, n0 + q * kBM, &full[s]);
+        }
+    } else if (tid == 32) {
+        // MMA issuer
         bool ok = true;
-        for (int kt = 0; kt < KT && ok; ++kt) {
+        for (int kt = 0; kt < KT; ++kt) {
             const int s = kt % kStages;
             if (!mbar_wait(&full[s], (kt / kStages) & 1)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a = saddr(ring + (size_t)s * 2 * kTileBytes), b = a + kTileBytes;
+            const uint32_t a = saddr(ring + (size_t)s * kStageBytes), b = a + kTileBytes;
 #pragma unroll
             for (int kk = 0; kk < kBK / 16; ++kk)
-                umma(tmem, sdesc(a + kk * 32), sdesc(b + kk * 32), (kt | kk) ? 1u : 0u);
+                umma<BN>(tmem, sdesc(a + kk * 32), sdesc(b + kk * 32), (kt | kk) ? 1u : 0u);
             umma_commit(&empty[s]);                        // stage s free once these MMAs have read it
-            if (kt + kStages < KT) {
-                if (!mbar_wait(&empty[s], (kt / kStages) & 1)) { ok = false; break; }
-                load(kt + kStages);
-            }
         }
         if (!ok) { give_up = 1; atomicOr(g.err, kErrTimeout); }
         umma_commit(&done);                                // accumulator complete
@@ -188,10 +203,11 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(const __grid_constant_
     const bool ok = !give_up && mbar_wait(&done, 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
-        const int row = m0 + warp * 32 + lane;
-        for (int c0 = 0; c0 < kBN; c0 += 32) {
+        const int quarter = warp & 3, half = warp >> 2;
+        const int row = m0 + quarter * 32 + lane;
+        for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 32) {
             uint32_t r[32];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
                          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
                          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
@@ -209,23 +225,32 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(const __grid_constant_
                                                                        __uint_as_float(r[q + 2]), __uint_as_float(r[q + 3]));
             } else {
                 __align__(16) __nv_bfloat16 hv[32], zv[32];
+                if (g.epi == EPI_BIAS_GELU) {
+                    // bias offsets are multiples of 128 floats by construction: float4 loads
+                    const float4 *b4 = reinterpret_cast<const float4 *>(g.bias + nb);
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const float acc = __uint_as_float(r[q]);
-                    float h;
-                    if (g.epi == EPI_BIAS_GELU) {
-                        const float z = acc + __ldg(&g.bias[nb + q]);
-                        zv[q] = __float2bfloat16(z);
-                        h = gelu(__bfloat162float(zv[q]));
-                    } else {
-                        h = acc * gelu_grad(__bfloat162float(g.Z[(size_t)row * g.N + nb + q]));
+                    for (int q4 = 0; q4 < 8; ++q4) {
+                        const float4 bq = __ldg(&b4[q4]);
+                        const float bb[4] = {bq.x, bq.y, bq.z, bq.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int q = 4 * q4 + e;
+                            zv[q] = __float2bfloat16(__uint_as_float(r[q]) + bb[e]);
+                            hv[q] = __float2bfloat16(gelu(__bfloat162float(zv[q])));
+                        }
                     }
-                    hv[q] = __float2bfloat16(h);
+                } else {
+                    const uint4 *zr = reinterpret_cast<const uint4 *>(g.Z + (size_t)row * g.N + nb);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) reinterpret_cast<uint4 *>(zv)[q] = zr[q];
+#pragma unroll
+                    for (int q = 0; q < 32; ++q)
+                        hv[q] = __float2bfloat16(__uint_as_float(r[q]) * gelu_grad(__bfloat162float(zv[q])));
                 }
                 uint4 *dh = reinterpret_cast<uint4 *>(g.H + (size_t)row * g.N + nb);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) dh[q] = reinterpret_cast<const uint4 *>(hv)[q];
-                if (g.epi == EPI_BIAS_GELU) {
+                if (g.epi == EPI_BIAS_GELU && g.Z) {        // pre-activation kept for the backward pass
                     uint4 *dz = reinterpret_cast<uint4 *>(g.Z + (size_t)row * g.N + nb);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) dz[q] = reinterpret_cast<const uint4 *>(zv)[q];
@@ -239,10 +264,11 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(const __grid_constant_
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
 }
 
-constexpr size_t kGemmSmem = (size_t)kStages * 2 * kTileBytes + 1024;
+template <int BN>
+constexpr size_t gemm_smem() { return (size_t)kStages * kTileBytes * (1 + BN / kBM) + 1024; }
 
 // ---- small kernels of the MLP -------------------------------------------
 
@@ -398,17 +424,25 @@ ms_status make_map(CUtensorMap *map, const void *ptr, int rows, int cols)
 ms_status gemm(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, const GemmArgs &proto,
                cudaStream_t st)
 {
-    if (M % kBM || N % kBN || K % kBK || M <= 0 || N <= 0 || K <= 0)
+    if (M % kBM || N % kBM || K % kBK || M <= 0 || N <= 0 || K <= 0)
         return fail(MS_ERR_ARG, "gemm: M and N must be multiples of 128 and K of 64");
     CUtensorMap ma, mb;
     ms_status s;
     if ((s = make_map(&ma, A, M, K)) != MS_OK) return s;
     if ((s = make_map(&mb, B, N, K)) != MS_OK) return s;
     static std::once_flag once;
-    std::call_once(once, [] { cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem); });
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(k_gemm_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<128>());
+        cudaFuncSetAttribute(k_gemm_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<256>());
+    });
     GemmArgs g = proto;
     g.M = M; g.N = N; g.K = K;
-    k_gemm_tc<<<dim3(N / kBN, M / kBM), kGemmThreads, kGemmSmem, st>>>(ma, mb, g);
+    // 128 x 256 tiles halve the A-tile traffic per FLOP; they need N % 256 == 0
+    // and enough tiles to fill the GPU
+    if (N % 256 == 0 && (size_t)(M / kBM) * (N / 256) >= 148)
+        k_gemm_tc<256><<<dim3(N / 256, M / kBM), kGemmThreads, gemm_smem<256>(), st>>>(ma, mb, g);
+    else
+        k_gemm_tc<128><<<dim3(N / kBM, M / kBM), kGemmThreads, gemm_smem<128>(), st>>>(ma, mb, g);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(MS_ERR_CUDA, std::string("gemm launch: ") + cudaGetErrorString(e));
     return MS_OK;
@@ -480,16 +514,18 @@ ms_status refresh_bf16(mlp_model *m)
     return MS_OK;
 }
 
-ms_status forward(mlp_model *m, int B)
+// keep: also store what the backward pass needs (Z1, Z2, H1^T)
+ms_status forward(mlp_model *m, int B, bool keep)
 {
     GemmArgs g{};
     g.err = m->err;
     // Z1 = X W1^T + b1, H1 = GELU(Z1) (and H1^T)
-    g.epi = EPI_BIAS_GELU; g.bias = m->P + m->off_b1; g.Z = m->Z1; g.H = m->H1; g.Ht = m->H1t;
+    g.epi = EPI_BIAS_GELU; g.bias = m->P + m->off_b1; g.Z = keep ? m->Z1 : nullptr; g.H = m->H1;
+    g.Ht = keep ? m->H1t : nullptr;
     ms_status s = gemm(m->X, m->W1b, B, m->n_h, m->n_in, g, m->stream);
     if (s != MS_OK) return s;
     // Z2 = H1 W2^T + b2, H2 = GELU(Z2)
-    g.bias = m->P + m->off_b2; g.Z = m->Z2; g.H = m->H2; g.Ht = nullptr;
+    g.bias = m->P + m->off_b2; g.Z = keep ? m->Z2 : nullptr; g.H = m->H2; g.Ht = nullptr;
     if ((s = gemm(m->H1, m->W2b, B, m->n_h, m->n_h, g, m->stream)) != MS_OK) return s;
     k_head<<<nblk((size_t)B * 32), 256, 0, m->stream>>>(m->H2, m->P + m->off_w3, m->P + m->off_b3, B, m->n_h, m->y);
     MLP_CUDA_TRY(cudaGetLastError());
@@ -546,7 +582,7 @@ ms_status mlp_create(int32_t n_in, int32_t n_hidden, int32_t max_batch, uint64_t
 {
     if (!out) return fail(MS_ERR_ARG, "out is NULL");
     *out = nullptr;
-    if (n_in <= 0 || n_hidden <= 0 || n_in % kBN || n_hidden % kBN || max_batch < kBM || max_batch % kBM)
+    if (n_in <= 0 || n_hidden <= 0 || n_in % kBM || n_hidden % kBM || max_batch < kBM || max_batch % kBM)
         return fail(MS_ERR_ARG, "n_in and n_hidden must be multiples of 128, max_batch a multiple of 128");
     if (alloc && (!alloc->alloc || !alloc->free)) return fail(MS_ERR_ARG, "allocator needs alloc and free");
     mlp_model *m = new (std::nothrow) mlp_model();
@@ -636,7 +672,7 @@ ms_status mlp_forward(mlp_model *m, int32_t B, float *y)
     if (!m) return fail(MS_ERR_ARG, "model is NULL");
     ms_status s = check_batch(m, B);
     if (s != MS_OK) return s;
-    if ((s = forward(m, B)) != MS_OK) return s;
+    if ((s = forward(m, B, false)) != MS_OK) return s;
     if (y) MLP_CUDA_TRY(cudaMemcpyAsync(y, m->y, sizeof(float) * B, cudaMemcpyDeviceToDevice, m->stream));
     return MS_OK;
 }
@@ -646,7 +682,7 @@ ms_status mlp_backward(mlp_model *m, const float *target, int32_t B, float *loss
     if (!m || !target) return fail(MS_ERR_ARG, "model and target are required");
     ms_status s = check_batch(m, B);
     if (s != MS_OK) return s;
-    if ((s = forward(m, B)) != MS_OK) return s;
+    if ((s = forward(m, B, true)) != MS_OK) return s;
     if ((s = backward(m, target, B)) != MS_OK) return s;
     if (loss) MLP_CUDA_TRY(cudaMemcpyAsync(loss, m->loss, sizeof(float), cudaMemcpyDeviceToDevice, m->stream));
     return MS_OK;

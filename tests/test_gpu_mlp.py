@@ -33,6 +33,23 @@ def test_gemm_matches_fp64(ms, M, N, K):
     assert err <= bound, (err, bound)
 
 
+@pytest.mark.parametrize("M,N,K", [(19456, 256, 192), (18944, 512, 1024)])
+def test_gemm_wide_tiles_match_fp64(ms, M, N, K):
+    """Problems with at least 148 tiles of 128 x 256 take the 256-wide tile
+    (two B boxes per stage, 256 TMEM columns); K = 192 is shorter than the
+    stage ring.  Checked on every 37th row against FP64."""
+    import torch
+    g = torch.Generator().manual_seed(M + N + K)
+    A = torch.randn(M, K, generator=g).bfloat16()
+    B = torch.randn(N, K, generator=g).bfloat16()
+    out = ms.gemm_bf16(A.cuda(), B.cuda()).double().cpu()
+    rows = torch.arange(0, M, 37)
+    ref = A[rows].double() @ B.double().T
+    err = (out[rows] - ref).abs().max().item()
+    bound = 1e-5 * (A[rows].double().abs() @ B.double().abs().T).max().item()
+    assert err <= bound, (err, bound)
+
+
 def _mlp_case(ms, B=256, n_in=2048, h=512, seed=1):
     import torch
     rng = np.random.default_rng(seed)
