@@ -39,7 +39,8 @@ namespace {
 
 constexpr int kBM = 128, kBK = 64;
 constexpr int kStages = 4;
-constexpr int kGemmThreads = 256;                                // 8 warps: two per TMEM lane quarter
+constexpr int kGemmThreads = 320;   // warp 0 loads, warp 1 issues MMAs, warps 2..9 run the epilogue
+constexpr int kEpiThreads = 256;
 constexpr uint32_t kTileBytes = kBM * kBK * 2;                  // 16 KB: one 128 x 64 bf16 box
 constexpr uint64_t kWaitNs = 2000000000ull;                       // 2 s
 
@@ -137,29 +138,89 @@ __device__ __forceinline__ float gelu_grad(float z)
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.3989422804014327f * expf(-0.5f * z * z);
 }
 
+// Epilogue of one 32-column chunk of a thread's row: r holds the fp32
+// accumulator C[row][nb .. nb + 31].
+__device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, const uint32_t (&r)[32], int row, int nb)
+{
+    if (g.epi == EPI_F32) {
+        float *dst = g.C + (size_t)row * g.N + nb;
+#pragma unroll
+        for (int q = 0; q < 32; q += 4)
+            *reinterpret_cast<float4 *>(dst + q) = make_float4(__uint_as_float(r[q]), __uint_as_float(r[q + 1]),
+                                                               __uint_as_float(r[q + 2]), __uint_as_float(r[q + 3]));
+        return;
+    }
+    __align__(16) __nv_bfloat16 hv[32], zv[32];
+    if (g.epi == EPI_BIAS_GELU) {
+        // bias offsets are multiples of 128 floats by construction: float4 loads
+        const float4 *b4 = reinterpret_cast<const float4 *>(g.bias + nb);
+#pragma unroll
+        for (int q4 = 0; q4 < 8; ++q4) {
+            const float4 bq = __ldg(&b4[q4]);
+            const float bb[4] = {bq.x, bq.y, bq.z, bq.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int q = 4 * q4 + e;
+                zv[q] = __float2bfloat16(__uint_as_float(r[q]) + bb[e]);
+                hv[q] = __float2bfloat16(gelu(__bfloat162float(zv[q])));
+            }
+        }
+    } else {
+        const uint4 *zr = reinterpret_cast<const uint4 *>(g.Z + (size_t)row * g.N + nb);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) reinterpret_cast<uint4 *>(zv)[q] = zr[q];
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+            hv[q] = __float2bfloat16(__uint_as_float(r[q]) * gelu_grad(__bfloat162float(zv[q])));
+    }
+    uint4 *dh = reinterpret_cast<uint4 *>(g.H + (size_t)row * g.N + nb);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dh[q] = reinterpret_cast<const uint4 *>(hv)[q];
+    if (g.epi == EPI_BIAS_GELU && g.Z) {                    // pre-activation kept for the backward pass
+        uint4 *dz = reinterpret_cast<uint4 *>(g.Z + (size_t)row * g.N + nb);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dz[q] = reinterpret_cast<const uint4 *>(zv)[q];
+    }
+    if (g.Ht)
+#pragma unroll
+        for (int q = 0; q < 32; ++q) g.Ht[(size_t)(nb + q) * g.M + row] = hv[q];
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
+}
+
+// Persistent tile loop.  Tiles are 128 x BN, numbered with N fastest (CTAs
+// that run at the same time share rows of A in L2); CTA c takes tiles c,
+// c + gridDim.x, ...  Warp 0 (one thread) loads, warp 1 (one thread) issues
+// the MMAs, warps 2..9 drain the accumulators.  Two accumulators of BN TMEM
+// columns alternate between tiles, so the epilogue of one tile overlaps the
+// main loop of the next:
+//   full[s] / empty[s]        shared-memory stage loaded / read by the MMAs
+//   acc_full[a] / acc_empty[a] accumulator a complete / drained by all 256
+//                              epilogue threads
 template <int BN>
-__global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(const __grid_constant__ CUtensorMap mapA,
-                                                          const __grid_constant__ CUtensorMap mapB, const GemmArgs g)
+__global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_tc(const __grid_constant__ CUtensorMap mapA,
+                                                             const __grid_constant__ CUtensorMap mapB, const GemmArgs g)
 {
     constexpr uint32_t kStageBytes = kTileBytes * (1 + BN / kBM);   // A tile + BN/128 B boxes
     extern __shared__ __align__(1024) unsigned char dyn[];
-    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_base;
-    __shared__ int give_up;
     // 1024-byte aligned ring of stages: A tile then the B tile (BN rows)
     unsigned char *ring = reinterpret_cast<unsigned char *>(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
+    const int tiles_n = g.N / BN, n_tiles = (g.M / kBM) * tiles_n;
     const int KT = g.K / kBK;
 
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_base)), "r"(BN) : "memory");
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_base)), "r"(2 * BN) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 32) {
         for (int s = 0; s < kStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-        mbar_init(&done, 1);
-        give_up = 0;
+        for (int a = 0; a < 2; ++a) { mbar_init(&acc_full[a], 1); mbar_init(&acc_empty[a], kEpiThreads); }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -167,104 +228,84 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(const __grid_constant_
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
 
-    if (tid == 0) {
-        // producer: stage s is refilled once the MMAs of k-tile kt - kStages released it
-        for (int kt = 0; kt < KT; ++kt) {
-            const int s = kt % kStages;
-            if (kt >= kStages && !mbar_wait(&empty[s], ((kt / kStages) - 1) & 1)) {
-                give_up = 1;
-                atomicOr(g.err, kErrTimeout);
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer: stage s is refilled once the MMAs of k-step it - kStages released it
+            unsigned it = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+                const int m0 = (tile / tiles_n) * kBM, n0 = (tile % tiles_n) * BN;
+                for (int kt = 0; kt < KT; ++kt, ++it) {
+                    const unsigned s = it % kStages;
+                    if (it >= (unsigned)kStages && !mbar_wait(&empty[s], ((it / kStages) - 1) & 1)) { ok = false; break; }
+                    unsigned char *a = ring + (size_t)s * kStageBytes;
+                    mbar_expect_tx(&full[s], kStageBytes);
+                    tma_load_2d(a, &mapA, kt * kBK, m0, &full[s]);
+#pragma unroll
+                    for (int q = 0; q < BN / kBM; ++q)
+                        tma_load_2d(a + kTileBytes * (1 + q), &mapB, kt * kBK, n0 + q * kBM, &full[s]);
+                }
+            }
+            if (!ok) atomicOr(g.err, kErrTimeout);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            unsigned it = 0, lt = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++lt) {
+                const unsigned acc = lt & 1u;
+                if (lt >= 2 && !mbar_wait(&acc_empty[acc], ((lt / 2) - 1) & 1)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + acc * BN;
+                for (int kt = 0; kt < KT; ++kt, ++it) {
+                    const unsigned s = it % kStages;
+                    if (!mbar_wait(&full[s], (it / kStages) & 1)) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a = saddr(ring + (size_t)s * kStageBytes), b = a + kTileBytes;
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 16; ++kk)
+                        umma<BN>(d, sdesc(a + kk * 32), sdesc(b + kk * 32), (kt | kk) ? 1u : 0u);
+                    umma_commit(&empty[s]);                // stage s free once these MMAs have read it
+                }
+                umma_commit(&acc_full[acc]);               // accumulator complete (or abandoned)
+            }
+            if (!ok) atomicOr(g.err, kErrTimeout);
+        }
+    } else {
+        // epilogue: warp w drains TMEM lanes 32 (w mod 4).. and half (w - 2) / 4 of the columns
+        const int quarter = warp & 3, half = (warp - 2) >> 2;
+        unsigned lt = 0;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++lt) {
+            const unsigned acc = lt & 1u;
+            if (!mbar_wait(&acc_full[acc], (lt / 2) & 1)) {
+                if (tid == 64) atomicOr(g.err, kErrTimeout);
                 break;
             }
-            unsigned char *a = ring + (size_t)s * kStageBytes;
-            mbar_expect_tx(&full[s], kStageBytes);
-            tma_load_2d(a, &mapA, kt * kBK, m0, &full[s]);
-#pragma unroll
-            for (int q = 0; q < BN / kBM; ++q)
-                tma_load_2d(a + kTileBytes * (1 + q), &mapB, kt * kBK, n0 + q * kBM, &full[s]);
-        }
-    } else if (tid == 32) {
-        // MMA issuer
-        bool ok = true;
-        for (int kt = 0; kt < KT; ++kt) {
-            const int s = kt % kStages;
-            if (!mbar_wait(&full[s], (kt / kStages) & 1)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a = saddr(ring + (size_t)s * kStageBytes), b = a + kTileBytes;
-#pragma unroll
-            for (int kk = 0; kk < kBK / 16; ++kk)
-                umma<BN>(tmem, sdesc(a + kk * 32), sdesc(b + kk * 32), (kt | kk) ? 1u : 0u);
-            umma_commit(&empty[s]);                        // stage s free once these MMAs have read it
-        }
-        if (!ok) { give_up = 1; atomicOr(g.err, kErrTimeout); }
-        umma_commit(&done);                                // accumulator complete
-    }
-    __syncthreads();
-    const bool ok = !give_up && mbar_wait(&done, 0);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
-        const int quarter = warp & 3, half = warp >> 2;
-        const int row = m0 + quarter * 32 + lane;
-        for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 32) {
-            uint32_t r[32];
-            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-                           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-                           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                         : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            const int nb = n0 + c0;
-            if (g.epi == EPI_F32) {
-                float *dst = g.C + (size_t)row * g.N + nb;
-#pragma unroll
-                for (int q = 0; q < 32; q += 4)
-                    *reinterpret_cast<float4 *>(dst + q) = make_float4(__uint_as_float(r[q]), __uint_as_float(r[q + 1]),
-                                                                       __uint_as_float(r[q + 2]), __uint_as_float(r[q + 3]));
-            } else {
-                __align__(16) __nv_bfloat16 hv[32], zv[32];
-                if (g.epi == EPI_BIAS_GELU) {
-                    // bias offsets are multiples of 128 floats by construction: float4 loads
-                    const float4 *b4 = reinterpret_cast<const float4 *>(g.bias + nb);
-#pragma unroll
-                    for (int q4 = 0; q4 < 8; ++q4) {
-                        const float4 bq = __ldg(&b4[q4]);
-                        const float bb[4] = {bq.x, bq.y, bq.z, bq.w};
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int q = 4 * q4 + e;
-                            zv[q] = __float2bfloat16(__uint_as_float(r[q]) + bb[e]);
-                            hv[q] = __float2bfloat16(gelu(__bfloat162float(zv[q])));
-                        }
-                    }
-                } else {
-                    const uint4 *zr = reinterpret_cast<const uint4 *>(g.Z + (size_t)row * g.N + nb);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) reinterpret_cast<uint4 *>(zv)[q] = zr[q];
-#pragma unroll
-                    for (int q = 0; q < 32; ++q)
-                        hv[q] = __float2bfloat16(__uint_as_float(r[q]) * gelu_grad(__bfloat162float(zv[q])));
-                }
-                uint4 *dh = reinterpret_cast<uint4 *>(g.H + (size_t)row * g.N + nb);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) dh[q] = reinterpret_cast<const uint4 *>(hv)[q];
-                if (g.epi == EPI_BIAS_GELU && g.Z) {        // pre-activation kept for the backward pass
-                    uint4 *dz = reinterpret_cast<uint4 *>(g.Z + (size_t)row * g.N + nb);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) dz[q] = reinterpret_cast<const uint4 *>(zv)[q];
-                }
-                if (g.Ht)
-#pragma unroll
-                    for (int q = 0; q < 32; ++q) g.Ht[(size_t)(nb + q) * g.M + row] = hv[q];
+            const int m0 = (tile / tiles_n) * kBM, n0 = (tile % tiles_n) * BN;
+            const int row = m0 + quarter * 32 + lane;
+            for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 32) {
+                uint32_t r[32];
+                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + acc * BN + (uint32_t)c0;
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                             "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                               "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                               "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                               "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                             : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                epilogue_chunk(g, r, row, n0 + c0);
             }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(&acc_empty[acc]);                  // accumulator acc may be overwritten
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
 }
 
 template <int BN>
@@ -431,18 +472,25 @@ ms_status gemm(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int
     if ((s = make_map(&ma, A, M, K)) != MS_OK) return s;
     if ((s = make_map(&mb, B, N, K)) != MS_OK) return s;
     static std::once_flag once;
+    static int n_sms = 0;
     std::call_once(once, [] {
         cudaFuncSetAttribute(k_gemm_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<128>());
         cudaFuncSetAttribute(k_gemm_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<256>());
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sms < 1) n_sms = 1;
     });
     GemmArgs g = proto;
     g.M = M; g.N = N; g.K = K;
     // 128 x 256 tiles halve the A-tile traffic per FLOP; they need N % 256 == 0
-    // and enough tiles to fill the GPU
-    if (N % 256 == 0 && (size_t)(M / kBM) * (N / 256) >= 148)
-        k_gemm_tc<256><<<dim3(N / 256, M / kBM), kGemmThreads, gemm_smem<256>(), st>>>(ma, mb, g);
-    else
-        k_gemm_tc<128><<<dim3(N / kBM, M / kBM), kGemmThreads, gemm_smem<128>(), st>>>(ma, mb, g);
+    // and enough tiles to give every SM one
+    const int t256 = N % 256 == 0 ? (M / kBM) * (N / 256) : 0;
+    if (t256 >= n_sms)
+        k_gemm_tc<256><<<std::min(t256, n_sms), kGemmThreads, gemm_smem<256>(), st>>>(ma, mb, g);
+    else {
+        const int t128 = (M / kBM) * (N / kBM);
+        k_gemm_tc<128><<<std::min(t128, n_sms), kGemmThreads, gemm_smem<128>(), st>>>(ma, mb, g);
+    }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(MS_ERR_CUDA, std::string("gemm launch: ") + cudaGetErrorString(e));
     return MS_OK;
