@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a)
     float *gph = reinterpret_cast<float *>(aa + n), *glk = gph + nv;
     const Env &e = a.env;
     const Records &rc = a.rec;
+    const unsigned rec_base = R.rec_base;          // the robot's first record
     float4 *ck = a.ckpt + (size_t)r * a.n_ckpt * a.n_cap * 2;
     float4 *sg = a.seg + (size_t)r * a.K * a.n_cap * 3;
 
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a)
             for (int i = tid; i < n; i += kAdjThreads) { c[2 * i] = xs[i]; c[2 * i + 1] = vs[i]; }
         }
         const float2 sc = a.sc[step];
-        for (int i = tid; i < n; i += kAdjThreads) aa[i] = robot_force(rc, R.slice_base, i, xs, vs, sc.x, sc.y);
+        for (int i = tid; i < n; i += kAdjThreads) aa[i] = robot_force(rc, R.slice_base, rec_base, i, xs, vs, sc.x, sc.y);
         __syncthreads();
         for (int i = tid; i < n; i += kAdjThreads) {
             float4 x = xs[i], v = vs[i];
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a)
         for (int step = n0; step < n1; ++step) {            // recompute the segment
             float4 *sgn = sg + (size_t)(step - n0) * a.n_cap * 3;
             const float2 sc = a.sc[step];
-            for (int i = tid; i < n; i += kAdjThreads) aa[i] = robot_force(rc, R.slice_base, i, xs, vs, sc.x, sc.y);
+            for (int i = tid; i < n; i += kAdjThreads) aa[i] = robot_force(rc, R.slice_base, rec_base, i, xs, vs, sc.x, sc.y);
             __syncthreads();
             for (int i = tid; i < n; i += kAdjThreads) {
                 float4 x = xs[i], v = vs[i], vt;
@@ -259,8 +260,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a)
                 for (unsigned s = 0; s < blen; ++s, q += 32u) {
                     const uint32_t be = __ldg(&rc.b_ent[q]);
                     if (be == kBackPad) continue;
-                    const int o = (int)(be & kOwnerMask);
-                    const unsigned r2 = __ldg(&rc.slice[R.slice_base + (o >> 5)].x) + (be >> kOwnerBits) * 32u + ((unsigned)o & 31u);
+                    const int o = (int)(be & kRobotOwnerMask);
+                    const unsigned r2 = rec_base + (be >> kRobotOwnerBits);
                     const float2 kl = __ldg(&rc.f_kl[r2]);
                     const float2 ab = __ldg(&rc.f_ab[r2]);
                     const float Lr = kl.y * (1.0f + (ab.x * sc.x + ab.y * sc.y));

@@ -518,8 +518,13 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
             for (int64_t m = rec_first[o]; m < rec_first[o + 1]; ++m) {
                 const int32_t j = rec_partner[m];
                 const int t = bfill[j]++;
+                const uint32_t slot = (uint32_t)(m - rec_first[o]);
+                // the persistent kernel runs the robot routines, whose back
+                // references hold the owner's record directly (robot-local form)
                 h_b[sl[j >> 5].bwd_off + 32u * (uint32_t)t + (uint32_t)(j & 31)] =
-                    (uint32_t)o | ((uint32_t)(m - rec_first[o]) << ms::kOwnerBits);
+                    persistent ? (uint32_t)o | ((sl[o >> 5].fwd_off - sl[0].fwd_off + 32u * slot + (uint32_t)(o & 31))
+                                                << ms::kRobotOwnerBits)
+                               : (uint32_t)o | (slot << ms::kOwnerBits);
             }
     }
     s->n_slots = n_slots;

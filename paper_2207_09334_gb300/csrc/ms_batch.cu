@@ -29,7 +29,7 @@
 namespace ms {
 namespace {
 
-constexpr int kBatchThreads = 256;
+constexpr int kBatchThreads = 512;
 constexpr int kWarpsPerCta = kBatchThreads / 32;
 constexpr int kWarpModeMax = 256;   // robots up to this many masses may run warp-per-robot
 
@@ -71,11 +71,13 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchArgs a)
             const int n = R.n;
             float4 *xs = smem, *vs = smem + n, *fs = smem + 2 * n;
             const float4 *g = a.st + 2 * R.mass_base;
+            const unsigned rec_base = R.rec_base;
             for (int i = tid; i < n; i += kBatchThreads) { xs[i] = g[2 * i]; vs[i] = g[2 * i + 1]; }
             __syncthreads();
             for (int step = 0; step < a.nsteps; ++step) {
                 const float2 sc = __ldg(&a.sc[step]);
-                for (int i = tid; i < n; i += kBatchThreads) fs[i] = robot_force(a.rec, R.slice_base, i, xs, vs, sc.x, sc.y);
+                for (int i = tid; i < n; i += kBatchThreads)
+                    fs[i] = robot_force<4>(a.rec, R.slice_base, rec_base, i, xs, vs, sc.x, sc.y);
                 __syncthreads();
                 for (int i = tid; i < n; i += kBatchThreads) {
                     float4 x = xs[i], v = vs[i];
@@ -111,11 +113,13 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchArgs a)
                 const int n = R.n;
                 float4 *xs = smem + (size_t)warp * 3 * a.warp_cap, *vs = xs + a.warp_cap, *fs = vs + a.warp_cap;
                 const float4 *g = a.st + 2 * R.mass_base;
+                const unsigned rec_base = R.rec_base;
                 for (int i = lane; i < n; i += 32) { xs[i] = g[2 * i]; vs[i] = g[2 * i + 1]; }
                 __syncwarp();
                 for (int step = 0; step < a.nsteps; ++step) {
                     const float2 sc = __ldg(&a.sc[step]);
-                    for (int i = lane; i < n; i += 32) fs[i] = robot_force(a.rec, R.slice_base, i, xs, vs, sc.x, sc.y);
+                    for (int i = lane; i < n; i += 32)
+                        fs[i] = robot_force<4>(a.rec, R.slice_base, rec_base, i, xs, vs, sc.x, sc.y);
                     __syncwarp();
                     for (int i = lane; i < n; i += 32) {
                         float4 x = xs[i], v = vs[i];
@@ -172,11 +176,12 @@ __global__ void __launch_bounds__(kBatchThreads) k_persistent(const Records rec,
     extern __shared__ float4 smem[];
     float4 *xs = smem, *vs = smem + n, *fs = smem + 2 * n;
     const int tid = threadIdx.x;
+    const unsigned rec_base = __ldg(&rec.slice[0].x);
     for (int i = tid; i < n; i += kBatchThreads) { xs[i] = st[2 * i]; vs[i] = st[2 * i + 1]; }
     __syncthreads();
     for (int step = 0; step < nsteps; ++step) {
         const float2 t = sc ? __ldg(&sc[step]) : make_float2(0.f, 0.f);
-        for (int i = tid; i < n; i += kBatchThreads) fs[i] = robot_force(rec, 0, i, xs, vs, t.x, t.y);
+        for (int i = tid; i < n; i += kBatchThreads) fs[i] = robot_force<4>(rec, 0, rec_base, i, xs, vs, t.x, t.y);
         __syncthreads();
         for (int i = tid; i < n; i += kBatchThreads) {
             float4 x = xs[i], v = vs[i];
@@ -572,6 +577,7 @@ ms_status build_voxels(const msb_voxel_spec *spec, int n_robots, const int32_t *
             for (int d = 0; d < 13; ++d) if (has[(size_t)o * 13 + d]) deg[o]++;
         const int ns = (n + 31) / 32;
         const size_t slice0 = h_slice.size();
+        R.rec_base = (uint32_t)h_nbr.size();              // the first slice's first record
         for (int s_ = 0; s_ < ns; ++s_) {
             int mx = 0;
             for (int l = 0; l < 32 && 32 * s_ + l < n; ++l) mx = std::max(mx, deg[32 * s_ + l]);
@@ -616,12 +622,15 @@ ms_status build_voxels(const msb_voxel_spec *spec, int n_robots, const int32_t *
         }
         (void)b0;
         std::vector<int> bfill(n, 0);
+        const uint32_t rec0 = h_slice[slice0].x;           // the robot's first record
         for (int o = 0; o < n; ++o) {
             const uint32_t base = h_slice[slice0 + (o >> 5)].x + (uint32_t)(o & 31);
             for (int s_ = 0; s_ < deg[o]; ++s_) {
-                const int j = h_nbr[base + 32u * s_];
+                const uint32_t rr = base + 32u * s_;
+                const int j = h_nbr[rr];
                 const int t = bfill[j]++;
-                h_b[h_slice[slice0 + (j >> 5)].y + 32u * t + (uint32_t)(j & 31)] = (uint32_t)o | ((uint32_t)s_ << kOwnerBits);
+                if (rr - rec0 >= (1u << (32 - kRobotOwnerBits))) return fail(MS_ERR_ARG, "robot has too many spring records");
+                h_b[h_slice[slice0 + (j >> 5)].y + 32u * t + (uint32_t)(j & 31)] = (uint32_t)o | ((rr - rec0) << kRobotOwnerBits);
             }
         }
         if (adjoint_maps) {
@@ -759,6 +768,8 @@ ms_status msb_run_loop(msb_batch *b, int32_t nsteps)
             const RobotDev &R = b->h_robots[r];
             a.N = R.n;
             a.slice = b->slice + R.slice_base;
+            a.back_local = 1;                  // robot records use robot-local back references
+            a.back_base = R.rec_base;
             a.st = cur + 2 * R.mass_base;
             a.sto = nxt + 2 * R.mass_base;
             MSB_CUDA_TRY(launch_step(a, b->stream));

@@ -39,6 +39,13 @@ struct Slice {                 // 16 bytes, read as one uint4
 
 constexpr uint32_t kOwnerBits = 27;
 constexpr uint32_t kOwnerMask = (1u << kOwnerBits) - 1u;
+// Back references of robots (and of the persistent single-system kernel),
+// robot-local form: owner o (< 4096 masses) in the low 12 bits, the owner's
+// record as an offset from the robot's first record above them (< 2^20
+// records per robot), or kBackPad.  One dependent load less than the
+// (owner, slot) form, which needs the owner's slice header.
+constexpr int kRobotOwnerBits = 12;
+constexpr uint32_t kRobotOwnerMask = (1u << kRobotOwnerBits) - 1u;
 constexpr uint32_t kBackPad = 0xffffffffu;
 constexpr int kMaxFwdDegree = 31;
 
@@ -63,6 +70,8 @@ struct StepArgs {
     const float *f_c;    // or nullptr (then c_uniform)
     const float2 *f_ab;  // (alpha, beta), or nullptr (passive)
     const uint32_t *b_ent;
+    int back_local;      // 1: b_ent in the robot-local form, records from back_base
+    uint32_t back_base;
     // tiled layout: tiles[2t] = (first mass, members, halo offset, halo count),
     // tiles[2t+1] = (first record slot, slots per member, 0, 0); slot s of
     // member m of tile t is record rec + s*kTileMasses + m (slot-major, so

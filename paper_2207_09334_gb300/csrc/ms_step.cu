@@ -171,8 +171,13 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a)
         int o = i;
         unsigned rr = 0;
         if (e != kBackPad) {
-            o = (int)(e & kOwnerMask);
-            rr = __ldg(&a.slice[o >> 5].x) + (e >> kOwnerBits) * 32u + ((unsigned)o & 31u);
+            if (a.back_local) {            // robot-local form (populations stepped robot by robot)
+                o = (int)(e & kRobotOwnerMask);
+                rr = a.back_base + (e >> kRobotOwnerBits);
+            } else {
+                o = (int)(e & kOwnerMask);
+                rr = __ldg(&a.slice[o >> 5].x) + (e >> kOwnerBits) * 32u + ((unsigned)o & 31u);
+            }
         }
         const float2 kl = __ldg(&a.f_kl[rr]);
         float L = kl.y;

@@ -8,7 +8,7 @@
 
 namespace ms {
 
-constexpr int kMaxRobotMasses = 4096;
+constexpr int kMaxRobotMasses = 4096;   // <= 2^kRobotOwnerBits (robot-local back references)
 
 struct RobotDev {
     long long mass_base;   // first mass in the population-wide numbering
@@ -18,6 +18,7 @@ struct RobotDev {
     int vox_base;          // first voxel of this robot in the concatenated grids
     int n_vox;             // voxels (including empty ones) of this robot
     float inv_mass;        // 1 / total mass
+    uint32_t rec_base;     // the robot's first record (= slice[slice_base].fwd_off)
 };
 
 // Host image of a population (robots concatenated; sliced-ELL rows with
@@ -89,9 +90,13 @@ __device__ __forceinline__ void vox_spring(const float4 xi, const float4 vi, con
     fx = fmaf(fs, dx, fx); fy = fmaf(fs, dy, fy); fz = fmaf(fs, dz, fz);
 }
 
-// Spring force on robot-local mass i from the shared-memory state.
-__device__ __forceinline__ float4 robot_force(const Records &a, int slice_base, int i, const float4 *xs,
-                                              const float4 *vs, float s_n, float c_n)
+// Spring force on robot-local mass i from the shared-memory state; rec_base
+// is the robot's first record (slice[slice_base].x).  UNROLL springs are
+// unrolled together so that their record loads (L2 round trips) overlap;
+// the population kernel gains from it, the register-heavy adjoint does not.
+template <int UNROLL = 1>
+__device__ __forceinline__ float4 robot_force(const Records &a, int slice_base, unsigned rec_base, int i,
+                                              const float4 *xs, const float4 *vs, float s_n, float c_n)
 {
     const unsigned lane = (unsigned)i & 31u;
     const uint4 meta = __ldg(&a.slice[slice_base + (i >> 5)]);
@@ -99,6 +104,7 @@ __device__ __forceinline__ float4 robot_force(const Records &a, int slice_base, 
     float fx = 0.f, fy = 0.f, fz = 0.f;
     const unsigned flen = meta.z & 0xffffu, blen = meta.z >> 16;
     unsigned r = meta.x + lane;
+#pragma unroll UNROLL
     for (unsigned s = 0; s < flen; ++s, r += 32u) {
         int j = __ldg(&a.f_nbr[r]);
         j = (j < 0) ? i : j;
@@ -108,13 +114,14 @@ __device__ __forceinline__ float4 robot_force(const Records &a, int slice_base, 
         vox_spring(xi, vi, xs[j], vs[j], kl.x, L, a.f_c ? __ldg(&a.f_c[r]) : a.c_uniform, fx, fy, fz);
     }
     unsigned q = meta.y + lane;
+#pragma unroll UNROLL
     for (unsigned s = 0; s < blen; ++s, q += 32u) {
         const uint32_t e = __ldg(&a.b_ent[q]);
         int o = i;
         unsigned rr = 0;
         if (e != kBackPad) {
-            o = (int)(e & kOwnerMask);
-            rr = __ldg(&a.slice[slice_base + (o >> 5)].x) + (e >> kOwnerBits) * 32u + ((unsigned)o & 31u);
+            o = (int)(e & kRobotOwnerMask);
+            rr = rec_base + (e >> kRobotOwnerBits);
         }
         const float2 kl = __ldg(&a.f_kl[rr]);
         const float2 ab = a.f_ab ? __ldg(&a.f_ab[rr]) : make_float2(0.f, 0.f);
