@@ -11,7 +11,7 @@
 // synchronisation in Algorithm 1), then every mass integrates in place.
 //
 // Two schedules share one kernel:
-//   block-per-robot  all 256 threads of a CTA work on one robot (__syncthreads);
+//   block-per-robot  all 512 threads of a CTA work on one robot (__syncthreads);
 //   warp-per-robot   each warp of a CTA owns a small robot (__syncwarp only).
 // The CTAs are persistent: they pull work items (a robot, or a group of up to
 // eight small robots) from a queue ordered by decreasing cost, and the
