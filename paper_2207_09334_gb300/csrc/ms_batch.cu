@@ -14,7 +14,7 @@
 //   block-per-robot  all 512 threads of a CTA work on one robot (__syncthreads);
 //   warp-per-robot   each warp of a CTA owns a small robot (__syncwarp only).
 // The CTAs are persistent: they pull work items (a robot, or a group of up to
-// eight small robots) from a queue ordered by decreasing cost, and the
+// sixteen small robots (one per warp)) from a queue ordered by decreasing cost, and the
 // choice of schedule per robot-size bucket is made by timing both
 // (msb_autotune).  At the end of its item a CTA reduces the robot's centre of
 // mass with warp shuffles and writes the x-travel.
@@ -340,7 +340,7 @@ int dir_index(int dx, int dy, int dz)
 }
 
 // Build the schedule items from per-robot modes: block items one per robot,
-// warp items groups of up to 8 robots of similar size; ordered by
+// warp items groups of up to kWarpsPerCta (16) robots of similar size; ordered by
 // decreasing cost so the persistent CTAs balance (longest item first).
 void set_items(msb_batch *b, const std::vector<int> &block_robots, std::vector<int> warp_robots)
 {
