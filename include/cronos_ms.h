@@ -164,7 +164,9 @@ ms_status ms_step(ms_sim *sim, int32_t nsteps);
  * synchronises the stream; page-locked memory gives the fastest copies).
  * Either pointer may be NULL to skip it.  ms_get_state to host also reports
  * MS_ERR_NONFINITE if the device flagged a non-finite value.  ms_set_state
- * keeps anchored masses' velocity at 0.
+ * keeps anchored masses' velocity at 0; with host input it checks every
+ * value on the device and returns MS_ERR_ARG (naming the first caller mass
+ * with a non-finite value) without modifying the state.
  */
 ms_status ms_get_state(ms_sim *sim, float *x, float *v, int32_t on_device);
 ms_status ms_set_state(ms_sim *sim, const float *x, const float *v, int32_t on_device);

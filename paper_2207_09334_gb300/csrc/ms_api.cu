@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cfloat>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -586,8 +587,9 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
         if ((st = upload<float4>(s, &s->rk_y[1], nullptr, 2 * (size_t)N)) != MS_OK) return st;
         if ((st = upload<float4>(s, &s->rk_acc, nullptr, 2 * (size_t)N)) != MS_OK) return st;
     }
-    if ((st = upload<int>(s, &s->err, nullptr, 1)) != MS_OK) return st;
-    MS_CUDA_TRY(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
+    // err[0]: sticky device error flags; err[1]: scratch of ms_set_state's finiteness check
+    if ((st = upload<int>(s, &s->err, nullptr, 2)) != MS_OK) return st;
+    MS_CUDA_TRY(cudaMemsetAsync(s->err, 0, 2 * sizeof(int), s->stream));
     // host arrays must outlive the asynchronous copies
     MS_CUDA_TRY(cudaStreamSynchronize(s->stream));
 
@@ -729,16 +731,20 @@ ms_status ms_set_state(ms_sim *s, const float *x, const float *v, int32_t on_dev
 {
     if (!s) return fail(MS_ERR_ARG, "sim is NULL");
     const int N = s->N;
-    if (!on_device) {
-        for (int i = 0; i < N; ++i)
-            if ((x && !finite3(x + 3 * i)) || (v && !finite3(v + 3 * i))) return fail(MS_ERR_ARG, "non-finite state at mass " + std::to_string(i));
-        if (x) MS_CUDA_TRY(cudaMemcpyAsync(s->stage, x, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, s->stream));
-        if (v) MS_CUDA_TRY(cudaMemcpyAsync(s->stage + 3 * (size_t)N, v, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, s->stream));
-        x = x ? s->stage : nullptr;
-        v = v ? s->stage + 3 * (size_t)N : nullptr;
+    if (on_device) {
+        MS_CUDA_TRY(ms::launch_scatter_state(s->st[s->cur], s->d_perm, N, x, v, s->stream));
+        return MS_OK;
     }
-    MS_CUDA_TRY(ms::launch_scatter_state(s->st[s->cur], s->d_perm, N, x, v, s->stream));
-    if (!on_device) MS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    // host input: copy to the staging buffer, check finiteness on the device,
+    // and scatter only if every value is finite (the state is untouched otherwise)
+    if (x) MS_CUDA_TRY(cudaMemcpyAsync(s->stage, x, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, s->stream));
+    if (v) MS_CUDA_TRY(cudaMemcpyAsync(s->stage + 3 * (size_t)N, v, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, s->stream));
+    MS_CUDA_TRY(ms::launch_checked_scatter_state(s->st[s->cur], s->d_perm, N, x ? s->stage : nullptr,
+                                                 v ? s->stage + 3 * (size_t)N : nullptr, s->err + 1, s->stream));
+    int first_bad = INT_MAX;
+    MS_CUDA_TRY(cudaMemcpyAsync(&first_bad, s->err + 1, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    MS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (first_bad != INT_MAX) return fail(MS_ERR_ARG, "non-finite state at mass " + std::to_string(first_bad));
     return MS_OK;
 }
 

@@ -119,11 +119,16 @@ cudaError_t launch_energy(const EnergyArgs &a, double *out, cudaStream_t s);
 // out[3 q + c] = x[idx[q]][c] for q < n
 cudaError_t launch_trace(const float4 *st, const int32_t *idx, int n, float *out, cudaStream_t s);
 
-// Launchers (ms_step.cu).
+// Launchers (ms_step.cu, ms_state.cu).
 cudaError_t launch_step(const StepArgs &a, cudaStream_t st);
 cudaError_t launch_gather_state(const float4 *st, const int32_t *perm, int N,
                                 float *x_out, float *v_out, cudaStream_t stream);
 cudaError_t launch_scatter_state(float4 *st, const int32_t *perm, int N,
                                  const float *x_in, const float *v_in, cudaStream_t stream);
+// the same, after a device-side finiteness check of the inputs: first_bad
+// (device int) receives the first caller index with a non-finite value, or
+// INT_MAX, and the state is written only when every value is finite
+cudaError_t launch_checked_scatter_state(float4 *st, const int32_t *perm, int N, const float *x_in,
+                                         const float *v_in, int *first_bad, cudaStream_t stream);
 
 }  // namespace ms

@@ -422,44 +422,5 @@ cudaError_t launch_step(const StepArgs &a, cudaStream_t st)
     return a.integrator == 3 ? launch_step_t<true>(a, st) : launch_step_t<false>(a, st);
 }
 
-__global__ void k_gather_state(const float4 *__restrict__ st, const int32_t *__restrict__ perm, int N,
-                               float *__restrict__ xo, float *__restrict__ vo)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const int c = perm ? perm[i] : i;
-    if (xo) { const float4 p = st[2 * i]; xo[3 * c] = p.x; xo[3 * c + 1] = p.y; xo[3 * c + 2] = p.z; }
-    if (vo) { const float4 p = st[2 * i + 1]; vo[3 * c] = p.x; vo[3 * c + 1] = p.y; vo[3 * c + 2] = p.z; }
-}
-
-__global__ void k_scatter_state(float4 *__restrict__ st, const int32_t *__restrict__ perm, int N,
-                                const float *__restrict__ xi, const float *__restrict__ vi)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const int c = perm ? perm[i] : i;
-    const float w = st[2 * i].w;
-    if (xi) st[2 * i] = make_float4(xi[3 * c], xi[3 * c + 1], xi[3 * c + 2], w);
-    if (vi) {
-        if (w < 0.0f) st[2 * i + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
-        else st[2 * i + 1] = make_float4(vi[3 * c], vi[3 * c + 1], vi[3 * c + 2], 0.f);
-    }
-}
-
-cudaError_t launch_gather_state(const float4 *st, const int32_t *perm, int N,
-                                float *x_out, float *v_out, cudaStream_t stream)
-{
-    if (N <= 0) return cudaSuccess;
-    k_gather_state<<<(N + 255) / 256, 256, 0, stream>>>(st, perm, N, x_out, v_out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_scatter_state(float4 *st, const int32_t *perm, int N,
-                                 const float *x_in, const float *v_in, cudaStream_t stream)
-{
-    if (N <= 0) return cudaSuccess;
-    k_scatter_state<<<(N + 255) / 256, 256, 0, stream>>>(st, perm, N, x_in, v_in);
-    return cudaGetLastError();
-}
 
 }  // namespace ms

@@ -318,3 +318,22 @@ def test_rk4_with_actuation_anchors_and_ground_contact(ms, ora, kernel):
     xo, _ = ora.run(s, f32p(p), 500, integrator="rk4")
     err = np.abs(xg - xo).max()
     assert err <= 1e-5 * body_size(s), (err, 1e-5 * body_size(s))
+
+
+def test_set_state_rejects_non_finite_host_input_and_keeps_the_state(ms):
+    """ms_set_state checks host input on the device: a NaN at caller mass 5
+    returns MS_ERR_ARG naming that mass, and the state is not modified."""
+    s = synth.soft_cube(n=4)
+    with ms.Sim(s, synth.soft_cube_params(contact=False)) as sim:
+        sim.step(3)
+        x0, v0 = sim.get_state()
+        xb = x0.copy(); xb[5, 1] = np.nan
+        xb[9, 0] = np.inf
+        with pytest.raises(ms.MsError) as e:
+            sim.set_state(xb, v0)
+        assert e.value.code == 1 and "mass 5" in str(e.value)
+        x1, v1 = sim.get_state()
+        assert np.array_equal(x1, x0) and np.array_equal(v1, v0)
+        sim.set_state(x0 + np.float32(1e-4), v0)          # a finite state is accepted
+        x2, _ = sim.get_state()
+        assert np.allclose(x2, x0 + np.float32(1e-4))
