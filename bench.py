@@ -130,6 +130,43 @@ def dist_setup():
     return world, rank, local
 
 
+class Replicas:
+    """N independent replicas launched by torchrun (one per GPU): no data-path
+    collective; only a barrier around each timed region and the max over
+    ranks of its duration, so `value` counts the work of all ranks over the
+    slowest rank's time.  backend: "nccl" on GPUs, "gloo" for host tests."""
+
+    def __init__(self, world: int, backend: str = "nccl"):
+        self.world = world
+        self.dist = None
+        self.device = "cuda" if backend == "nccl" else "cpu"
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist:
+            self.dist.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.dist:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def throughput(self, units_per_rank: float, seconds: float) -> float:
+        """whole-job units per second: every rank's units over the max time"""
+        return self.world * units_per_rank / self.max(seconds)
+
+    def close(self):
+        if self.dist:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
 def lattice_workload(n: int):
     s = synth.throughput_lattice(n=n)
     p = synth.throughput_params()
@@ -207,10 +244,7 @@ def run_ours(args, world, rank, local):
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU (no CPU fallback)")
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    reps = Replicas(world)
     ms.load()
     n = args.n
     t0 = time.perf_counter()
@@ -232,8 +266,7 @@ def run_ours(args, world, rank, local):
     sim.sync()
 
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    if dist:
-        dist.barrier()
+    reps.barrier()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
         ev[0].record(stream)
@@ -241,17 +274,13 @@ def run_ours(args, world, rank, local):
             sim.step(1)
             ev[q + 1].record(stream)
         torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    reps.barrier()
     total_ms = ev[0].elapsed_time(ev[-1])
     per = [ev[q].elapsed_time(ev[q + 1]) for q in range(args.steps)]
     sim.sync()
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    value = reps.throughput((N + S) * args.steps, total_ms * 1e-3)
+    total_ms = reps.max(total_ms)
     ms_per_step = total_ms / args.steps
-    value = world * (N + S) * args.steps / (total_ms * 1e-3)
 
     # end to end through the public API with host buffers: upload the state
     # from pinned host memory, run the workload's 200 steps, read it back
@@ -263,6 +292,7 @@ def run_ours(args, world, rank, local):
         vh = torch.from_numpy(np.ascontiguousarray(s["v"])).pin_memory()
         xo = torch.empty_like(xh).pin_memory(); vo = torch.empty_like(vh).pin_memory()
         e2e_times = []
+        reps.barrier()
         for it in range(args.e2e_iters + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -272,7 +302,7 @@ def run_ours(args, world, rank, local):
             el = time.perf_counter() - t0
             if it > 0:
                 e2e_times.append(el)
-        e2e_val = world * (N + S) * e2e_steps / statistics.median(e2e_times)
+        e2e_val = reps.throughput((N + S) * e2e_steps, statistics.median(e2e_times))
         e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_state,
                "d2h_bytes_per_step": bytes_state,
                "note": f"each e2e step = ms_set_state(pinned host) + ms_step({e2e_steps}) + ms_get_state(pinned host)"}
@@ -310,8 +340,7 @@ def run_ours(args, world, rank, local):
     if rank == 0:
         print(json.dumps(line), flush=True)
     sim.close()
-    if dist:
-        dist.destroy_process_group()
+    reps.close()
     return 0
 
 
@@ -332,19 +361,23 @@ def run_population(args, world, rank, local):
     t_create = time.perf_counter() - t0
     S = args.sim_steps_per_bench_step
     stream = torch.cuda.current_stream()
+    reps = Replicas(world)
     for _ in range(args.warmup):
         pop.run(S)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    reps.barrier()
     with Clocks(local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
             pop.run(S)
         e1.record(stream)
         torch.cuda.synchronize()
+    reps.barrier()
     ms_total = e0.elapsed_time(e1)
     sim_s = args.robots * S * p["dt"] * args.steps
-    value = sim_s / (ms_total * 1e-3)
+    value = reps.throughput(sim_s, ms_total * 1e-3)
+    ms_total = reps.max(ms_total)
     el_per_step = inf["n_masses"] + inf["n_records"]
     # the plain per-robot loop on a short sample of steps
     L = args.loop_steps
@@ -364,7 +397,7 @@ def run_population(args, world, rank, local):
                        "n_masses": inf["n_masses"], "n_springs_merged": inf["n_records"],
                        "block_robots": inf["n_block_items"], "warp_robots": inf["n_warp_items"],
                        "setup_s": round(t_create, 1)},
-            "elements_per_s": el_per_step * S * args.steps / (ms_total * 1e-3),
+            "elements_per_s": world * el_per_step * S * args.steps / (ms_total * 1e-3),
             "per_robot_loop": {"value": loop_value, "unit": "robot-sim-s/s", "sim_steps": L,
                                "speedup_of_batched": value / loop_value},
             "gpu_launches": 3 * args.steps, "clocks": clk.summary(),
@@ -372,6 +405,7 @@ def run_population(args, world, rank, local):
     if rank == 0:
         print(json.dumps(line), flush=True)
     pop.close()
+    reps.close()
     return 0
 
 
@@ -395,19 +429,23 @@ def run_surrogate(args, world, rank, local):
         for s in range(0, n_cand, B):
             net.load_materials(cand[s:s + B])
             net.forward(B, out[s:s + B])
+    reps = Replicas(world)
     for _ in range(args.warmup):
         screen_once()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    reps.barrier()
     with Clocks(local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
             screen_once()
         e1.record(stream)
         torch.cuda.synchronize()
+    reps.barrier()
     ms_total = e0.elapsed_time(e1)
-    value = n_cand * args.steps / (ms_total * 1e-3)
-    flops = 2.0 * (2048 * 512 + 512 * 512 + 512) * n_cand * args.steps
+    value = reps.throughput(n_cand * args.steps, ms_total * 1e-3)
+    ms_total = reps.max(ms_total)
+    flops = 2.0 * (2048 * 512 + 512 * 512 + 512) * n_cand * args.steps * world
     # training step throughput (forward + backward + Adam, batch 1024)
     TB = 1024
     tgt = torch.randn(TB, device="cuda")
@@ -443,12 +481,13 @@ def run_surrogate(args, world, rank, local):
             "tensor_tflops": flops / (ms_total * 1e-3) / 1e12,
             "train_step_ms_batch1024": train_ms,
             "simulator_designs_per_s_2s_rollout": sim_rate,
-            "screen_speedup_vs_simulation": value / sim_rate,
+            "screen_speedup_vs_simulation": value / (world * sim_rate),
             "gpu_launches": args.steps * (2 * (n_cand // B) + 2 * (n_cand // B)),
             "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     net.close()
+    reps.close()
     return 0
 
 
@@ -470,19 +509,22 @@ def run_adjoint(args, world, rank, local):
     adj = ms.Adjoint(mats, synth.VOXEL_MATERIALS, synth.VOXEL_FREQ, synth.VOXEL_EDGE, synth.VOXEL_MASS,
                      synth.voxel_params(), checkpoint_every=100, max_steps=nsteps)
     stream = torch.cuda.current_stream()
+    reps = Replicas(world)
     for _ in range(args.warmup):
         adj.gradients(nsteps, phase, logk)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    reps.barrier()
     with Clocks(local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
             loss, gp, gk = adj.gradients(nsteps, phase, logk)
         e1.record(stream)
         torch.cuda.synchronize()
+    reps.barrier()
     ms_total = e0.elapsed_time(e1)
-    per = ms_total / args.steps
-    value = args.walkers * nsteps * synth.voxel_params()["dt"] / (per * 1e-3)
+    value = reps.throughput(args.walkers * nsteps * synth.voxel_params()["dt"] * args.steps, ms_total * 1e-3)
+    per = reps.max(ms_total) / args.steps
     line = {"metric": "differentiated robot-sim-s/s", "value": value, "unit": "robot-sim-s/s (forward + reverse)",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -496,6 +538,7 @@ def run_adjoint(args, world, rank, local):
     if rank == 0:
         print(json.dumps(line), flush=True)
     adj.close()
+    reps.close()
     return 0
 
 
