@@ -80,7 +80,11 @@ struct ms_sim {
     int n_slices = 0;
     int64_t n_slots = 0, n_back_slots = 0, n_records = 0;
     int max_fwd = 0, max_back = 0;
-    float4 *st[2] = {nullptr, nullptr};   // 2 float4 per mass: (x, w), (v, 0)
+    // state, packed and double buffered: sa = (x, y, z, vx), sb = (vy, vz);
+    // w = 1/m, or -m for an anchored mass (constant)
+    float4 *sa[2] = {nullptr, nullptr};
+    float2 *sb[2] = {nullptr, nullptr};
+    float *w = nullptr;
     int cur = 0;
     float4 *fext = nullptr;
     uint4 *slice = nullptr;
@@ -106,8 +110,9 @@ struct ms_sim {
     int32_t *tr_idx = nullptr;          // traced masses (internal order)
     float *tr_buf = nullptr;            // tr_cap steps x tr_n masses x 3
     int tr_n = 0, tr_cap = 0, tr_count = 0;
-    // RK4: two stage states and the slope accumulator (2 float4 per mass each)
-    float4 *rk_y[2] = {nullptr, nullptr};
+    // RK4: two stage states (packed as the state) and the slope accumulator (2 float4 per mass)
+    float4 *rk_a[2] = {nullptr, nullptr};
+    float2 *rk_b[2] = {nullptr, nullptr};
     float4 *rk_acc = nullptr;
 
     double freq = 0.0;
@@ -534,7 +539,9 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
     s->rec_slot_b.swap(slot_b);
 
     // masses
-    std::vector<float4> hs(2 * (size_t)N), hf;
+    std::vector<float4> ha(N), hf;
+    std::vector<float2> hb(N);
+    std::vector<float> hw(N);
     double bound = 0.0;
     const double dt2 = (double)p->dt * p->dt;
     for (int32_t i = 0; i < N; ++i) {
@@ -544,9 +551,9 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
         // smallest negative normal, so the sign still marks the anchor)
         const float w = !anchored ? (float)(1.0 / (double)mass[cidx])
                         : (mass[cidx] > 0.f && std::isfinite(mass[cidx])) ? -mass[cidx] : -FLT_MIN;
-        hs[2 * (size_t)i] = make_float4(x0[3 * cidx], x0[3 * cidx + 1], x0[3 * cidx + 2], w);
-        hs[2 * (size_t)i + 1] = anchored ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                         : make_float4(v0[3 * cidx], v0[3 * cidx + 1], v0[3 * cidx + 2], 0.f);
+        ha[i] = make_float4(x0[3 * cidx], x0[3 * cidx + 1], x0[3 * cidx + 2], anchored ? 0.f : v0[3 * cidx]);
+        hb[i] = anchored ? make_float2(0.f, 0.f) : make_float2(v0[3 * cidx + 1], v0[3 * cidx + 2]);
+        hw[i] = w;
         if (!anchored) bound = std::max(bound, dt2 * (2.0 * sumK[i] + (p->contact_on ? p->k_c : 0.0)) / mass[cidx]);
     }
     s->stability = bound;
@@ -565,8 +572,11 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
 
     // 4. device upload
     ms_status st;
-    if ((st = upload(s, &s->st[0], hs.data(), 2 * (size_t)N)) != MS_OK) return st;
-    if ((st = upload(s, &s->st[1], hs.data(), 2 * (size_t)N)) != MS_OK) return st;
+    for (int q = 0; q < 2; ++q) {
+        if ((st = upload(s, &s->sa[q], ha.data(), N)) != MS_OK) return st;
+        if ((st = upload(s, &s->sb[q], hb.data(), N)) != MS_OK) return st;
+    }
+    if ((st = upload(s, &s->w, hw.data(), N)) != MS_OK) return st;
     if (fext && (st = upload(s, &s->fext, hf.data(), N)) != MS_OK) return st;
     static_assert(sizeof(ms::Slice) == sizeof(uint4), "slice size");
     if ((st = upload(s, &s->slice, (const uint4 *)sl.data(), n_slices)) != MS_OK) return st;
@@ -583,8 +593,10 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
     if (s->permuted && (st = upload(s, &s->d_perm, s->perm.data(), N)) != MS_OK) return st;
     if ((st = upload<float>(s, &s->stage, nullptr, (size_t)N * 6)) != MS_OK) return st;
     if (p->integrator == 3) {
-        if ((st = upload<float4>(s, &s->rk_y[0], nullptr, 2 * (size_t)N)) != MS_OK) return st;
-        if ((st = upload<float4>(s, &s->rk_y[1], nullptr, 2 * (size_t)N)) != MS_OK) return st;
+        for (int q = 0; q < 2; ++q) {
+            if ((st = upload<float4>(s, &s->rk_a[q], nullptr, (size_t)N)) != MS_OK) return st;
+            if ((st = upload<float2>(s, &s->rk_b[q], nullptr, (size_t)N)) != MS_OK) return st;
+        }
         if ((st = upload<float4>(s, &s->rk_acc, nullptr, 2 * (size_t)N)) != MS_OK) return st;
     }
     // err[0]: sticky device error flags; err[1]: scratch of ms_set_state's finiteness check
@@ -659,11 +671,13 @@ ms_status ms_step(ms_sim *s, int32_t nsteps)
             sc = s->sc;
         }
         ms::Records rec{s->slice, s->f_nbr, s->f_kl, s->f_c, s->actuated ? s->f_ab : nullptr, s->b_ent, s->c_uniform};
-        MS_CUDA_TRY(ms::launch_persistent(rec, ms::make_env(s->p), s->st[s->cur], s->N, sc, nsteps, s->err, s->stream));
+        MS_CUDA_TRY(ms::launch_persistent(rec, ms::make_env(s->p), s->sa[s->cur], s->sb[s->cur], s->w, s->N, sc, nsteps,
+                                          s->err, s->stream));
         s->step_count += nsteps;
         return MS_OK;
     }
     ms::StepArgs a{};
+    a.w = s->w;
     a.fext = s->fext; a.slice = s->slice; a.f_nbr = s->f_nbr; a.f_kl = s->f_kl;
     a.f_c = s->f_c; a.f_ab = s->actuated ? s->f_ab : nullptr;
     a.b_ent = s->b_ent; a.err = s->err; a.N = s->N; a.c_uniform = s->c_uniform;
@@ -677,10 +691,10 @@ ms_status ms_step(ms_sim *s, int32_t nsteps)
         a.first_step = (s->step_count + n == 0) ? 1 : 0;
         const double t = (double)(s->step_count + n) * (double)s->p.dt;
         if (s->p.integrator == 3) {
-            // four stage launches: Y_0 = Y_n -> rk_y[0] -> rk_y[1] -> rk_y[0] -> Y_{n+1};
+            // four stage launches: Y_0 = Y_n -> rk stage 0 -> rk stage 1 -> rk stage 0 -> Y_{n+1};
             // stage q sees the actuation at t_n + c_q dt, c = 0, 1/2, 1/2, 1
             static const double c_stage[4] = {0.0, 0.5, 0.5, 1.0};
-            a.rk_base = s->st[s->cur];
+            a.rk_ba = s->sa[s->cur]; a.rk_bb = s->sb[s->cur];
             for (int q = 0; q < 4; ++q) {
                 if (s->actuated) {
                     const double tq = t + c_stage[q] * (double)s->p.dt;
@@ -688,8 +702,10 @@ ms_status ms_step(ms_sim *s, int32_t nsteps)
                     a.c_n = (float)std::cos(two_pi_f * tq);
                 }
                 a.rk_stage = q;
-                a.st = q == 0 ? s->st[s->cur] : s->rk_y[(q - 1) & 1];
-                a.sto = q == 3 ? s->st[s->cur ^ 1] : s->rk_y[q & 1];
+                a.sa = q == 0 ? s->sa[s->cur] : s->rk_a[(q - 1) & 1];
+                a.sb = q == 0 ? s->sb[s->cur] : s->rk_b[(q - 1) & 1];
+                a.oa = q == 3 ? s->sa[s->cur ^ 1] : s->rk_a[q & 1];
+                a.ob = q == 3 ? s->sb[s->cur ^ 1] : s->rk_b[q & 1];
                 MS_CUDA_TRY(ms::launch_step(a, s->stream));
             }
         } else {
@@ -697,13 +713,13 @@ ms_status ms_step(ms_sim *s, int32_t nsteps)
                 a.s_n = (float)std::sin(two_pi_f * t);
                 a.c_n = (float)std::cos(two_pi_f * t);
             }
-            a.st = s->st[s->cur];
-            a.sto = s->st[s->cur ^ 1];
+            a.sa = s->sa[s->cur]; a.sb = s->sb[s->cur];
+            a.oa = s->sa[s->cur ^ 1]; a.ob = s->sb[s->cur ^ 1];
             MS_CUDA_TRY(ms::launch_step(a, s->stream));
         }
         s->cur ^= 1;
         if (s->tr_n > 0 && s->tr_count < s->tr_cap) {
-            MS_CUDA_TRY(ms::launch_trace(s->st[s->cur], s->tr_idx, s->tr_n,
+            MS_CUDA_TRY(ms::launch_trace(s->sa[s->cur], s->tr_idx, s->tr_n,
                                          s->tr_buf + (size_t)s->tr_count * s->tr_n * 3, s->stream));
             ++s->tr_count;
         }
@@ -717,11 +733,11 @@ ms_status ms_get_state(ms_sim *s, float *x, float *v, int32_t on_device)
     if (!s) return fail(MS_ERR_ARG, "sim is NULL");
     const int N = s->N;
     if (on_device) {
-        MS_CUDA_TRY(ms::launch_gather_state(s->st[s->cur], s->d_perm, N, x, v, s->stream));
+        MS_CUDA_TRY(ms::launch_gather_state(s->sa[s->cur], s->sb[s->cur], s->d_perm, N, x, v, s->stream));
         return MS_OK;
     }
     float *sx = x ? s->stage : nullptr, *sv = v ? s->stage + 3 * (size_t)N : nullptr;
-    MS_CUDA_TRY(ms::launch_gather_state(s->st[s->cur], s->d_perm, N, sx, sv, s->stream));
+    MS_CUDA_TRY(ms::launch_gather_state(s->sa[s->cur], s->sb[s->cur], s->d_perm, N, sx, sv, s->stream));
     if (x) MS_CUDA_TRY(cudaMemcpyAsync(x, sx, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, s->stream));
     if (v) MS_CUDA_TRY(cudaMemcpyAsync(v, sv, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, s->stream));
     return ms_sync(s);
@@ -732,14 +748,14 @@ ms_status ms_set_state(ms_sim *s, const float *x, const float *v, int32_t on_dev
     if (!s) return fail(MS_ERR_ARG, "sim is NULL");
     const int N = s->N;
     if (on_device) {
-        MS_CUDA_TRY(ms::launch_scatter_state(s->st[s->cur], s->d_perm, N, x, v, s->stream));
+        MS_CUDA_TRY(ms::launch_scatter_state(s->sa[s->cur], s->sb[s->cur], s->w, s->d_perm, N, x, v, s->stream));
         return MS_OK;
     }
     // host input: copy to the staging buffer, check finiteness on the device,
     // and scatter only if every value is finite (the state is untouched otherwise)
     if (x) MS_CUDA_TRY(cudaMemcpyAsync(s->stage, x, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, s->stream));
     if (v) MS_CUDA_TRY(cudaMemcpyAsync(s->stage + 3 * (size_t)N, v, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, s->stream));
-    MS_CUDA_TRY(ms::launch_checked_scatter_state(s->st[s->cur], s->d_perm, N, x ? s->stage : nullptr,
+    MS_CUDA_TRY(ms::launch_checked_scatter_state(s->sa[s->cur], s->sb[s->cur], s->w, s->d_perm, N, x ? s->stage : nullptr,
                                                  v ? s->stage + 3 * (size_t)N : nullptr, s->err + 1, s->stream));
     int first_bad = INT_MAX;
     MS_CUDA_TRY(cudaMemcpyAsync(&first_bad, s->err + 1, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
@@ -763,7 +779,8 @@ ms_status ms_energy(ms_sim *s, double *out, int32_t on_device)
 {
     if (!s || !out) return fail(MS_ERR_ARG, "sim or out is NULL");
     ms::EnergyArgs a{};
-    a.st = s->st[s->cur]; a.slice = s->slice; a.f_nbr = s->f_nbr; a.t_nbr = s->t_nbr;
+    a.sa = s->sa[s->cur]; a.sb = s->sb[s->cur]; a.w = s->w;
+    a.slice = s->slice; a.f_nbr = s->f_nbr; a.t_nbr = s->t_nbr;
     a.tiles = s->tiles; a.halo = s->halo; a.f_kl = s->f_kl; a.f_ab = s->actuated ? s->f_ab : nullptr;
     a.N = s->N; a.n_tiles = s->n_tiles; a.tiled = s->kernel == ms::kKernelTiled;
     if (s->actuated) {

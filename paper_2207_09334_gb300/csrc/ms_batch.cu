@@ -169,15 +169,23 @@ __global__ void k_sc_table_from(long long n0, int nsteps, double dt, double two_
     out[n] = make_float2((float)s, (float)c);
 }
 
-// All steps of one small system in one CTA (the robot step, block mode).
-__global__ void __launch_bounds__(kBatchThreads) k_persistent(const Records rec, const Env env, float4 *st, int n,
-                                                              const float2 *sc, int nsteps, int *err)
+// All steps of one small system in one CTA (the robot step, block mode).  The
+// system's state is packed as the single-system step keeps it: sa = (x, vx),
+// sb = (vy, vz), w = 1/m or -m.
+__global__ void __launch_bounds__(kBatchThreads) k_persistent(const Records rec, const Env env, float4 *sa, float2 *sb,
+                                                              const float *w, int n, const float2 *sc, int nsteps,
+                                                              int *err)
 {
     extern __shared__ float4 smem[];
     float4 *xs = smem, *vs = smem + n, *fs = smem + 2 * n;
     const int tid = threadIdx.x;
     const unsigned rec_base = __ldg(&rec.slice[0].x);
-    for (int i = tid; i < n; i += kBatchThreads) { xs[i] = st[2 * i]; vs[i] = st[2 * i + 1]; }
+    for (int i = tid; i < n; i += kBatchThreads) {
+        const float4 p = sa[i];
+        const float2 q = sb[i];
+        xs[i] = make_float4(p.x, p.y, p.z, w[i]);
+        vs[i] = make_float4(p.w, q.x, q.y, 0.f);
+    }
     __syncthreads();
     for (int step = 0; step < nsteps; ++step) {
         const float2 t = sc ? __ldg(&sc[step]) : make_float2(0.f, 0.f);
@@ -193,7 +201,8 @@ __global__ void __launch_bounds__(kBatchThreads) k_persistent(const Records rec,
     bool bad = false;
     for (int i = tid; i < n; i += kBatchThreads) {
         const float4 x = xs[i], v = vs[i];
-        st[2 * i] = x; st[2 * i + 1] = v;
+        sa[i] = make_float4(x.x, x.y, x.z, v.x);
+        sb[i] = make_float2(v.y, v.z);
         bad |= !isfinite(x.x + x.y + x.z + v.x + v.y + v.z);
     }
     if (__syncthreads_or(bad) && tid == 0) atomicOr(err, kErrNonFinite);
@@ -245,6 +254,11 @@ struct msb_batch {
 
     RobotDev *robots = nullptr;
     float4 *st = nullptr, *st2 = nullptr;
+    // robot-by-robot loop (msb_run_loop): the population in the single-system
+    // step's packed layout, allocated on first use
+    float4 *loop_a[2] = {nullptr, nullptr};
+    float2 *loop_b[2] = {nullptr, nullptr};
+    float *loop_w = nullptr;
     uint4 *slice = nullptr;
     int32_t *f_nbr = nullptr;
     float2 *f_kl = nullptr, *f_ab = nullptr;
@@ -457,15 +471,15 @@ void launch_sc_table_from(long long n0, int nsteps, double dt, double two_pi_f, 
     if (nsteps > 0) k_sc_table_from<<<(nsteps + 255) / 256, 256, 0, s>>>(n0, nsteps, dt, two_pi_f, out);
 }
 
-cudaError_t launch_persistent(const Records &rec, const Env &env, float4 *st, int n, const float2 *sc, int nsteps,
-                              int *err, cudaStream_t s)
+cudaError_t launch_persistent(const Records &rec, const Env &env, float4 *sa, float2 *sb, const float *w, int n,
+                              const float2 *sc, int nsteps, int *err, cudaStream_t s)
 {
     if (n <= 0 || nsteps <= 0) return cudaSuccess;
     if (n > kMaxRobotMasses) return cudaErrorInvalidValue;
     const size_t smem = (size_t)n * 3 * sizeof(float4);
     cudaError_t e = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_persistent<<<1, kBatchThreads, smem, s>>>(rec, env, st, n, sc, nsteps, err);
+    k_persistent<<<1, kBatchThreads, smem, s>>>(rec, env, sa, sb, w, n, sc, nsteps, err);
     return cudaGetLastError();
 }
 
@@ -754,12 +768,22 @@ ms_status msb_run_loop(msb_batch *b, int32_t nsteps)
 {
     if (!b) return fail(MS_ERR_ARG, "batch is NULL");
     if (nsteps < 0) return fail(MS_ERR_ARG, "nsteps must be >= 0");
+    if (!b->loop_w) {
+        ms_status st;
+        for (int q = 0; q < 2; ++q) {
+            if ((st = bupload<float4>(b, &b->loop_a[q], nullptr, (size_t)b->n_masses)) != MS_OK) return st;
+            if ((st = bupload<float2>(b, &b->loop_b[q], nullptr, (size_t)b->n_masses)) != MS_OK) return st;
+        }
+        if ((st = bupload<float>(b, &b->loop_w, nullptr, (size_t)b->n_masses)) != MS_OK) return st;
+    }
+    // the single-system step kernel keeps the state packed: convert, step robot by robot, convert back
+    MSB_CUDA_TRY(launch_pack_state(b->st, (int)b->n_masses, b->loop_a[0], b->loop_b[0], b->loop_w, b->stream));
     StepArgs a{};
     a.f_nbr = b->f_nbr; a.f_kl = b->f_kl; a.f_c = b->f_c; a.f_ab = b->f_ab; a.b_ent = b->b_ent;
     a.err = b->err; a.dt = b->p.dt; a.gx = b->p.g[0]; a.gy = b->p.g[1]; a.gz = b->p.g[2];
     a.k_c = b->p.k_c; a.mu = b->p.mu; a.keep = 1.0f - b->p.vel_damping; a.contact = b->p.contact_on;
     const double two_pi_f = 2.0 * M_PI * b->freq;
-    float4 *cur = b->st, *nxt = b->st2;
+    int cur = 0;
     for (int n = 0; n < nsteps; ++n) {
         const double t = (double)(b->step_count + n) * (double)b->p.dt;
         a.s_n = (float)std::sin(two_pi_f * t);
@@ -770,14 +794,14 @@ ms_status msb_run_loop(msb_batch *b, int32_t nsteps)
             a.slice = b->slice + R.slice_base;
             a.back_local = 1;                  // robot records use robot-local back references
             a.back_base = R.rec_base;
-            a.st = cur + 2 * R.mass_base;
-            a.sto = nxt + 2 * R.mass_base;
+            a.sa = b->loop_a[cur] + R.mass_base; a.sb = b->loop_b[cur] + R.mass_base;
+            a.oa = b->loop_a[cur ^ 1] + R.mass_base; a.ob = b->loop_b[cur ^ 1] + R.mass_base;
+            a.w = b->loop_w + R.mass_base;
             MSB_CUDA_TRY(launch_step(a, b->stream));
         }
-        std::swap(cur, nxt);
+        cur ^= 1;
     }
-    if (cur != b->st)
-        MSB_CUDA_TRY(cudaMemcpyAsync(b->st, cur, sizeof(float4) * 2 * b->n_masses, cudaMemcpyDeviceToDevice, b->stream));
+    MSB_CUDA_TRY(launch_unpack_state(b->loop_a[cur], b->loop_b[cur], b->loop_w, (int)b->n_masses, b->st, b->stream));
     // keep the batched kernel's clock in step with this one
     if (nsteps > 0) {
         k_advance<<<1, 1, 0, b->stream>>>(b->counter, nsteps);

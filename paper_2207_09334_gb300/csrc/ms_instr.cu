@@ -31,8 +31,10 @@ struct Terms {
 
 __device__ __forceinline__ void mass_terms(const EnergyArgs &a, int i, Terms &t)
 {
-    const float4 x = __ldg(&a.st[2 * i]);
-    const float4 v = __ldg(&a.st[2 * i + 1]);
+    const float4 p = __ldg(&a.sa[i]);
+    const float2 q = __ldg(&a.sb[i]);
+    const float4 x = make_float4(p.x, p.y, p.z, __ldg(&a.w[i]));
+    const float3 v = make_float3(p.w, q.x, q.y);
     const float m = x.w > 0.0f ? 1.0f / x.w : -x.w;     // free: 1/m stored; anchored: -m
     t.ke += 0.5f * m * fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z));
     t.gpe -= m * fmaf(a.gx, x.x, fmaf(a.gy, x.y, a.gz * x.z));
@@ -80,14 +82,14 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy_gather(const EnergyAr
     if (i < a.N) {
         mass_terms(a, i, t);
         const uint4 meta = __ldg(&a.slice[i >> 5]);
-        const float4 xi = __ldg(&a.st[2 * i]);
+        const float4 xi = __ldg(&a.sa[i]);
         const unsigned flen = meta.z & 0xffffu;
         unsigned r = meta.x + ((unsigned)i & 31u);
         float pe = 0.f;
         for (unsigned s = 0; s < flen; ++s, r += 32u) {
             const int j = __ldg(&a.f_nbr[r]);
             if (j < 0) continue;                              // padding slot
-            pe += spring_pe(a, xi, __ldg(&a.st[2 * j]), r);
+            pe += spring_pe(a, xi, __ldg(&a.sa[j]), r);
         }
         t.pe = 0.5f * pe;
     }
@@ -105,14 +107,14 @@ __global__ void __launch_bounds__(kTileMasses) k_energy_tiled(const EnergyArgs a
     if (m < T.y) {
         const int i = T.x + m;
         mass_terms(a, i, t);
-        const float4 xi = __ldg(&a.st[2 * i]);
+        const float4 xi = __ldg(&a.sa[i]);
         float pe = 0.f;
         for (int s = 0; s < R.y; ++s) {
             const unsigned r = (unsigned)R.x + (unsigned)s * kTileMasses + (unsigned)m;
             const unsigned loc = __ldg(&a.t_nbr[r]);
             if (loc == 0xffffu) continue;                     // padding slot
             const int j = (int)loc < T.y ? T.x + (int)loc : __ldg(&a.halo[T.z + (int)loc - T.y]);
-            pe += spring_pe(a, xi, __ldg(&a.st[2 * j]), r);
+            pe += spring_pe(a, xi, __ldg(&a.sa[j]), r);
         }
         t.pe = 0.25f * pe;
     }
@@ -137,11 +139,11 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy_final(const double *p
     if (threadIdx.x < 4) out[threadIdx.x] = s[threadIdx.x][0];
 }
 
-__global__ void k_trace(const float4 *__restrict__ st, const int32_t *__restrict__ idx, int n, float *__restrict__ out)
+__global__ void k_trace(const float4 *__restrict__ sa, const int32_t *__restrict__ idx, int n, float *__restrict__ out)
 {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
-    const float4 p = st[2 * idx[q]];
+    const float4 p = sa[idx[q]];
     out[3 * q] = p.x; out[3 * q + 1] = p.y; out[3 * q + 2] = p.z;
 }
 
@@ -163,10 +165,10 @@ cudaError_t launch_energy(const EnergyArgs &a, double *out, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_trace(const float4 *st, const int32_t *idx, int n, float *out, cudaStream_t s)
+cudaError_t launch_trace(const float4 *sa, const int32_t *idx, int n, float *out, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    k_trace<<<(n + 127) / 128, 128, 0, s>>>(st, idx, n, out);
+    k_trace<<<(n + 127) / 128, 128, 0, s>>>(sa, idx, n, out);
     return cudaGetLastError();
 }
 

@@ -60,9 +60,15 @@ constexpr int kTileStages = 2;     // pipeline depth
 constexpr int kErrNonFinite = 1;   // bits of the device error flag
 constexpr int kErrTimeout = 2;
 
+// State of a single system, packed per mass: a = (x, y, z, vx), b = (vy, vz)
+// (double buffered) and w = 1/m, or -m for an anchored mass (constant):
+// 28 bytes read and 24 written per mass and step.
 struct StepArgs {
-    const float4 *st;    // state at t_n (2 float4 per mass)
-    float4 *sto;         // state at t_{n+1}
+    const float4 *sa;    // state at t_n
+    const float2 *sb;
+    float4 *oa;          // state at t_{n+1}
+    float2 *ob;
+    const float *w;
     const float4 *fext;  // or nullptr
     const uint4 *slice;
     const int32_t *f_nbr;
@@ -92,14 +98,17 @@ struct StepArgs {
     int contact;
     int integrator;      // 0 symplectic Euler, 1 forward Euler, 2 position Verlet, 3 RK4
     int first_step;      // 1 on the first step since creation (Verlet's eq. 5)
-    const float4 *rk_base;   // RK4: the state Y_n of the step (2 float4 per mass)
+    const float4 *rk_ba;     // RK4: the state Y_n of the step (packed as the state)
+    const float2 *rk_bb;
     float4 *rk_acc;          // RK4: weighted sum of the stage slopes (2 float4 per mass)
     int rk_stage;            // RK4: stage 0..3
 };
 
 // Energy reduction (ms_instr.cu) over either record layout.
 struct EnergyArgs {
-    const float4 *st;
+    const float4 *sa;        // packed state, as in StepArgs
+    const float2 *sb;
+    const float *w;
     const uint4 *slice;      // gather layout
     const int32_t *f_nbr;
     const uint16_t *t_nbr;   // tiled layout
@@ -117,18 +126,22 @@ int energy_blocks(const EnergyArgs &a);
 // out (device): kinetic, elastic, gravitational, ground-penalty energy (FP64)
 cudaError_t launch_energy(const EnergyArgs &a, double *out, cudaStream_t s);
 // out[3 q + c] = x[idx[q]][c] for q < n
-cudaError_t launch_trace(const float4 *st, const int32_t *idx, int n, float *out, cudaStream_t s);
+cudaError_t launch_trace(const float4 *sa, const int32_t *idx, int n, float *out, cudaStream_t s);
 
 // Launchers (ms_step.cu, ms_state.cu).
 cudaError_t launch_step(const StepArgs &a, cudaStream_t st);
-cudaError_t launch_gather_state(const float4 *st, const int32_t *perm, int N,
+cudaError_t launch_gather_state(const float4 *sa, const float2 *sb, const int32_t *perm, int N,
                                 float *x_out, float *v_out, cudaStream_t stream);
-cudaError_t launch_scatter_state(float4 *st, const int32_t *perm, int N,
+cudaError_t launch_scatter_state(float4 *sa, float2 *sb, const float *w, const int32_t *perm, int N,
                                  const float *x_in, const float *v_in, cudaStream_t stream);
 // the same, after a device-side finiteness check of the inputs: first_bad
 // (device int) receives the first caller index with a non-finite value, or
 // INT_MAX, and the state is written only when every value is finite
-cudaError_t launch_checked_scatter_state(float4 *st, const int32_t *perm, int N, const float *x_in,
-                                         const float *v_in, int *first_bad, cudaStream_t stream);
+cudaError_t launch_checked_scatter_state(float4 *sa, float2 *sb, const float *w, const int32_t *perm, int N,
+                                         const float *x_in, const float *v_in, int *first_bad, cudaStream_t stream);
+// packed state <-> 2 float4 per mass ((x, w), (v, 0)), for n masses
+cudaError_t launch_pack_state(const float4 *pairs, int n, float4 *sa, float2 *sb, float *w, cudaStream_t stream);
+cudaError_t launch_unpack_state(const float4 *sa, const float2 *sb, const float *w, int n, float4 *pairs,
+                                cudaStream_t stream);
 
 }  // namespace ms

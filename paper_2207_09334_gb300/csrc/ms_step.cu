@@ -25,26 +25,12 @@
 namespace ms {
 
 // Hooke term of eq. 2 plus the axial dashpot, added to (fx, fy, fz) for the
-// mass at xi with partner xj (d = xj - xi):
-//   f = (k (l - L) + c (vj - vi).d / l) d / l.
+// mass at (xi, vi) with the partner's state packed as pa = (x, y, z, vx),
+// pb = (vy, vz) (d = x_partner - x_self):
+//   f = (k (l - L) + c (v_partner - v_self).d / l) d / l.
 // One reciprocal square root serves both l and the unit vector.  The result
 // is an exact negation when the endpoints are swapped, and a spring of zero
 // length (or a padding slot pointing at the mass itself) adds nothing.
-__device__ __forceinline__ void spring_term(const float4 xi, const float4 vi, const float4 xj,
-                                            const float4 vj, float k, float L, float c,
-                                            float &fx, float &fy, float &fz)
-{
-    const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-    const float l2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float il = rsqrtf(l2);
-    const float l = l2 * il;
-    const float rv = fmaf(vj.x - vi.x, dx, fmaf(vj.y - vi.y, dy, (vj.z - vi.z) * dz)) * il;
-    float fs = fmaf(k, l - L, c * rv) * il;     // force magnitude / l
-    fs = (l2 > 0.0f) ? fs : 0.0f;
-    fx = fmaf(fs, dx, fx); fy = fmaf(fs, dy, fy); fz = fmaf(fs, dz, fz);
-}
-
-// The same term with the partner's state packed as (x, y, z, vx), (vy, vz).
 __device__ __forceinline__ void spring_term_packed(const float4 xi, const float4 vi, const float4 pa,
                                                    const float2 pb, float k, float L, float c,
                                                    float &fx, float &fy, float &fz)
@@ -57,6 +43,22 @@ __device__ __forceinline__ void spring_term_packed(const float4 xi, const float4
     float fs = fmaf(k, l - L, c * rv) * il;
     fs = (l2 > 0.0f) ? fs : 0.0f;
     fx = fmaf(fs, dx, fx); fy = fmaf(fs, dy, fy); fz = fmaf(fs, dz, fz);
+}
+
+// Packed state of mass i as the kernels use it: xi = (x, w), vi = (v, 0).
+__device__ __forceinline__ void load_mass(const float4 *sa, const float2 *sb, const float *w, int i, float4 &xi,
+                                          float4 &vi)
+{
+    const float4 p = __ldg(&sa[i]);
+    const float2 q = __ldg(&sb[i]);
+    xi = make_float4(p.x, p.y, p.z, __ldg(&w[i]));
+    vi = make_float4(p.w, q.x, q.y, 0.f);
+}
+
+__device__ __forceinline__ void store_mass(const StepArgs &a, int i, const float4 xn, const float4 vn)
+{
+    a.oa[i] = make_float4(xn.x, xn.y, xn.z, vn.x);
+    a.ob[i] = make_float2(vn.y, vn.z);
 }
 
 // Gravity, external force, ground contact (penalty normal force, Coulomb
@@ -86,7 +88,9 @@ __device__ __forceinline__ void integrate_mass(const StepArgs &a, int i, const f
         // Y_{n+1} = Y_n + h/6 (K_0 + 2 K_1 + 2 K_2 + K_3).
         const int q = a.rk_stage;
         const float ax = fx * w + a.gx, ay = fy * w + a.gy, az = fz * w + a.gz;
-        const float4 bx = __ldg(&a.rk_base[2 * i]), bv = __ldg(&a.rk_base[2 * i + 1]);
+        const float4 ba = __ldg(&a.rk_ba[i]);
+        const float2 bb = __ldg(&a.rk_bb[i]);
+        const float3 bx = make_float3(ba.x, ba.y, ba.z), bv = make_float3(ba.w, bb.x, bb.y);
         float4 sx = make_float4(vi.x, vi.y, vi.z, 0.f), sv = make_float4(ax, ay, az, 0.f);
         if (q > 0) {
             const float wq = q == 3 ? 1.0f : 2.0f;
@@ -146,8 +150,8 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a)
     if (i >= a.N) return;
     const unsigned lane = (unsigned)i & 31u;
     const uint4 meta = __ldg(&a.slice[i >> 5]);
-    const float4 xi = __ldg(&a.st[2 * i]);
-    const float4 vi = __ldg(&a.st[2 * i + 1]);
+    float4 xi, vi;
+    load_mass(a.sa, a.sb, a.w, i, xi, vi);
     float fx = 0.f, fy = 0.f, fz = 0.f;
 
     // springs owned by this mass
@@ -161,7 +165,7 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a)
         float L = kl.y;
         const float c = HAS_C ? __ldg(&a.f_c[r]) : a.c_uniform;
         if (HAS_ACT) { const float2 ab = __ldg(&a.f_ab[r]); L = L * (1.0f + (ab.x * a.s_n + ab.y * a.c_n)); }
-        spring_term(xi, vi, __ldg(&a.st[2 * j]), __ldg(&a.st[2 * j + 1]), kl.x, L, c, fx, fy, fz);
+        spring_term_packed(xi, vi, __ldg(&a.sa[j]), __ldg(&a.sb[j]), kl.x, L, c, fx, fy, fz);
     }
     // springs owned by partners, reached through back references
     unsigned q = meta.y + lane;
@@ -183,13 +187,12 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a)
         float L = kl.y;
         const float c = HAS_C ? __ldg(&a.f_c[rr]) : a.c_uniform;
         if (HAS_ACT) { const float2 ab = __ldg(&a.f_ab[rr]); L = L * (1.0f + (ab.x * a.s_n + ab.y * a.c_n)); }
-        spring_term(xi, vi, __ldg(&a.st[2 * o]), __ldg(&a.st[2 * o + 1]), kl.x, L, c, fx, fy, fz);
+        spring_term_packed(xi, vi, __ldg(&a.sa[o]), __ldg(&a.sb[o]), kl.x, L, c, fx, fy, fz);
     }
 
     float4 xn, vn;
     integrate_mass<HAS_FEXT, RK4>(a, i, xi, vi, fx, fy, fz, xn, vn);
-    a.sto[2 * i] = xn;
-    a.sto[2 * i + 1] = vn;
+    store_mass(a, i, xn, vn);
 }
 
 // ---------------------------------------------------------------------------
@@ -308,16 +311,17 @@ __global__ void __launch_bounds__(kTileMasses) k_step_tiled(const StepArgs a)
     const bool active = tid < nb;
     float4 xi = make_float4(0.f, 0.f, 0.f, 0.f), vi = xi;
     if (active) {
-        xi = __ldg(&a.st[2 * (base + tid)]);
-        vi = __ldg(&a.st[2 * (base + tid) + 1]);
-        spa[tid] = make_float4(xi.x, xi.y, xi.z, vi.x);
-        spb[tid] = make_float2(vi.y, vi.z);
+        const float4 p = __ldg(&a.sa[base + tid]);
+        const float2 q = __ldg(&a.sb[base + tid]);
+        xi = make_float4(p.x, p.y, p.z, __ldg(&a.w[base + tid]));
+        vi = make_float4(p.w, q.x, q.y, 0.f);
+        spa[tid] = p;
+        spb[tid] = q;
     }
     for (int h = tid; h < nh; h += kTileMasses) {
         const int g = __ldg(&a.halo[hoff + h]);
-        const float4 hx = __ldg(&a.st[2 * g]), hv = __ldg(&a.st[2 * g + 1]);
-        spa[nb + h] = make_float4(hx.x, hx.y, hx.z, hv.x);
-        spb[nb + h] = make_float2(hv.y, hv.z);
+        spa[nb + h] = __ldg(&a.sa[g]);
+        spb[nb + h] = __ldg(&a.sb[g]);
     }
     __syncthreads();
     float fx = 0.f, fy = 0.f, fz = 0.f;
@@ -366,8 +370,7 @@ __global__ void __launch_bounds__(kTileMasses) k_step_tiled(const StepArgs a)
     const int i = base + tid;
     float4 xn, vn;
     integrate_mass<HAS_FEXT, RK4>(a, i, xi, vi, fx, fy, fz, xn, vn);
-    a.sto[2 * i] = xn;
-    a.sto[2 * i + 1] = vn;
+    store_mass(a, i, xn, vn);
 }
 
 size_t tiled_smem_bytes(int tile_local, bool has_c, bool has_act)

@@ -168,10 +168,10 @@ __device__ __forceinline__ float warp_sum(float v)
 #ifdef __CUDACC__
 // Persistent single-system run (ms_batch.cu): all nsteps steps of one system
 // of at most kMaxRobotMasses masses in one CTA, state in shared memory,
-// read from and written back to st (2 float4 per mass).  sc holds (sin, cos)
+// read from and written back to the packed state (sa, sb; w constant).  sc holds (sin, cos)
 // of 2 pi f t_n for the nsteps steps, or is nullptr for passive springs.
-cudaError_t launch_persistent(const Records &rec, const Env &env, float4 *st, int n, const float2 *sc,
-                              int nsteps, int *err, cudaStream_t s);
+cudaError_t launch_persistent(const Records &rec, const Env &env, float4 *sa, float2 *sb, const float *w, int n,
+                              const float2 *sc, int nsteps, int *err, cudaStream_t s);
 // (sin, cos)(two_pi_f * (n0 + n) * dt) for n < nsteps.
 void launch_sc_table_from(long long n0, int nsteps, double dt, double two_pi_f, float2 *out, cudaStream_t s);
 #endif
