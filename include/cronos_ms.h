@@ -399,7 +399,9 @@ int64_t mlp_num_params(const mlp_model *m);
 /* host fp32 parameter vector in / out (grads: last computed gradient, may be NULL) */
 ms_status mlp_set_params(mlp_model *m, const float *params);
 ms_status mlp_get_params(mlp_model *m, float *params, float *grads);
-/* load a batch: one-hot encode device materials [B][n_in/4] (ids 0..3), or copy bf16 inputs [B][n_in] */
+/* load a batch: device materials [B][n_in/4] (ids 0..3) to be one-hot encoded (the model keeps a
+ * copy; an inference pass builds the one-hot tiles of X in shared memory inside the first GEMM,
+ * a training pass writes X), or bf16 inputs [B][n_in] (copied) */
 ms_status mlp_encode(mlp_model *m, const uint8_t *materials, int32_t B);
 ms_status mlp_set_input(mlp_model *m, const uint16_t *x_bf16, int32_t B);
 /* predictions of the loaded batch into device y [B] (may be NULL); inference only: the

@@ -41,6 +41,7 @@ constexpr int kBM = 128, kBK = 64;
 constexpr int kStages = 4;
 constexpr int kGemmThreads = 320;   // warp 0 loads, warp 1 issues MMAs, warps 2..9 run the epilogue
 constexpr int kEpiThreads = 256;
+constexpr int kOnehotThreads = 448; // one-hot variant: warps 10..13 build the A tiles
 constexpr uint32_t kTileBytes = kBM * kBK * 2;                  // 16 KB: one 128 x 64 bf16 box
 constexpr uint64_t kWaitNs = 2000000000ull;                       // 2 s
 
@@ -54,6 +55,8 @@ struct GemmArgs {
     __nv_bfloat16 *Z;         // EPI_BIAS_GELU: pre-activation out [M][N] (or nullptr); EPI_DGELU: pre-activation in
     __nv_bfloat16 *H;         // row-major out [M][N] (GELU(z) or dz)
     __nv_bfloat16 *Ht;        // transposed out [N][M] (or nullptr)
+    const uint8_t *mats;      // one-hot A operand: materials [M][n_vox] (ids 0..3), K = 4 n_vox
+    int n_vox;
     int *err;
 };
 
@@ -200,11 +203,35 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *b)
 //   full[s] / empty[s]        shared-memory stage loaded / read by the MMAs
 //   acc_full[a] / acc_empty[a] accumulator a complete / drained by all 256
 //                              epilogue threads
-template <int BN>
-__global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_tc(const __grid_constant__ CUtensorMap mapA,
+// One-hot A tile (ONEHOT): four builder warps write the 128 x 64 bf16 tile of
+// X[b][4 v + m] = (materials[b][v] == m) for 16 voxels straight into shared
+// memory, in the layout a 128-byte-swizzled TMA load of X would give (row r
+// at r * 128 bytes, 16-byte chunk j of the row at chunk j ^ (r mod 8)), so the
+// one-hot matrix never exists in global memory.  Builder thread r owns row r.
+__device__ __forceinline__ uint64_t onehot4(uint32_t m)
+{   // the four bf16 (m == 0, .., m == 3) of one voxel, 1.0 = 0x3f80; all zero for m > 3
+    return m < 4u ? (uint64_t)0x3f80u << (16u * m) : 0ull;
+}
+
+// row r of the tile from its 16 material bytes mv
+__device__ __forceinline__ void build_onehot_row(unsigned char *tile, int r, const uint4 mv)
+{
+    const uint32_t w[4] = {mv.x, mv.y, mv.z, mv.w};
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {                    // chunk j: voxels 2j, 2j + 1
+        const uint64_t a = onehot4((w[j >> 1] >> (16 * (j & 1))) & 0xffu);
+        const uint64_t b = onehot4((w[j >> 1] >> (16 * (j & 1) + 8)) & 0xffu);
+        const uint4 c = make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));
+        *reinterpret_cast<uint4 *>(tile + r * 128 + ((j ^ (r & 7)) << 4)) = c;
+    }
+}
+
+template <int BN, bool ONEHOT>
+__global__ void __launch_bounds__(ONEHOT ? kOnehotThreads : kGemmThreads, 1) k_gemm_tc(const __grid_constant__ CUtensorMap mapA,
                                                              const __grid_constant__ CUtensorMap mapB, const GemmArgs g)
 {
     constexpr uint32_t kStageBytes = kTileBytes * (1 + BN / kBM);   // A tile + BN/128 B boxes
+    constexpr uint32_t kTxBytes = ONEHOT ? kStageBytes - kTileBytes : kStageBytes;   // bytes the TMA brings
     extern __shared__ __align__(1024) unsigned char dyn[];
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_base;
@@ -219,7 +246,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_tc(const __grid_consta
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 32) {
-        for (int s = 0; s < kStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        // full[s]: the TMA thread's expect_tx arrival, plus the 128 builders after writing a one-hot tile
+        for (int s = 0; s < kStages; ++s) { mbar_init(&full[s], ONEHOT ? 1 + kBM : 1); mbar_init(&empty[s], 1); }
         for (int a = 0; a < 2; ++a) { mbar_init(&acc_full[a], 1); mbar_init(&acc_empty[a], kEpiThreads); }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -239,8 +267,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_tc(const __grid_consta
                     const unsigned s = it % kStages;
                     if (it >= (unsigned)kStages && !mbar_wait(&empty[s], ((it / kStages) - 1) & 1)) { ok = false; break; }
                     unsigned char *a = ring + (size_t)s * kStageBytes;
-                    mbar_expect_tx(&full[s], kStageBytes);
-                    tma_load_2d(a, &mapA, kt * kBK, m0, &full[s]);
+                    mbar_expect_tx(&full[s], kTxBytes);
+                    if (!ONEHOT) tma_load_2d(a, &mapA, kt * kBK, m0, &full[s]);
 #pragma unroll
                     for (int q = 0; q < BN / kBM; ++q)
                         tma_load_2d(a + kTileBytes * (1 + q), &mapB, kt * kBK, n0 + q * kBM, &full[s]);
@@ -248,6 +276,27 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_tc(const __grid_consta
             }
             if (!ok) atomicOr(g.err, kErrTimeout);
         }
+    } else if (ONEHOT && warp >= kGemmThreads / 32) {
+        // one-hot builders: thread r writes row r of every A tile, with the
+        // next k-step's material bytes loaded while the current row is built
+        const int r = tid - kGemmThreads;
+        unsigned it = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+            const int m0 = (tile / tiles_n) * kBM;
+            const uint4 *src = reinterpret_cast<const uint4 *>(g.mats + (size_t)(m0 + r) * g.n_vox);
+            uint4 mv = __ldg(&src[0]);
+            for (int kt = 0; kt < KT; ++kt, ++it) {
+                const uint4 next = kt + 1 < KT ? __ldg(&src[kt + 1]) : mv;
+                const unsigned s = it % kStages;
+                if (it >= (unsigned)kStages && !mbar_wait(&empty[s], ((it / kStages) - 1) & 1)) { ok = false; break; }
+                build_onehot_row(ring + (size_t)s * kStageBytes, r, mv);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor core
+                mbar_arrive(&full[s]);
+                mv = next;
+            }
+        }
+        if (!ok && r == 0) atomicOr(g.err, kErrTimeout);
     } else if (warp == 1) {
         if (lane == 0) {
             // MMA issuer
@@ -272,7 +321,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_tc(const __grid_consta
             }
             if (!ok) atomicOr(g.err, kErrTimeout);
         }
-    } else {
+    } else if (warp < kGemmThreads / 32) {
         // epilogue: warp w drains TMEM lanes 32 (w mod 4).. and half (w - 2) / 4 of the columns
         const int quarter = warp & 3, half = (warp - 2) >> 2;
         unsigned lt = 0;
@@ -462,38 +511,52 @@ ms_status make_map(CUtensorMap *map, const void *ptr, int rows, int cols)
     return MS_OK;
 }
 
-ms_status gemm(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, const GemmArgs &proto,
-               cudaStream_t st)
+// C = A . B^T with A [M x K] either a bf16 matrix or, when mats is not null,
+// the one-hot encoding of materials [M][K/4] built in shared memory.
+ms_status gemm_any(const __nv_bfloat16 *A, const uint8_t *mats, const __nv_bfloat16 *B, int M, int N, int K,
+                   const GemmArgs &proto, cudaStream_t st)
 {
     if (M % kBM || N % kBM || K % kBK || M <= 0 || N <= 0 || K <= 0)
         return fail(MS_ERR_ARG, "gemm: M and N must be multiples of 128 and K of 64");
     CUtensorMap ma, mb;
     ms_status s;
-    if ((s = make_map(&ma, A, M, K)) != MS_OK) return s;
     if ((s = make_map(&mb, B, N, K)) != MS_OK) return s;
+    if (mats) ma = mb;                               // unused: the A tiles are built from mats
+    else if ((s = make_map(&ma, A, M, K)) != MS_OK) return s;
     static std::once_flag once;
     static int n_sms = 0;
     std::call_once(once, [] {
-        cudaFuncSetAttribute(k_gemm_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<128>());
-        cudaFuncSetAttribute(k_gemm_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<256>());
+        cudaFuncSetAttribute(k_gemm_tc<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<128>());
+        cudaFuncSetAttribute(k_gemm_tc<256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<256>());
+        cudaFuncSetAttribute(k_gemm_tc<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<128>());
+        cudaFuncSetAttribute(k_gemm_tc<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<256>());
         int dev = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sms < 1) n_sms = 1;
     });
     GemmArgs g = proto;
     g.M = M; g.N = N; g.K = K;
+    g.mats = mats; g.n_vox = K / 4;
     // 128 x 256 tiles halve the A-tile traffic per FLOP; they need N % 256 == 0
     // and enough tiles to give every SM one
     const int t256 = N % 256 == 0 ? (M / kBM) * (N / 256) : 0;
-    if (t256 >= n_sms)
-        k_gemm_tc<256><<<std::min(t256, n_sms), kGemmThreads, gemm_smem<256>(), st>>>(ma, mb, g);
-    else {
-        const int t128 = (M / kBM) * (N / kBM);
-        k_gemm_tc<128><<<std::min(t128, n_sms), kGemmThreads, gemm_smem<128>(), st>>>(ma, mb, g);
+    const int t128 = (M / kBM) * (N / kBM);
+    if (t256 >= n_sms) {
+        if (mats) k_gemm_tc<256, true><<<std::min(t256, n_sms), kOnehotThreads, gemm_smem<256>(), st>>>(ma, mb, g);
+        else k_gemm_tc<256, false><<<std::min(t256, n_sms), kGemmThreads, gemm_smem<256>(), st>>>(ma, mb, g);
+    } else {
+        if (mats) k_gemm_tc<128, true><<<std::min(t128, n_sms), kOnehotThreads, gemm_smem<128>(), st>>>(ma, mb, g);
+        else k_gemm_tc<128, false><<<std::min(t128, n_sms), kGemmThreads, gemm_smem<128>(), st>>>(ma, mb, g);
     }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(MS_ERR_CUDA, std::string("gemm launch: ") + cudaGetErrorString(e));
     return MS_OK;
+}
+
+ms_status gemm(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, const GemmArgs &proto,
+               cudaStream_t st)
+{
+    return gemm_any(A, nullptr, B, M, N, K, proto, st);
 }
 
 }  // namespace
@@ -516,6 +579,10 @@ struct mlp_model {
     __nv_bfloat16 *dZ2 = nullptr, *dZ2t = nullptr, *dZ1 = nullptr, *dZ1t = nullptr;
     float *y = nullptr, *dy = nullptr, *lterm = nullptr, *loss = nullptr;
     int *err = nullptr;
+    // materials of the loaded batch (mlp_encode); X holds their one-hot
+    // encoding only once a pass needs it (x_pending = not yet written)
+    uint8_t *mats = nullptr;
+    bool x_pending = false;
     int64_t t = 0;                     // Adam step
 
     void *dev_alloc(size_t bytes)
@@ -562,15 +629,32 @@ ms_status refresh_bf16(mlp_model *m)
     return MS_OK;
 }
 
-// keep: also store what the backward pass needs (Z1, Z2, H1^T)
+// X = one-hot(materials) for a batch loaded by mlp_encode, if not yet written
+ms_status ensure_x(mlp_model *m, int B)
+{
+    if (!m->x_pending) return MS_OK;
+    k_encode<<<nblk((size_t)B * (m->n_in / 4)), 256, 0, m->stream>>>(m->mats, B, m->n_in / 4, m->X);
+    MLP_CUDA_TRY(cudaGetLastError());
+    m->x_pending = false;
+    return MS_OK;
+}
+
+// keep: also store what the backward pass needs (Z1, Z2, H1^T, and X)
 ms_status forward(mlp_model *m, int B, bool keep)
 {
     GemmArgs g{};
     g.err = m->err;
-    // Z1 = X W1^T + b1, H1 = GELU(Z1) (and H1^T)
+    // Z1 = X W1^T + b1, H1 = GELU(Z1) (and H1^T).  An inference pass on a
+    // batch of materials builds the one-hot X tiles inside the GEMM instead.
     g.epi = EPI_BIAS_GELU; g.bias = m->P + m->off_b1; g.Z = keep ? m->Z1 : nullptr; g.H = m->H1;
     g.Ht = keep ? m->H1t : nullptr;
-    ms_status s = gemm(m->X, m->W1b, B, m->n_h, m->n_in, g, m->stream);
+    ms_status s;
+    if (!keep && m->x_pending) {
+        s = gemm_any(nullptr, m->mats, m->W1b, B, m->n_h, m->n_in, g, m->stream);
+    } else {
+        if ((s = ensure_x(m, B)) != MS_OK) return s;
+        s = gemm(m->X, m->W1b, B, m->n_h, m->n_in, g, m->stream);
+    }
     if (s != MS_OK) return s;
     // Z2 = H1 W2^T + b2, H2 = GELU(Z2)
     g.bias = m->P + m->off_b2; g.Z = keep ? m->Z2 : nullptr; g.H = m->H2; g.Ht = nullptr;
@@ -651,6 +735,8 @@ ms_status mlp_create(int32_t n_in, int32_t n_hidden, int32_t max_batch, uint64_t
     m->dZ1 = mal<__nv_bfloat16>(m, B * H); m->dZ1t = mal<__nv_bfloat16>(m, B * H);
     m->y = mal<float>(m, B); m->dy = mal<float>(m, B); m->lterm = mal<float>(m, B); m->loss = mal<float>(m, 1);
     m->err = mal<int>(m, 1);
+    m->mats = mal<uint8_t>(m, B * (I / 4));
+    if (!m->mats) return fail(MS_ERR_OOM, "device allocation failed");
     if (!m->P || !m->G || !m->Mo || !m->Vo || !m->W1b || !m->W2b || !m->W2tb || !m->X || !m->Xt || !m->Z1 ||
         !m->H1 || !m->H1t || !m->Z2 || !m->H2 || !m->dZ2 || !m->dZ2t || !m->dZ1 || !m->dZ1t || !m->y || !m->dy ||
         !m->lterm || !m->loss || !m->err)
@@ -701,8 +787,9 @@ ms_status mlp_encode(mlp_model *m, const uint8_t *materials, int32_t B)
     if (!m || !materials) return fail(MS_ERR_ARG, "model and materials are required");
     ms_status s = check_batch(m, B);
     if (s != MS_OK) return s;
-    k_encode<<<nblk((size_t)B * (m->n_in / 4)), 256, 0, m->stream>>>(materials, B, m->n_in / 4, m->X);
-    MLP_CUDA_TRY(cudaGetLastError());
+    // keep a copy of the materials; X is encoded when a pass needs it
+    MLP_CUDA_TRY(cudaMemcpyAsync(m->mats, materials, (size_t)B * (m->n_in / 4), cudaMemcpyDeviceToDevice, m->stream));
+    m->x_pending = true;
     return MS_OK;
 }
 
@@ -712,6 +799,7 @@ ms_status mlp_set_input(mlp_model *m, const uint16_t *x_bf16, int32_t B)
     ms_status s = check_batch(m, B);
     if (s != MS_OK) return s;
     MLP_CUDA_TRY(cudaMemcpyAsync(m->X, x_bf16, sizeof(uint16_t) * (size_t)B * m->n_in, cudaMemcpyDeviceToDevice, m->stream));
+    m->x_pending = false;
     return MS_OK;
 }
 

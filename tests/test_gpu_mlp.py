@@ -50,6 +50,27 @@ def test_gemm_wide_tiles_match_fp64(ms, M, N, K):
     assert err <= bound, (err, bound)
 
 
+@pytest.mark.parametrize("B", [1024, 16384])
+def test_onehot_tiles_equal_the_materialised_input(ms, B):
+    """Inference on a batch of materials builds the one-hot A tiles in shared
+    memory (128-byte swizzled) instead of reading X: the predictions equal,
+    bit for bit, those from the same one-hot matrix given as bf16 input.
+    B = 16384 takes the 128 x 256 tiles, B = 1024 the 128 x 128 ones."""
+    import torch
+    rng = np.random.default_rng(B)
+    mats = torch.tensor(rng.integers(0, 4, size=(B, 512)).astype(np.uint8), device="cuda")
+    x = torch.nn.functional.one_hot(mats.long(), 4).reshape(B, 2048).to(torch.bfloat16).contiguous()
+    net = ms.Surrogate(2048, 512, max_batch=16384, seed=3)
+    y1 = torch.empty(B, device="cuda"); y2 = torch.empty(B, device="cuda")
+    net.load_materials(mats)
+    net.forward(B, y1)
+    net.load_input(x)
+    net.forward(B, y2)
+    net.sync()
+    assert torch.equal(y1, y2)
+    net.close()
+
+
 def _mlp_case(ms, B=256, n_in=2048, h=512, seed=1):
     import torch
     rng = np.random.default_rng(seed)
