@@ -805,6 +805,7 @@ ms_status mlp_set_input(mlp_model *m, const uint16_t *x_bf16, int32_t B)
 
 ms_status mlp_forward(mlp_model *m, int32_t B, float *y)
 {
+    ms::Range range_("mlp_forward");
     if (!m) return fail(MS_ERR_ARG, "model is NULL");
     ms_status s = check_batch(m, B);
     if (s != MS_OK) return s;
@@ -815,6 +816,7 @@ ms_status mlp_forward(mlp_model *m, int32_t B, float *y)
 
 ms_status mlp_backward(mlp_model *m, const float *target, int32_t B, float *loss)
 {
+    ms::Range range_("mlp_backward");
     if (!m || !target) return fail(MS_ERR_ARG, "model and target are required");
     ms_status s = check_batch(m, B);
     if (s != MS_OK) return s;
@@ -826,6 +828,7 @@ ms_status mlp_backward(mlp_model *m, const float *target, int32_t B, float *loss
 
 ms_status mlp_adam(mlp_model *m, float lr, float beta1, float beta2, float eps)
 {
+    ms::Range range_("mlp_adam");
     if (!m) return fail(MS_ERR_ARG, "model is NULL");
     m->t += 1;
     const float c1 = 1.f - (float)std::pow((double)beta1, (double)m->t), c2 = 1.f - (float)std::pow((double)beta2, (double)m->t);

@@ -453,6 +453,7 @@ ms_status msa_create(const ms_params *p, const msb_voxel_spec *spec, int32_t n_r
 ms_status msa_gradients(msa_adjoint *b, int32_t nsteps, const float *phase, const float *logk,
                         const float *seed_x, float *loss, float *g_phase, float *g_logk, int32_t on_device)
 {
+    ms::Range range_("msa_gradients");
     if (!b || !phase || !logk || !loss || !g_phase || !g_logk) return fail(MS_ERR_ARG, "missing argument");
     if (nsteps < 1 || nsteps > b->max_steps) return fail(MS_ERR_ARG, "nsteps must be in [1, max_steps]");
     const cudaMemcpyKind in = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;

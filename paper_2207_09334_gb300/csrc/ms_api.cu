@@ -654,6 +654,7 @@ ms_status ms_set_actuation(ms_sim *s, float freq_hz, const float *amp, const flo
 
 ms_status ms_step(ms_sim *s, int32_t nsteps)
 {
+    ms::Range range_("ms_step");
     if (!s) return fail(MS_ERR_ARG, "sim is NULL");
     if (nsteps < 0) return fail(MS_ERR_ARG, "nsteps must be >= 0");
     const double two_pi_f = 2.0 * M_PI * s->freq;
@@ -730,6 +731,7 @@ ms_status ms_step(ms_sim *s, int32_t nsteps)
 
 ms_status ms_get_state(ms_sim *s, float *x, float *v, int32_t on_device)
 {
+    ms::Range range_("ms_get_state");
     if (!s) return fail(MS_ERR_ARG, "sim is NULL");
     const int N = s->N;
     if (on_device) {
@@ -745,6 +747,7 @@ ms_status ms_get_state(ms_sim *s, float *x, float *v, int32_t on_device)
 
 ms_status ms_set_state(ms_sim *s, const float *x, const float *v, int32_t on_device)
 {
+    ms::Range range_("ms_set_state");
     if (!s) return fail(MS_ERR_ARG, "sim is NULL");
     const int N = s->N;
     if (on_device) {
@@ -777,6 +780,7 @@ ms_status ms_sync(ms_sim *s)
 
 ms_status ms_energy(ms_sim *s, double *out, int32_t on_device)
 {
+    ms::Range range_("ms_energy");
     if (!s || !out) return fail(MS_ERR_ARG, "sim or out is NULL");
     ms::EnergyArgs a{};
     a.sa = s->sa[s->cur]; a.sb = s->sb[s->cur]; a.w = s->w;

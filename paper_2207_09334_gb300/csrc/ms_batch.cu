@@ -740,6 +740,7 @@ ms_status msb_create(const ms_params *p, const msb_voxel_spec *spec, int32_t n_r
 
 ms_status msb_run(msb_batch *b, int32_t nsteps)
 {
+    ms::Range range_("msb_run");
     if (!b) return fail(MS_ERR_ARG, "batch is NULL");
     if (nsteps < 0) return fail(MS_ERR_ARG, "nsteps must be >= 0");
     if (nsteps == 0) return MS_OK;
@@ -766,6 +767,7 @@ ms_status msb_run(msb_batch *b, int32_t nsteps)
 
 ms_status msb_run_loop(msb_batch *b, int32_t nsteps)
 {
+    ms::Range range_("msb_run_loop");
     if (!b) return fail(MS_ERR_ARG, "batch is NULL");
     if (nsteps < 0) return fail(MS_ERR_ARG, "nsteps must be >= 0");
     if (!b->loop_w) {
@@ -815,6 +817,7 @@ ms_status msb_run_loop(msb_batch *b, int32_t nsteps)
 
 ms_status msb_autotune(msb_batch *b, int32_t sample_steps, int32_t policy)
 {
+    ms::Range range_("msb_autotune");
     if (!b) return fail(MS_ERR_ARG, "batch is NULL");
     if (policy < 0 || policy > 2) return fail(MS_ERR_ARG, "policy must be 0, 1 or 2");
     const size_t smem_limit = 200 * 1024;

@@ -8,7 +8,19 @@
 
 #include "cronos_ms.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace ms {
+
+// An NVTX range around one API call, for timeline profilers (Nsight
+// Systems).  NVTX is header-only: without an attached tool a range costs a
+// check of a function pointer.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 // Records msg as the calling thread's last error and returns st (ms_api.cu).
 ms_status fail(ms_status st, const std::string &msg);
