@@ -71,8 +71,12 @@ typedef struct {
                                2 = caller order */
     int32_t kernel;         /* 0 = library default: tiled (gather when a tile's partners do not fit
                                shared memory); 1 = gather, 2 = tiled (MS_ERR_ARG if a tile does not fit),
-                               3 = persistent (all steps of one ms_step call in one launch, the state in
-                               shared memory; MS_ERR_ARG beyond 4096 masses or with external force) */
+                               3 = persistent: all steps of one ms_step call in one launch of a
+                               thread-block cluster (one CTA per 256 masses, at most 16), with the
+                               state and the spring records in shared memory and partners in other
+                               CTAs read through distributed shared memory; for small systems.
+                               MS_ERR_ARG beyond 4096 masses, about 40 springs per mass, or with
+                               an integrator other than symplectic Euler */
 } ms_params;
 
 /* Optional device allocator (e.g. a framework's caching allocator).

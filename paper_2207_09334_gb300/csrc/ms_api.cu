@@ -94,7 +94,13 @@ struct ms_sim {
     uint32_t *b_ent = nullptr;
     // tiled layout
     int kernel = 0;                     // ms::kKernelGather or ms::kKernelTiled (record layout)
-    bool persistent = false;            // gather layout stepped by one persistent CTA
+    bool persistent = false;            // stepped by the persistent cluster kernel (ms_cluster.cu)
+    uint16_t *cl_nbr = nullptr;         // its records (both directions, per tile slot-major)
+    float2 *cl_kl = nullptr, *cl_ab = nullptr;
+    float *cl_c = nullptr;
+    int cl_slots = 0;
+    int64_t cl_n = 0;
+    std::vector<uint32_t> cl_slot_a, cl_slot_b;   // merged record -> its two cluster slots
     float2 *sc = nullptr;               // (sin, cos) table of a persistent multi-step call
     int sc_cap = 0;
     int n_tiles = 0, max_tile_local = 0;
@@ -231,9 +237,9 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
     s->c_uniform = c_uniform;
 
     if (p->kernel < 0 || p->kernel > 3 || p->reorder < 0 || p->reorder > 2) return fail(MS_ERR_ARG, "kernel must be 0..3 and reorder 0..2");
-    const bool small = N <= ms::kMaxRobotMasses && !fext && p->integrator == 0;
+    const bool small = N <= ms::kClMasses * ms::kClusterMax && p->integrator == 0;
     if (p->kernel == 3 && !small)
-        return fail(MS_ERR_ARG, "the persistent kernel takes at most 4096 masses, no external force and symplectic Euler");
+        return fail(MS_ERR_ARG, "the persistent kernel takes at most 4096 masses and symplectic Euler");
     s->kernel = p->kernel == 1 ? ms::kKernelGather
               : p->kernel == 2 ? ms::kKernelTiled
               : p->kernel == 3 ? ms::kKernelPersistent
@@ -244,7 +250,7 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
     // 1. mass order
     s->perm.resize(N); s->iperm.resize(N);
     for (int32_t i = 0; i < N; ++i) s->perm[i] = i;
-    const bool morton = p->reorder == 1 || (p->reorder == 0 && s->kernel == ms::kKernelTiled);
+    const bool morton = p->reorder == 1 || (p->reorder == 0 && (s->kernel == ms::kKernelTiled || persistent));
     if (morton) {
         float lo[3] = {x0[0], x0[1], x0[2]}, hi[3] = {x0[0], x0[1], x0[2]};
         for (int32_t i = 0; i < N; ++i)
@@ -525,18 +531,59 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
                 const int32_t j = rec_partner[m];
                 const int t = bfill[j]++;
                 const uint32_t slot = (uint32_t)(m - rec_first[o]);
-                // the persistent kernel runs the robot routines, whose back
-                // references hold the owner's record directly (robot-local form)
-                h_b[sl[j >> 5].bwd_off + 32u * (uint32_t)t + (uint32_t)(j & 31)] =
-                    persistent ? (uint32_t)o | ((sl[o >> 5].fwd_off - sl[0].fwd_off + 32u * slot + (uint32_t)(o & 31))
-                                                << ms::kRobotOwnerBits)
-                               : (uint32_t)o | (slot << ms::kOwnerBits);
+                h_b[sl[j >> 5].bwd_off + 32u * (uint32_t)t + (uint32_t)(j & 31)] = (uint32_t)o | (slot << ms::kOwnerBits);
             }
     }
     s->n_slots = n_slots;
     s->persistent = persistent && s->kernel == ms::kKernelGather;
     s->rec_slot_a.swap(slot_a);
     s->rec_slot_b.swap(slot_b);
+
+    // persistent cluster layout: tiles of kClMasses masses; every mass lists
+    // all of its springs (both directions), slot-major per tile, the partner
+    // coded (tile << 8) | member
+    std::vector<uint16_t> c_nbr;
+    std::vector<float2> c_kl;
+    std::vector<float> c_c;
+    if (s->persistent) {
+        const int CM = ms::kClMasses;
+        const int tiles = (N + CM - 1) / CM;
+        std::vector<std::vector<std::pair<int32_t, uint32_t>>> inc(N);   // (partner, record)
+        for (int32_t o = 0; o < N; ++o)
+            for (int64_t m = rec_first[o]; m < rec_first[o + 1]; ++m) {
+                inc[o].push_back({rec_partner[m], (uint32_t)m});
+                inc[rec_partner[m]].push_back({o, (uint32_t)m});
+            }
+        int slots = 1;
+        for (int32_t i = 0; i < N; ++i) slots = std::max<int>(slots, (int)inc[i].size());
+        if (ms::cluster_smem_bytes(slots, c != nullptr, true) > 227 * 1024)
+            return fail(MS_ERR_ARG, "the persistent kernel holds at most about 40 springs per mass in shared memory; a mass has " +
+                                        std::to_string(slots));
+        const size_t per_tile = (size_t)slots * CM;
+        c_nbr.assign((size_t)tiles * per_tile, 0);
+        c_kl.assign((size_t)tiles * per_tile, make_float2(0.f, 0.f));
+        if (c) c_c.assign((size_t)tiles * per_tile, 0.f);
+        s->cl_slot_a.assign(n_rec, UINT32_MAX);
+        s->cl_slot_b.assign(n_rec, UINT32_MAX);
+        for (int32_t i = 0; i < N; ++i) {
+            const int t = i / CM, mi = i % CM;
+            for (int q = 0; q < slots; ++q) {
+                const size_t r = (size_t)t * per_tile + (size_t)q * CM + mi;
+                if (q < (int)inc[i].size()) {
+                    const int32_t j = inc[i][q].first;
+                    const uint32_t m = inc[i][q].second;
+                    c_nbr[r] = (uint16_t)(((j / CM) << 8) | (j % CM));
+                    c_kl[r] = rec_kl[m];
+                    if (c) c_c[r] = rec_c[m];
+                    if (s->cl_slot_a[m] == UINT32_MAX) s->cl_slot_a[m] = (uint32_t)r; else s->cl_slot_b[m] = (uint32_t)r;
+                } else {
+                    c_nbr[r] = (uint16_t)((t << 8) | mi);       // padding: the mass itself, (k, L0) = 0
+                }
+            }
+        }
+        s->cl_slots = slots;
+        s->cl_n = (int64_t)tiles * per_tile;
+    }
 
     // masses
     std::vector<float4> ha(N), hf;
@@ -592,6 +639,11 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
     }
     if (s->permuted && (st = upload(s, &s->d_perm, s->perm.data(), N)) != MS_OK) return st;
     if ((st = upload<float>(s, &s->stage, nullptr, (size_t)N * 6)) != MS_OK) return st;
+    if (s->persistent) {
+        if ((st = upload(s, &s->cl_nbr, c_nbr.data(), c_nbr.size())) != MS_OK) return st;
+        if ((st = upload(s, &s->cl_kl, c_kl.data(), c_kl.size())) != MS_OK) return st;
+        if (c && (st = upload(s, &s->cl_c, c_c.data(), c_c.size())) != MS_OK) return st;
+    }
     if (p->integrator == 3) {
         for (int q = 0; q < 2; ++q) {
             if ((st = upload<float4>(s, &s->rk_a[q], nullptr, (size_t)N)) != MS_OK) return st;
@@ -646,6 +698,18 @@ ms_status ms_set_actuation(ms_sim *s, float freq_hz, const float *amp, const flo
     ms_status st;
     if (!s->f_ab && (st = upload<float2>(s, &s->f_ab, nullptr, n)) != MS_OK) return st;
     MS_CUDA_TRY(cudaMemcpyAsync(s->f_ab, ab.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, s->stream));
+    std::vector<float2> cab;
+    if (s->persistent) {
+        cab.assign(s->cl_n, make_float2(0.f, 0.f));
+        for (int64_t m = 0; m < nrec; ++m) {
+            if (!(s->rec_KL[m] > 0)) continue;
+            const float2 v = make_float2((float)(sa[m] / s->rec_KL[m]), (float)(sb[m] / s->rec_KL[m]));
+            if (s->cl_slot_a[m] != UINT32_MAX) cab[s->cl_slot_a[m]] = v;
+            if (s->cl_slot_b[m] != UINT32_MAX) cab[s->cl_slot_b[m]] = v;
+        }
+        if (!s->cl_ab && (st = upload<float2>(s, &s->cl_ab, nullptr, (size_t)s->cl_n)) != MS_OK) return st;
+        MS_CUDA_TRY(cudaMemcpyAsync(s->cl_ab, cab.data(), sizeof(float2) * (size_t)s->cl_n, cudaMemcpyHostToDevice, s->stream));
+    }
     MS_CUDA_TRY(cudaStreamSynchronize(s->stream));
     s->actuated = true;
     s->freq = freq_hz;
@@ -671,9 +735,12 @@ ms_status ms_step(ms_sim *s, int32_t nsteps)
             MS_CUDA_TRY(cudaGetLastError());
             sc = s->sc;
         }
-        ms::Records rec{s->slice, s->f_nbr, s->f_kl, s->f_c, s->actuated ? s->f_ab : nullptr, s->b_ent, s->c_uniform};
-        MS_CUDA_TRY(ms::launch_persistent(rec, ms::make_env(s->p), s->sa[s->cur], s->sb[s->cur], s->w, s->N, sc, nsteps,
-                                          s->err, s->stream));
+        ms::ClusterArgs ca{};
+        ca.sa = s->sa[s->cur]; ca.sb = s->sb[s->cur]; ca.w = s->w; ca.fext = s->fext;
+        ca.nbr = s->cl_nbr; ca.kl = s->cl_kl; ca.c = s->cl_c; ca.ab = s->actuated ? s->cl_ab : nullptr;
+        ca.c_uniform = s->c_uniform; ca.N = s->N; ca.slots = s->cl_slots;
+        ca.sc = sc; ca.nsteps = nsteps; ca.env = ms::make_env(s->p); ca.err = s->err;
+        MS_CUDA_TRY(ms::launch_cluster(ca, s->stream));
         s->step_count += nsteps;
         return MS_OK;
     }

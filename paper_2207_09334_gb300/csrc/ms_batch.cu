@@ -169,45 +169,6 @@ __global__ void k_sc_table_from(long long n0, int nsteps, double dt, double two_
     out[n] = make_float2((float)s, (float)c);
 }
 
-// All steps of one small system in one CTA (the robot step, block mode).  The
-// system's state is packed as the single-system step keeps it: sa = (x, vx),
-// sb = (vy, vz), w = 1/m or -m.
-__global__ void __launch_bounds__(kBatchThreads) k_persistent(const Records rec, const Env env, float4 *sa, float2 *sb,
-                                                              const float *w, int n, const float2 *sc, int nsteps,
-                                                              int *err)
-{
-    extern __shared__ float4 smem[];
-    float4 *xs = smem, *vs = smem + n, *fs = smem + 2 * n;
-    const int tid = threadIdx.x;
-    const unsigned rec_base = __ldg(&rec.slice[0].x);
-    for (int i = tid; i < n; i += kBatchThreads) {
-        const float4 p = sa[i];
-        const float2 q = sb[i];
-        xs[i] = make_float4(p.x, p.y, p.z, w[i]);
-        vs[i] = make_float4(p.w, q.x, q.y, 0.f);
-    }
-    __syncthreads();
-    for (int step = 0; step < nsteps; ++step) {
-        const float2 t = sc ? __ldg(&sc[step]) : make_float2(0.f, 0.f);
-        for (int i = tid; i < n; i += kBatchThreads) fs[i] = robot_force<4>(rec, 0, rec_base, i, xs, vs, t.x, t.y);
-        __syncthreads();
-        for (int i = tid; i < n; i += kBatchThreads) {
-            float4 x = xs[i], v = vs[i];
-            robot_integrate(env, x, v, fs[i]);
-            xs[i] = x; vs[i] = v;
-        }
-        __syncthreads();
-    }
-    bool bad = false;
-    for (int i = tid; i < n; i += kBatchThreads) {
-        const float4 x = xs[i], v = vs[i];
-        sa[i] = make_float4(x.x, x.y, x.z, v.x);
-        sb[i] = make_float2(v.y, v.z);
-        bad |= !isfinite(x.x + x.y + x.z + v.x + v.y + v.z);
-    }
-    if (__syncthreads_or(bad) && tid == 0) atomicOr(err, kErrNonFinite);
-}
-
 // Centre-of-mass x travel of every robot from the global state (one CTA per robot).
 __global__ void k_com_travel(const RobotDev *robots, const float4 *st, float *travel)
 {
@@ -471,17 +432,6 @@ void launch_sc_table_from(long long n0, int nsteps, double dt, double two_pi_f, 
     if (nsteps > 0) k_sc_table_from<<<(nsteps + 255) / 256, 256, 0, s>>>(n0, nsteps, dt, two_pi_f, out);
 }
 
-cudaError_t launch_persistent(const Records &rec, const Env &env, float4 *sa, float2 *sb, const float *w, int n,
-                              const float2 *sc, int nsteps, int *err, cudaStream_t s)
-{
-    if (n <= 0 || nsteps <= 0) return cudaSuccess;
-    if (n > kMaxRobotMasses) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)n * 3 * sizeof(float4);
-    cudaError_t e = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_persistent<<<1, kBatchThreads, smem, s>>>(rec, env, sa, sb, w, n, sc, nsteps, err);
-    return cudaGetLastError();
-}
 
 ms_status build_voxels(const msb_voxel_spec *spec, int n_robots, const int32_t *dims, const uint8_t *materials,
                        const float *phase, const float *logk, bool adjoint_maps, VoxelBuild &out)

@@ -64,6 +64,32 @@ inline Env make_env(const ms_params &p)
     return e;
 }
 
+// Persistent cluster step (ms_cluster.cu): tiles of kClMasses masses, one
+// CTA each, at most kClusterMax CTAs in one cluster.
+constexpr int kClMasses = 256;
+constexpr int kClusterMax = 16;
+
+struct ClusterArgs {
+    float4 *sa;              // packed state (internal order): read at the start, written at the end
+    float2 *sb;
+    const float *w;          // 1/m, or -m for an anchored mass
+    const float4 *fext;      // or nullptr
+    // records, both directions, per tile slot-major: [tile][slot][kClMasses];
+    // partner coded (tile << 8) | member, padding = the mass itself with (k, L0) = 0
+    const uint16_t *nbr;
+    const float2 *kl;
+    const float *c;          // or nullptr (then c_uniform)
+    const float2 *ab;        // or nullptr (passive)
+    float c_uniform;
+    int N, slots;
+    const float2 *sc;        // (sin, cos)(2 pi f t_n) for the nsteps steps, if ab
+    int nsteps;
+    Env env;
+    int *err;
+};
+size_t cluster_smem_bytes(int slots, bool has_c, bool has_act);
+cudaError_t launch_cluster(const ClusterArgs &a, cudaStream_t st);
+
 #ifdef __CUDACC__
 // Spring records of a population (device pointers).
 struct Records {
@@ -166,12 +192,7 @@ __device__ __forceinline__ float warp_sum(float v)
 #endif  // __CUDACC__
 
 #ifdef __CUDACC__
-// Persistent single-system run (ms_batch.cu): all nsteps steps of one system
-// of at most kMaxRobotMasses masses in one CTA, state in shared memory,
-// read from and written back to the packed state (sa, sb; w constant).  sc holds (sin, cos)
-// of 2 pi f t_n for the nsteps steps, or is nullptr for passive springs.
-cudaError_t launch_persistent(const Records &rec, const Env &env, float4 *sa, float2 *sb, const float *w, int n,
-                              const float2 *sc, int nsteps, int *err, cudaStream_t s);
+
 // (sin, cos)(two_pi_f * (n0 + n) * dt) for n < nsteps.
 void launch_sc_table_from(long long n0, int nsteps, double dt, double two_pi_f, float2 *out, cudaStream_t s);
 #endif

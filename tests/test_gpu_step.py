@@ -46,8 +46,8 @@ KERNELS = ["gather", "tiled", "persistent"]
 
 
 def gpu_run(ms, s, p, n, reorder=None, chunks=1, kernel=None):
-    if kernel == "persistent" and (s["x"].shape[0] > 4096 or s.get("fext") is not None):
-        pytest.skip("the persistent kernel takes at most 4096 masses and no external force")
+    if kernel == "persistent" and s["x"].shape[0] > 4096:
+        pytest.skip("the persistent kernel takes at most 4096 masses")
     with ms.Sim(s, p, reorder=reorder, kernel=kernel) as sim:
         done = 0
         for q in range(chunks):
@@ -337,3 +337,21 @@ def test_set_state_rejects_non_finite_host_input_and_keeps_the_state(ms):
         sim.set_state(x0 + np.float32(1e-4), v0)          # a finite state is accepted
         x2, _ = sim.get_state()
         assert np.allclose(x2, x0 + np.float32(1e-4))
+
+
+def test_persistent_cluster_of_16_tiles(ms, ora):
+    """4096 masses: the persistent kernel's largest cluster (16 CTAs of 256
+    masses, non-portable cluster size), against the oracle; actuated, with
+    contact and friction, over two calls."""
+    s = synth.soft_cube(n=16, z0=0.001)
+    rng = np.random.default_rng(17)
+    S = s["ij"].shape[0]
+    s["A"] = rng.uniform(0, 0.1, S).astype(np.float32)
+    s["phi"] = rng.uniform(0, 2 * np.pi, S).astype(np.float32)
+    s["freq"] = 5.0
+    s["v"][:] = np.array([0.2, 0.0, -0.3], np.float32)
+    p = synth.soft_cube_params(contact=True)
+    xg, _ = gpu_run(ms, s, p, 200, chunks=2, kernel="persistent")
+    xo, _ = ora.run(s, f32p(p), 200)
+    err = np.abs(xg - xo).max()
+    assert err <= 1e-4 * body_size(s), (err, 1e-4 * body_size(s))
