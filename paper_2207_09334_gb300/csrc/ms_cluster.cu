@@ -15,8 +15,11 @@
 // (distributed shared memory, through the generic address of the remote
 // buffer).  The only synchronisation is one cluster barrier per step, after
 // which every CTA may read the new buffer and overwrite the old one.
-// Integration is symplectic Euler with gravity, external force, ground
-// contact, Coulomb friction and global damping (the robot routines).
+// Each mass has kClLanes threads: lane l sums the springs of slots l,
+// l + kClLanes, ..., and the lanes' partial forces are combined by shuffles in
+// a fixed order, so a step's latency is a quarter of one thread walking every
+// spring.  Integration is symplectic Euler with gravity, external force,
+// ground contact, Coulomb friction and global damping (the robot routines).
 #include <cooperative_groups.h>
 
 #include "ms_internal.h"
@@ -27,8 +30,11 @@ namespace {
 
 namespace cg = cooperative_groups;
 
+constexpr int kClLanes = 4;                          // threads per mass
+constexpr int kClThreads = kClMasses * kClLanes;
+
 template <bool HAS_C, bool HAS_ACT, bool HAS_FEXT>
-__global__ void __launch_bounds__(kClMasses) k_cluster(const ClusterArgs a)
+__global__ void __launch_bounds__(kClThreads) k_cluster(const ClusterArgs a)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ const float4 *rem_a[kClusterMax];   // buffer 0 of every CTA's state (generic addresses)
@@ -49,19 +55,21 @@ __global__ void __launch_bounds__(kClMasses) k_cluster(const ClusterArgs a)
 
     // records of this tile, once per call
     const size_t off = (size_t)rank * nrec;
-    for (size_t e = tid; e < nrec; e += kClMasses) {
+    for (size_t e = tid; e < nrec; e += kClThreads) {
         rn[e] = __ldg(&a.nbr[off + e]);
         rkl[e] = __ldg(&a.kl[off + e]);
         if (HAS_C) rc[e] = __ldg(&a.c[off + e]);
         if (HAS_ACT) rab[e] = __ldg(&a.ab[off + e]);
     }
+    const int mi = tid / kClLanes, lane = tid % kClLanes;  // this thread's mass and slot lane
+    const bool owner = mi < nb;
     float w = 0.f;
     float4 fe = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (tid < nb) {
-        sa[tid] = a.sa[base + tid];
-        sb[tid] = a.sb[base + tid];
-        w = __ldg(&a.w[base + tid]);
-        if (HAS_FEXT) fe = __ldg(&a.fext[base + tid]);
+    if (owner && lane == 0) {
+        sa[mi] = a.sa[base + mi];
+        sb[mi] = a.sb[base + mi];
+        w = __ldg(&a.w[base + mi]);
+        if (HAS_FEXT) fe = __ldg(&a.fext[base + mi]);
     }
     if (tid < (int)cl.num_blocks()) {
         rem_a[tid] = cl.map_shared_rank(sa, tid);
@@ -72,15 +80,18 @@ __global__ void __launch_bounds__(kClMasses) k_cluster(const ClusterArgs a)
     bool bad = false;
     for (int step = 0; step < a.nsteps; ++step) {
         const unsigned cur = (unsigned)step & 1u;
-        if (tid < nb) {
-            const float4 p = sa[cur * kClMasses + tid];
-            const float2 q = sb[cur * kClMasses + tid];
-            float4 x = make_float4(p.x, p.y, p.z, w), v = make_float4(p.w, q.x, q.y, 0.f);
+        float fx = 0.f, fy = 0.f, fz = 0.f;
+        float4 x = make_float4(0.f, 0.f, 0.f, w), v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (owner) {
+            const float4 p = sa[cur * kClMasses + mi];
+            const float2 q = sb[cur * kClMasses + mi];
+            x = make_float4(p.x, p.y, p.z, w);
+            v = make_float4(p.w, q.x, q.y, 0.f);
             float s_n = 0.f, c_n = 0.f;
             if (HAS_ACT) { const float2 t = __ldg(&a.sc[step]); s_n = t.x; c_n = t.y; }
-            float fx = fe.x, fy = fe.y, fz = fe.z;
-            for (int s = 0; s < slots; ++s) {
-                const unsigned e = (unsigned)s * kClMasses + tid;
+#pragma unroll 2
+            for (int s = lane; s < slots; s += kClLanes) {
+                const unsigned e = (unsigned)s * kClMasses + mi;
                 const unsigned code = rn[e];
                 const unsigned pt = code >> 8, pm = cur * kClMasses + (code & 0xffu);
                 const float4 pa = rem_a[pt][pm];
@@ -99,17 +110,26 @@ __global__ void __launch_bounds__(kClMasses) k_cluster(const ClusterArgs a)
                 fs = (l2 > 0.0f) ? fs : 0.0f;
                 fx = fmaf(fs, dx, fx); fy = fmaf(fs, dy, fy); fz = fmaf(fs, dz, fz);
             }
-            robot_integrate(a.env, x, v, make_float4(fx, fy, fz, 0.f));
-            sa[(cur ^ 1u) * kClMasses + tid] = make_float4(x.x, x.y, x.z, v.x);
-            sb[(cur ^ 1u) * kClMasses + tid] = make_float2(v.y, v.z);
+        }
+        // combine the lanes of each mass (fixed order: pairs, then pairs of pairs)
+#pragma unroll
+        for (int o = 1; o < kClLanes; o <<= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, o);
+            fy += __shfl_xor_sync(0xffffffffu, fy, o);
+            fz += __shfl_xor_sync(0xffffffffu, fz, o);
+        }
+        if (owner && lane == 0) {
+            robot_integrate(a.env, x, v, make_float4(fx + fe.x, fy + fe.y, fz + fe.z, 0.f));
+            sa[(cur ^ 1u) * kClMasses + mi] = make_float4(x.x, x.y, x.z, v.x);
+            sb[(cur ^ 1u) * kClMasses + mi] = make_float2(v.y, v.z);
             bad |= !isfinite(x.x + x.y + x.z + v.x + v.y + v.z);
         }
         cl.sync();                                  // the new state is complete in every tile
     }
-    if (tid < nb) {
+    if (owner && lane == 0) {
         const unsigned fin = (unsigned)a.nsteps & 1u;
-        a.sa[base + tid] = sa[fin * kClMasses + tid];
-        a.sb[base + tid] = sb[fin * kClMasses + tid];
+        a.sa[base + mi] = sa[fin * kClMasses + mi];
+        a.sb[base + mi] = sb[fin * kClMasses + mi];
     }
     if (__syncthreads_or(bad) && tid == 0) atomicOr(a.err, kErrNonFinite);
     cl.sync();                                      // no CTA leaves while others may read its memory
@@ -133,7 +153,7 @@ cudaError_t launch_cluster(const ClusterArgs &a, cudaStream_t st)
     const size_t smem = cluster_smem_bytes(a.slots, hc, ha);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)tiles);
-    cfg.blockDim = dim3(kClMasses);
+    cfg.blockDim = dim3(kClThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
