@@ -594,6 +594,55 @@ def run_cube(args, world, rank, local):
     return 0
 
 
+def run_sweep(args, world, rank, local):
+    """Element update rate against system size (the paper's rate-vs-size
+    experiment): throughput lattices of n^3 masses, the default kernel, and the
+    persistent cluster kernel where the system fits it (<= 4096 masses)."""
+    import torch
+    import paper_2207_09334_gb300 as ms
+    torch.cuda.set_device(local)
+    ms.load()
+    stream = torch.cuda.current_stream()
+    reps = Replicas(world)
+    rows = []
+    for n in args.sweep_sizes:
+        s, p = lattice_workload(n)
+        N, S = s["x"].shape[0], s["ij"].shape[0]
+        kernels = ["auto"] + (["persistent"] if N <= 4096 else [])
+        for kernel in kernels:
+            with ms.Sim(s, p, kernel=None if kernel == "auto" else kernel, stream=stream) as sim:
+                steps = max(20, min(2000, int(2e9 // (N + S))))     # about 2e9 element updates per point
+                sim.step(max(3, steps // 10))
+                sim.sync()
+                e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+                reps.barrier()
+                torch.cuda.synchronize()
+                e0.record(stream)
+                if kernel == "persistent":
+                    sim.step(steps)
+                else:
+                    for _ in range(steps):
+                        sim.step(1)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                reps.barrier()
+                t = e0.elapsed_time(e1) * 1e-3
+                rows.append({"n": n, "masses": N, "springs": S, "kernel": ["", "gather", "tiled", "persistent"][sim.info()["kernel"]],
+                             "steps": steps, "us_per_step": reps.max(t) * 1e6 / steps,
+                             "elements_per_s": reps.throughput((N + S) * steps, t)})
+    best = max(r["elements_per_s"] for r in rows)
+    line = {"metric": "element updates/s vs system size", "value": best, "unit": "elements/s", "n_gpus": world,
+            "steps": None, "warmup": None, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+            "config": {"workload": "throughput lattices n^3 (the 256^3 workload's parameters), default kernel and, up to "
+                                   "4096 masses, the persistent cluster kernel", "sizes": list(args.sweep_sizes)},
+            "points": rows}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    reps.close()
+    return 0
+
+
 def run_adjoint(args, world, rank, local):
     """Differentiable batch: 256 walkers of 8^3 voxels, loss = centre-of-mass
     x-travel after 2000 steps, gradients w.r.t. every voxel's phase and
@@ -662,8 +711,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--ref-side", type=int, default=40)
-    ap.add_argument("--workload", default="lattice", choices=["lattice", "population", "surrogate", "adjoint", "screen", "cube"])
+    ap.add_argument("--workload", default="lattice",
+                    choices=["lattice", "population", "surrogate", "adjoint", "screen", "cube", "sweep"])
     ap.add_argument("--cube-steps", type=int, default=10000, help="cube workload: steps per kernel")
+    ap.add_argument("--sweep-sizes", type=int, nargs="+", default=[8, 12, 16, 20, 32, 48, 64, 96, 128, 192, 256],
+                    help="sweep workload: lattice sides")
     ap.add_argument("--train-designs", type=int, default=16384, help="screen workload: labelled training designs (200000 = the full config)")
     ap.add_argument("--walkers", type=int, default=256)
     ap.add_argument("--rollout-steps", type=int, default=2000)
@@ -689,6 +741,8 @@ def main():
         return run_screen(args, world, rank, local)
     if args.workload == "cube":
         return run_cube(args, world, rank, local)
+    if args.workload == "sweep":
+        return run_sweep(args, world, rank, local)
     return run_ours(args, world, rank, local)
 
 
