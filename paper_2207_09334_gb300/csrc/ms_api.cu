@@ -463,6 +463,10 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
             for (int t = 0; t < n_tiles; ++t) {
                 const int4 T = h_tiles[2 * t], R = h_tiles[2 * t + 1];
                 const int32_t *hb = h_halo.data() + T.z;
+                // a padding slot of a member points at the member itself (zero
+                // length, k = 0: no force), so the kernel needs no test for it
+                for (int sl2 = 0; sl2 < R.y; ++sl2)
+                    for (int m = 0; m < T.y; ++m) h_nbr16[(size_t)R.x + (size_t)sl2 * B + m] = (uint16_t)m;
                 for (int32_t i = T.x; i < T.x + T.y; ++i) {
                     int slot = 0;
                     for (int64_t q = inc_first[i]; q < inc_first[i + 1]; ++q, ++slot) {

@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kTileMasses) k_energy_tiled(const EnergyArgs a
         for (int s = 0; s < R.y; ++s) {
             const unsigned r = (unsigned)R.x + (unsigned)s * kTileMasses + (unsigned)m;
             const unsigned loc = __ldg(&a.t_nbr[r]);
-            if (loc == 0xffffu) continue;                     // padding slot
+            if (loc == 0xffffu || (int)loc == m) continue;  // padding slot (marked, or the mass itself)
             const int j = (int)loc < T.y ? T.x + (int)loc : __ldg(&a.halo[T.z + (int)loc - T.y]);
             pe += spring_pe(a, xi, __ldg(&a.sa[j]), r);
         }

@@ -24,6 +24,16 @@
 
 namespace ms {
 
+// 1/sqrt(x) by the hardware approximation (PTX rsqrt.approx.ftz.f32, relative
+// error below 2^-22); subnormal inputs count as zero.  Squared spring lengths
+// are never subnormal: a zero length is handled by the caller.
+__device__ __forceinline__ float rsqrt_hw(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Hooke term of eq. 2 plus the axial dashpot, added to (fx, fy, fz) for the
 // mass at (xi, vi) with the partner's state packed as pa = (x, y, z, vx),
 // pb = (vy, vz) (d = x_partner - x_self):
@@ -37,7 +47,7 @@ __device__ __forceinline__ void spring_term_packed(const float4 xi, const float4
 {
     const float dx = pa.x - xi.x, dy = pa.y - xi.y, dz = pa.z - xi.z;
     const float l2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float il = rsqrtf(l2);
+    const float il = rsqrt_hw(l2);
     const float l = l2 * il;
     const float rv = fmaf(pa.w - vi.x, dx, fmaf(pb.x - vi.y, dy, (pb.y - vi.z) * dz)) * il;
     float fs = fmaf(k, l - L, c * rv) * il;
@@ -230,12 +240,22 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
 
-// global -> shared bulk copy completing on an mbarrier (sizes and both
-// addresses are multiples of 16 bytes by construction of the layout)
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+// L2 policy for data read once per step (the spring records): evicted first,
+// so that the state, whose halo is read again by neighbouring tiles, stays in L2
+__device__ __forceinline__ uint64_t l2_evict_first()
 {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// global -> shared bulk copy completing on an mbarrier, with an L2 policy
+// (sizes and both addresses are multiples of 16 bytes by construction of the
+// layout)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar, uint64_t pol)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
@@ -284,6 +304,7 @@ __global__ void __launch_bounds__(kTileMasses) k_step_tiled(const StepArgs a)
     unsigned char *stage0 = dyn + (((size_t)a.tile_local * 24 + 127) & ~(size_t)127);
 
     auto stage_ptr = [&](unsigned p) { return stage0 + (size_t)p * SL::bytes; };
+    const uint64_t pol = l2_evict_first();
     auto issue = [&](unsigned g) {          // one thread: bulk-copy slot group g into its stage
         const unsigned p = g % kTileStages;
         const unsigned s0 = g * kTileGroup;
@@ -292,10 +313,10 @@ __global__ void __launch_bounds__(kTileMasses) k_step_tiled(const StepArgs a)
         const uint32_t cnt = ns * kTileMasses;
         unsigned char *st = stage_ptr(p);
         mbar_expect_tx(&bar[p], cnt * (2u + 8u + (HAS_C ? 4u : 0u) + (HAS_ACT ? 8u : 0u)));
-        bulk_g2s(st, a.t_nbr + first, cnt * 2u, &bar[p]);
-        bulk_g2s(st + SL::nbr, a.f_kl + first, cnt * 8u, &bar[p]);
-        if (HAS_C) bulk_g2s(st + SL::nbr + SL::kl, a.f_c + first, cnt * 4u, &bar[p]);
-        if (HAS_ACT) bulk_g2s(st + SL::nbr + SL::kl + SL::c, a.f_ab + first, cnt * 8u, &bar[p]);
+        bulk_g2s(st, a.t_nbr + first, cnt * 2u, &bar[p], pol);
+        bulk_g2s(st + SL::nbr, a.f_kl + first, cnt * 8u, &bar[p], pol);
+        if (HAS_C) bulk_g2s(st + SL::nbr + SL::kl, a.f_c + first, cnt * 4u, &bar[p], pol);
+        if (HAS_ACT) bulk_g2s(st + SL::nbr + SL::kl + SL::c, a.f_ab + first, cnt * 8u, &bar[p], pol);
     };
 
     if (tid == 0) {
@@ -340,8 +361,7 @@ __global__ void __launch_bounds__(kTileMasses) k_step_tiled(const StepArgs a)
             for (unsigned u = 0; u < (unsigned)kTileGroup; ++u) {
                 if (u < ns) {
                     const unsigned e = u * kTileMasses + tid;
-                    unsigned j = snbr[e];
-                    j = (j == 0xffffu) ? (unsigned)tid : j;
+                    const unsigned j = snbr[e];    // a padding slot points at the mass itself
                     const float2 kl = skl[e];
                     float L = kl.y;
                     const float c = HAS_C ? sc[e] : a.c_uniform;
