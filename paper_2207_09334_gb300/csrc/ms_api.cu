@@ -95,10 +95,10 @@ struct ms_sim {
     // tiled layout
     int kernel = 0;                     // ms::kKernelGather or ms::kKernelTiled (record layout)
     bool persistent = false;            // stepped by the persistent cluster kernel (ms_cluster.cu)
-    uint16_t *cl_nbr = nullptr;         // its records (both directions, per tile slot-major)
+    uint16_t *cl_nbr = nullptr;         // its records (both directions, lane-interleaved per tile)
     float2 *cl_kl = nullptr, *cl_ab = nullptr;
     float *cl_c = nullptr;
-    int cl_slots = 0;
+    int cl_slots = 0, cl_tm = 0;        // slots per mass (a multiple of the lanes), masses per tile
     int64_t cl_n = 0;
     std::vector<uint32_t> cl_slot_a, cl_slot_b;   // merged record -> its two cluster slots
     float2 *sc = nullptr;               // (sin, cos) table of a persistent multi-step call
@@ -237,9 +237,9 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
     s->c_uniform = c_uniform;
 
     if (p->kernel < 0 || p->kernel > 3 || p->reorder < 0 || p->reorder > 2) return fail(MS_ERR_ARG, "kernel must be 0..3 and reorder 0..2");
-    const bool small = N <= ms::kClMasses * ms::kClusterMax && p->integrator == 0;
+    const bool small = N <= ms::kClMassesMax * ms::kClusterMax && p->integrator == 0;
     if (p->kernel == 3 && !small)
-        return fail(MS_ERR_ARG, "the persistent kernel takes at most 4096 masses and symplectic Euler");
+        return fail(MS_ERR_ARG, "the persistent kernel takes at most 8192 masses and symplectic Euler");
     s->kernel = p->kernel == 1 ? ms::kKernelGather
               : p->kernel == 2 ? ms::kKernelTiled
               : p->kernel == 3 ? ms::kKernelPersistent
@@ -543,14 +543,17 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
     s->rec_slot_a.swap(slot_a);
     s->rec_slot_b.swap(slot_b);
 
-    // persistent cluster layout: tiles of kClMasses masses; every mass lists
-    // all of its springs (both directions), slot-major per tile, the partner
-    // coded (tile << 8) | member
+    // persistent cluster layout: tiles of CM masses, the smallest of 64, 128,
+    // 256, 512 that needs at most kClusterMax tiles; every mass lists all of
+    // its springs (both directions), the slots of its L lanes interleaved,
+    // the partner coded by its mass index
     std::vector<uint16_t> c_nbr;
     std::vector<float2> c_kl;
     std::vector<float> c_c;
     if (s->persistent) {
-        const int CM = ms::kClMasses;
+        int CM = 64;
+        while (CM < ms::kClMassesMax && (int64_t)CM * ms::kClusterMax < N) CM *= 2;
+        const int LN = ms::kClThreads / CM;
         const int tiles = (N + CM - 1) / CM;
         std::vector<std::vector<std::pair<int32_t, uint32_t>>> inc(N);   // (partner, record)
         for (int32_t o = 0; o < N; ++o)
@@ -560,9 +563,10 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
             }
         int slots = 1;
         for (int32_t i = 0; i < N; ++i) slots = std::max<int>(slots, (int)inc[i].size());
-        if (ms::cluster_smem_bytes(slots, c != nullptr, true) > 227 * 1024)
-            return fail(MS_ERR_ARG, "the persistent kernel holds at most about 40 springs per mass in shared memory; a mass has " +
-                                        std::to_string(slots));
+        slots = (slots + LN - 1) / LN * LN;
+        if (ms::cluster_smem_bytes(CM, slots, c != nullptr, false) > 227 * 1024)
+            return fail(MS_ERR_ARG, "the persistent kernel's records of " + std::to_string(slots) + " springs per mass over " +
+                                        std::to_string(CM) + "-mass tiles do not fit shared memory");
         const size_t per_tile = (size_t)slots * CM;
         c_nbr.assign((size_t)tiles * per_tile, 0);
         c_kl.assign((size_t)tiles * per_tile, make_float2(0.f, 0.f));
@@ -571,20 +575,20 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
         s->cl_slot_b.assign(n_rec, UINT32_MAX);
         for (int32_t i = 0; i < N; ++i) {
             const int t = i / CM, mi = i % CM;
-            for (int q = 0; q < slots; ++q) {
-                const size_t r = (size_t)t * per_tile + (size_t)q * CM + mi;
-                if (q < (int)inc[i].size()) {
-                    const int32_t j = inc[i][q].first;
-                    const uint32_t m = inc[i][q].second;
-                    c_nbr[r] = (uint16_t)(((j / CM) << 8) | (j % CM));
-                    c_kl[r] = rec_kl[m];
-                    if (c) c_c[r] = rec_c[m];
-                    if (s->cl_slot_a[m] == UINT32_MAX) s->cl_slot_a[m] = (uint32_t)r; else s->cl_slot_b[m] = (uint32_t)r;
-                } else {
-                    c_nbr[r] = (uint16_t)((t << 8) | mi);       // padding: the mass itself, (k, L0) = 0
-                }
+            auto rec_at = [&](int q) {
+                return (size_t)t * per_tile + ((size_t)(q / LN) * CM + mi) * LN + (size_t)(q % LN);
+            };
+            for (int q = 0; q < slots; ++q) c_nbr[rec_at(q)] = (uint16_t)i;   // padding: the mass itself, (k, L0) = 0
+            for (size_t q = 0; q < inc[i].size(); ++q) {
+                const size_t r = rec_at((int)q);
+                const uint32_t m = inc[i][q].second;
+                c_nbr[r] = (uint16_t)inc[i][q].first;
+                c_kl[r] = rec_kl[m];
+                if (c) c_c[r] = rec_c[m];
+                if (s->cl_slot_a[m] == UINT32_MAX) s->cl_slot_a[m] = (uint32_t)r; else s->cl_slot_b[m] = (uint32_t)r;
             }
         }
+        s->cl_tm = CM;
         s->cl_slots = slots;
         s->cl_n = (int64_t)tiles * per_tile;
     }
@@ -683,6 +687,9 @@ ms_status ms_set_actuation(ms_sim *s, float freq_hz, const float *amp, const flo
     if (!amp) { s->actuated = false; s->freq = 0.0; return MS_OK; }
     if (!phase) return fail(MS_ERR_ARG, "phase is required with amp");
     if (!std::isfinite(freq_hz)) return fail(MS_ERR_ARG, "freq must be finite");
+    if (s->persistent && ms::cluster_smem_bytes(s->cl_tm, s->cl_slots, s->cl_c != nullptr, true) > 227 * 1024)
+        return fail(MS_ERR_ARG, "the persistent kernel cannot hold the actuation coefficients of this system in "
+                                "shared memory; create it with the tiled kernel");
     const int64_t S = s->S, nrec = s->n_records, n = s->n_slots;
     std::vector<double> sa(nrec, 0.0), sb(nrec, 0.0);
     for (int64_t e = 0; e < S; ++e) {
@@ -742,7 +749,7 @@ ms_status ms_step(ms_sim *s, int32_t nsteps)
         ms::ClusterArgs ca{};
         ca.sa = s->sa[s->cur]; ca.sb = s->sb[s->cur]; ca.w = s->w; ca.fext = s->fext;
         ca.nbr = s->cl_nbr; ca.kl = s->cl_kl; ca.c = s->cl_c; ca.ab = s->actuated ? s->cl_ab : nullptr;
-        ca.c_uniform = s->c_uniform; ca.N = s->N; ca.slots = s->cl_slots;
+        ca.c_uniform = s->c_uniform; ca.N = s->N; ca.slots = s->cl_slots; ca.tm = s->cl_tm;
         ca.sc = sc; ca.nsteps = nsteps; ca.env = ms::make_env(s->p); ca.err = s->err;
         MS_CUDA_TRY(ms::launch_cluster(ca, s->stream));
         s->step_count += nsteps;

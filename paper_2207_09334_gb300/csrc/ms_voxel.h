@@ -64,9 +64,11 @@ inline Env make_env(const ms_params &p)
     return e;
 }
 
-// Persistent cluster step (ms_cluster.cu): tiles of kClMasses masses, one
-// CTA each, at most kClusterMax CTAs in one cluster.
-constexpr int kClMasses = 256;
+// Persistent cluster step (ms_cluster.cu): tiles of tm masses (64 to
+// kClMassesMax), one CTA of kClThreads threads each, at most kClusterMax CTAs
+// in one cluster.
+constexpr int kClMassesMax = 512;
+constexpr int kClThreads = 1024;
 constexpr int kClusterMax = 16;
 
 struct ClusterArgs {
@@ -74,20 +76,23 @@ struct ClusterArgs {
     float2 *sb;
     const float *w;          // 1/m, or -m for an anchored mass
     const float4 *fext;      // or nullptr
-    // records, both directions, per tile slot-major: [tile][slot][kClMasses];
-    // partner coded (tile << 8) | member, padding = the mass itself with (k, L0) = 0
+    // records, both directions, per tile; with L = kClThreads / tm lanes per
+    // mass, slot q of member m is at [tile][q / L][m][q % L] (slots padded to
+    // a multiple of L); partner coded by its mass index, padding = the mass
+    // itself with (k, L0) = 0
     const uint16_t *nbr;
     const float2 *kl;
     const float *c;          // or nullptr (then c_uniform)
     const float2 *ab;        // or nullptr (passive)
     float c_uniform;
-    int N, slots;
+    int N, slots;            // slots: a multiple of L
+    int tm;                  // masses per tile: 64, 128, 256 or 512
     const float2 *sc;        // (sin, cos)(2 pi f t_n) for the nsteps steps, if ab
     int nsteps;
     Env env;
     int *err;
 };
-size_t cluster_smem_bytes(int slots, bool has_c, bool has_act);
+size_t cluster_smem_bytes(int tm, int slots, bool has_c, bool has_act);
 cudaError_t launch_cluster(const ClusterArgs &a, cudaStream_t st);
 
 #ifdef __CUDACC__

@@ -46,8 +46,8 @@ KERNELS = ["gather", "tiled", "persistent"]
 
 
 def gpu_run(ms, s, p, n, reorder=None, chunks=1, kernel=None):
-    if kernel == "persistent" and s["x"].shape[0] > 4096:
-        pytest.skip("the persistent kernel takes at most 4096 masses")
+    if kernel == "persistent" and s["x"].shape[0] > 8192:
+        pytest.skip("the persistent kernel takes at most 8192 masses")
     with ms.Sim(s, p, reorder=reorder, kernel=kernel) as sim:
         done = 0
         for q in range(chunks):
@@ -318,6 +318,59 @@ def test_rk4_with_actuation_anchors_and_ground_contact(ms, ora, kernel):
     xo, _ = ora.run(s, f32p(p), 500, integrator="rk4")
     err = np.abs(xg - xo).max()
     assert err <= 1e-5 * body_size(s), (err, 1e-5 * body_size(s))
+
+
+def test_persistent_wide_tiles_soft_cube(ms, ora):
+    """8000 masses: 16 CTAs of 512 masses with two lanes per mass, per-spring
+    damping, dropped onto the ground with friction, over two calls."""
+    s = synth.soft_cube(n=20, z0=0.001)
+    rng = np.random.default_rng(23)
+    S = s["ij"].shape[0]
+    s["c"] = rng.uniform(0.0, 0.2, S).astype(np.float32)
+    s["v"][:] = np.array([0.1, -0.05, -0.3], np.float32)
+    p = synth.soft_cube_params(contact=True)
+    with ms.Sim(s, p, kernel="persistent") as sim:
+        assert sim.info()["kernel"] == 3
+        sim.step(120); sim.step(80)
+        xg, _ = sim.get_state()
+    xo, _ = ora.run(s, f32p(p), 200)
+    err = np.abs(xg.astype(np.float64) - xo).max()
+    assert err <= 1e-4 * body_size(s), (err, 1e-4 * body_size(s))
+
+
+def test_persistent_wide_tiles_actuated_irregular_network(ms, ora):
+    """5000 best-candidate points (10 tiles of 512, degree <= 16): actuation
+    and an external force on the wide tiles, against the oracle."""
+    s = synth.quasi_uniform_lattice(5000, box=(0.17, 0.17, 0.17), seed=3)
+    rng = np.random.default_rng(29)
+    S = s["ij"].shape[0]; N = s["x"].shape[0]
+    s["A"] = rng.uniform(0, 0.1, S).astype(np.float32)
+    s["phi"] = rng.uniform(0, 2 * np.pi, S).astype(np.float32)
+    s["freq"] = 4.0
+    s["fext"] = (1e-3 * rng.standard_normal((N, 3))).astype(np.float32)
+    p = synth.soft_cube_params(contact=False)
+    with ms.Sim(s, p, kernel="persistent") as sim:
+        assert sim.info()["kernel"] == 3
+        sim.step(150); sim.step(150)
+        xg, _ = sim.get_state()
+    xo, _ = ora.run(s, f32p(p), 300)
+    err = np.abs(xg.astype(np.float64) - xo).max()
+    assert err <= 1e-5 * body_size(s), (err, 1e-5 * body_size(s))
+
+
+def test_persistent_actuation_that_does_not_fit_shared_memory_is_refused(ms):
+    """8000 masses of a 26-neighbour lattice: the records fit the wide tiles,
+    their actuation coefficients do not; set_actuation says so and the
+    system keeps stepping passively."""
+    s = synth.soft_cube(n=20, z0=0.001)
+    S = s["ij"].shape[0]
+    with ms.Sim(s, synth.soft_cube_params(contact=True), kernel="persistent") as sim:
+        with pytest.raises(ms.MsError) as e:
+            sim.set_actuation(2.0, np.full(S, 0.1, np.float32), np.zeros(S, np.float32))
+        assert e.value.code == 1 and "tiled kernel" in str(e.value)
+        sim.step(10)
+        x, _ = sim.get_state()
+        assert np.isfinite(x).all()
 
 
 def test_set_state_rejects_non_finite_host_input_and_keeps_the_state(ms):
