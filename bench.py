@@ -723,7 +723,7 @@ def main():
     ap.add_argument("--sim-steps-per-bench-step", type=int, default=100)
     ap.add_argument("--loop-steps", type=int, default=5)
     ap.add_argument("--candidates", type=int, default=1 << 20)
-    ap.add_argument("--screen-batch", type=int, default=16384)
+    ap.add_argument("--screen-batch", type=int, default=65536, help="designs per surrogate forward pass")
     ap.add_argument("--sim-designs", type=int, default=1024)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -66,8 +66,9 @@ def train(materials, labels, epochs: int = 20, batch: int = 1024, lr: float = 1e
         raise ValueError("need at least one full batch of designs")
     dm = torch.tensor(mats, device="cuda")
     dy = torch.tensor(yt, device="cuda")
-    # the model's buffers also serve screening, which runs larger forward batches
-    net = net or Surrogate(mats.shape[1] * 4, hidden, max_batch=max(batch, 16384), seed=seed)
+    # the model's buffers also serve screening, which runs forward passes of
+    # 65536 designs (fewer, fuller waves of GEMM tiles than smaller passes)
+    net = net or Surrogate(mats.shape[1] * 4, hidden, max_batch=max(batch, 65536), seed=seed)
     rng = np.random.default_rng(seed)
     for _ in range(epochs):
         perm = torch.tensor(rng.permutation(len(mats))[:n], device="cuda")
