@@ -4,8 +4,11 @@
 // Each robot is small (at most 4096 masses), so its whole state lives in
 // shared memory for the length of the run: positions+inverse mass, velocity
 // and the force accumulator, 48 bytes per mass.  Spring records stay in
-// global memory (the same sliced-ELL layout as the single-system step, with
-// robot-local mass indices) and are re-read every step from L2.  A step is
+// global memory and are re-read every step from L2: sliced-ELL rows (32
+// masses per slice, robot-local mass indices) in which every mass lists all
+// of its springs, both directions, so the force sum is one pass of coalesced
+// loads with no dependent back-reference gathers.  (The robot-by-robot loop
+// and the adjoint use the owner-row + back-reference layout.)  A step is
 // two phases separated by a barrier: every mass gathers its spring forces
 // from the shared-memory state at t_n (Jacobi, like the paper's grid-wide
 // synchronisation in Algorithm 1), then every mass integrates in place.
@@ -41,7 +44,7 @@ struct BatchArgs {
     int n_items;
     int *queue;            // next item (zeroed before each launch)
     float4 *st;            // population state, 2 float4 per mass
-    Records rec;
+    AllRows rows;
     Env env;
     const float2 *sc;      // (sin, cos)(2 pi f t_n) per step of this run
     int nsteps;
@@ -71,13 +74,12 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchArgs a)
             const int n = R.n;
             float4 *xs = smem, *vs = smem + n, *fs = smem + 2 * n;
             const float4 *g = a.st + 2 * R.mass_base;
-            const unsigned rec_base = R.rec_base;
             for (int i = tid; i < n; i += kBatchThreads) { xs[i] = g[2 * i]; vs[i] = g[2 * i + 1]; }
             __syncthreads();
             for (int step = 0; step < a.nsteps; ++step) {
                 const float2 sc = __ldg(&a.sc[step]);
                 for (int i = tid; i < n; i += kBatchThreads)
-                    fs[i] = robot_force<4>(a.rec, R.slice_base, rec_base, i, xs, vs, sc.x, sc.y);
+                    fs[i] = robot_force_all<4>(a.rows, R.slice_base, i, xs, vs, sc.x, sc.y);
                 __syncthreads();
                 for (int i = tid; i < n; i += kBatchThreads) {
                     float4 x = xs[i], v = vs[i];
@@ -113,13 +115,12 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchArgs a)
                 const int n = R.n;
                 float4 *xs = smem + (size_t)warp * 3 * a.warp_cap, *vs = xs + a.warp_cap, *fs = vs + a.warp_cap;
                 const float4 *g = a.st + 2 * R.mass_base;
-                const unsigned rec_base = R.rec_base;
                 for (int i = lane; i < n; i += 32) { xs[i] = g[2 * i]; vs[i] = g[2 * i + 1]; }
                 __syncwarp();
                 for (int step = 0; step < a.nsteps; ++step) {
                     const float2 sc = __ldg(&a.sc[step]);
                     for (int i = lane; i < n; i += 32)
-                        fs[i] = robot_force<4>(a.rec, R.slice_base, rec_base, i, xs, vs, sc.x, sc.y);
+                        fs[i] = robot_force_all<4>(a.rows, R.slice_base, i, xs, vs, sc.x, sc.y);
                     __syncwarp();
                     for (int i = lane; i < n; i += 32) {
                         float4 x = xs[i], v = vs[i];
@@ -225,6 +226,11 @@ struct msb_batch {
     float2 *f_kl = nullptr, *f_ab = nullptr;
     float *f_c = nullptr;
     uint32_t *b_ent = nullptr;
+    // every-spring rows (the persistent population kernel)
+    uint2 *a_slice = nullptr;
+    uint16_t *a_nbr = nullptr;
+    float2 *a_kl = nullptr, *a_ab = nullptr;
+    float *a_c = nullptr;
     float *travel = nullptr;
     int *err = nullptr;
     int *queue = nullptr;
@@ -398,7 +404,7 @@ BatchArgs batch_args(msb_batch *b, int nsteps)
     BatchArgs a{};
     a.robots = b->robots; a.items = b->items; a.wlist = b->wlist; a.n_items = (int)b->h_items.size(); a.queue = b->queue;
     a.st = b->st;
-    a.rec = Records{b->slice, b->f_nbr, b->f_kl, b->f_c, b->f_ab, b->b_ent, 0.f};
+    a.rows = AllRows{b->a_slice, b->a_nbr, b->a_kl, b->a_ab, b->a_c};
     a.env = make_env(b->p);
     a.sc = b->sc; a.nsteps = nsteps;
     a.warp_cap = b->warp_cap; a.travel = b->travel; a.err = b->err;
@@ -597,6 +603,39 @@ ms_status build_voxels(const msb_voxel_spec *spec, int n_robots, const int32_t *
                 h_b[h_slice[slice0 + (j >> 5)].y + 32u * t + (uint32_t)(j & 31)] = (uint32_t)o | ((rr - rec0) << kRobotOwnerBits);
             }
         }
+        if (!adjoint_maps) {
+            // every-spring rows: per mass its own records, then its back
+            // references (in b_ent order), then padding pointing at itself
+            for (int s_ = 0; s_ < ns; ++s_) {
+                int mx = 0;
+                for (int l = 0; l < 32 && 32 * s_ + l < n; ++l) mx = std::max(mx, deg[32 * s_ + l] + bdeg[32 * s_ + l]);
+                out.aslice.push_back(make_uint2((uint32_t)out.anbr.size(), (uint32_t)mx));
+                const size_t first = out.anbr.size();
+                out.anbr.resize(first + 32 * (size_t)mx, 0);
+                for (int l = 0; l < 32; ++l)
+                    for (int q = 0; q < mx; ++q) out.anbr[first + 32 * (size_t)q + l] = (uint16_t)std::min(32 * s_ + l, n - 1);
+            }
+            out.akl.resize(out.anbr.size(), make_float2(0.f, 0.f));
+            out.aab.resize(out.anbr.size(), make_float2(0.f, 0.f));
+            out.ac.resize(out.anbr.size(), 0.f);
+            for (int i = 0; i < n; ++i) {
+                const uint2 am = out.aslice[slice0 + (i >> 5)];
+                uint32_t w = am.x + (uint32_t)(i & 31);
+                auto put = [&](int partner, uint32_t rr) {
+                    out.anbr[w] = (uint16_t)partner;
+                    out.akl[w] = h_kl[rr]; out.aab[w] = h_ab[rr]; out.ac[w] = h_c[rr];
+                    w += 32u;
+                };
+                const uint32_t fbase = h_slice[slice0 + (i >> 5)].x + (uint32_t)(i & 31);
+                for (int s_ = 0; s_ < deg[i]; ++s_) put(h_nbr[fbase + 32u * s_], fbase + 32u * s_);
+                const uint32_t bbase = h_slice[slice0 + (i >> 5)].y + (uint32_t)(i & 31);
+                for (int t = 0; t < bdeg[i]; ++t) {
+                    const uint32_t e = h_b[bbase + 32u * t];
+                    put((int)(e & kRobotOwnerMask), rec0 + (e >> kRobotOwnerBits));
+                }
+            }
+            if (out.anbr.size() >= (size_t)UINT32_MAX / 2) return fail(MS_ERR_ARG, "population too large for 32-bit record offsets");
+        }
         if (adjoint_maps) {
             for (int64_t v = 0; v < nvox; ++v) {
                 for (int pr = 0; pr < 28; ++pr) {
@@ -670,6 +709,11 @@ ms_status msb_create(const ms_params *p, const msb_voxel_spec *spec, int32_t n_r
     if ((st = bupload(b, &b->f_ab, h_ab.data(), h_ab.size())) != MS_OK) return st;
     if ((st = bupload(b, &b->f_c, h_c.data(), h_c.size())) != MS_OK) return st;
     if ((st = bupload(b, &b->b_ent, h_b.data(), h_b.size())) != MS_OK) return st;
+    if ((st = bupload(b, &b->a_slice, vb.aslice.data(), vb.aslice.size())) != MS_OK) return st;
+    if ((st = bupload(b, &b->a_nbr, vb.anbr.data(), vb.anbr.size())) != MS_OK) return st;
+    if ((st = bupload(b, &b->a_kl, vb.akl.data(), vb.akl.size())) != MS_OK) return st;
+    if ((st = bupload(b, &b->a_ab, vb.aab.data(), vb.aab.size())) != MS_OK) return st;
+    if ((st = bupload(b, &b->a_c, vb.ac.data(), vb.ac.size())) != MS_OK) return st;
     if ((st = bupload<float>(b, &b->travel, nullptr, n_robots)) != MS_OK) return st;
     if ((st = bupload<int>(b, &b->err, nullptr, 1)) != MS_OK) return st;
     if ((st = bupload<int>(b, &b->queue, nullptr, 1)) != MS_OK) return st;

@@ -32,6 +32,14 @@ struct VoxelBuild {
     std::vector<float2> ab;            // (alpha, beta)
     std::vector<float> c;
     std::vector<uint32_t> bent;
+    // every-spring rows (population kernel; filled when the adjoint maps are
+    // not requested): per slice (same index as `slice`) the first slot and
+    // the row length; per slot the partner (robot-local, the mass itself for
+    // padding) and the spring's (k, L0), (alpha, beta) and c
+    std::vector<uint2> aslice;
+    std::vector<uint16_t> anbr;
+    std::vector<float2> akl, aab;
+    std::vector<float> ac;
     // adjoint maps (filled when requested):
     std::vector<short4> slot_vox;      // per slot: up to 4 robot-local voxels sharing the spring (-1 = none)
     std::vector<uint32_t> vox_slots;   // per voxel (concatenated): slot of each of its 28 corner pairs (or 0xffffffff)
@@ -107,6 +115,17 @@ struct Records {
     float c_uniform;
 };
 
+// Every-spring rows of a population (device pointers): each mass's row lists
+// all of its springs, both directions, so one pass of coalesced loads serves
+// the whole force sum.
+struct AllRows {
+    const uint2 *slice;    // per slice: (first slot, slots per lane)
+    const uint16_t *nbr;
+    const float2 *kl;
+    const float2 *ab;
+    const float *c;
+};
+
 // Hooke + dashpot term (eq. 2), the same arithmetic as the single-system step.
 __device__ __forceinline__ void vox_spring(const float4 xi, const float4 vi, const float4 xj, const float4 vj,
                                            float k, float L, float c, float &fx, float &fy, float &fz)
@@ -141,7 +160,7 @@ __device__ __forceinline__ float4 robot_force(const Records &a, int slice_base, 
         j = (j < 0) ? i : j;
         const float2 kl = __ldg(&a.f_kl[r]);
         const float2 ab = a.f_ab ? __ldg(&a.f_ab[r]) : make_float2(0.f, 0.f);
-        const float L = kl.y * (1.0f + (ab.x * s_n + ab.y * c_n));
+        const float L = kl.y * (1.0f + fmaf(ab.x, s_n, ab.y * c_n));
         vox_spring(xi, vi, xs[j], vs[j], kl.x, L, a.f_c ? __ldg(&a.f_c[r]) : a.c_uniform, fx, fy, fz);
     }
     unsigned q = meta.y + lane;
@@ -156,8 +175,30 @@ __device__ __forceinline__ float4 robot_force(const Records &a, int slice_base, 
         }
         const float2 kl = __ldg(&a.f_kl[rr]);
         const float2 ab = a.f_ab ? __ldg(&a.f_ab[rr]) : make_float2(0.f, 0.f);
-        const float L = kl.y * (1.0f + (ab.x * s_n + ab.y * c_n));
+        const float L = kl.y * (1.0f + fmaf(ab.x, s_n, ab.y * c_n));
         vox_spring(xi, vi, xs[o], vs[o], kl.x, L, a.f_c ? __ldg(&a.f_c[rr]) : a.c_uniform, fx, fy, fz);
+    }
+    return make_float4(fx, fy, fz, 0.f);
+}
+
+// The same force from the every-spring rows: the springs of mass i in the
+// order of robot_force (its own records, then the back references), so both
+// give bit-identical sums.
+template <int UNROLL = 1>
+__device__ __forceinline__ float4 robot_force_all(const AllRows &g, int slice_base, int i, const float4 *xs,
+                                                  const float4 *vs, float s_n, float c_n)
+{
+    const uint2 meta = __ldg(&g.slice[slice_base + (i >> 5)]);
+    const float4 xi = xs[i], vi = vs[i];
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    unsigned r = meta.x + ((unsigned)i & 31u);
+#pragma unroll UNROLL
+    for (unsigned s = 0; s < meta.y; ++s, r += 32u) {
+        const int j = __ldg(&g.nbr[r]);
+        const float2 kl = __ldg(&g.kl[r]);
+        const float2 ab = __ldg(&g.ab[r]);
+        const float L = kl.y * (1.0f + fmaf(ab.x, s_n, ab.y * c_n));
+        vox_spring(xi, vi, xs[j], vs[j], kl.x, L, __ldg(&g.c[r]), fx, fy, fz);
     }
     return make_float4(fx, fy, fz, 0.f);
 }
@@ -173,19 +214,20 @@ __device__ __forceinline__ void robot_integrate(const Env &e, float4 &x, float4 
     const bool pen = e.contact && x.z < 0.0f;
     float Fn = 0.f;
     if (pen) { Fn = -e.k_c * x.z; f.z += Fn; }
-    float vx = v.x + e.dt * (f.x * w + e.gx);
-    float vy = v.y + e.dt * (f.y * w + e.gy);
-    float vz = v.z + e.dt * (f.z * w + e.gz);
+    // explicit fused operations: every inlined copy rounds the same way
+    float vx = fmaf(e.dt, fmaf(f.x, w, e.gx), v.x);
+    float vy = fmaf(e.dt, fmaf(f.y, w, e.gy), v.y);
+    float vz = fmaf(e.dt, fmaf(f.z, w, e.gz), v.z);
     if (vt) *vt = make_float4(vx, vy, vz, pen ? 1.0f : 0.0f);
     if (pen && e.mu > 0.0f) {
         const float D = e.mu * Fn * e.dt * w;
-        const float vtn = sqrtf(vx * vx + vy * vy);
+        const float vtn = sqrtf(fmaf(vx, vx, vy * vy));
         if (vtn <= D) { vx = 0.f; vy = 0.f; }
         else { const float sc = 1.0f - D / vtn; vx *= sc; vy *= sc; }
     }
     vx *= e.keep; vy *= e.keep; vz *= e.keep;
     v = make_float4(vx, vy, vz, 0.f);
-    x = make_float4(x.x + e.dt * vx, x.y + e.dt * vy, x.z + e.dt * vz, w);
+    x = make_float4(fmaf(e.dt, vx, x.x), fmaf(e.dt, vy, x.y), fmaf(e.dt, vz, x.z), w);
 }
 
 __device__ __forceinline__ float warp_sum(float v)
