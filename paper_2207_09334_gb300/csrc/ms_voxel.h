@@ -213,8 +213,9 @@ __device__ __forceinline__ void robot_integrate(const Env &e, float4 &x, float4 
     if (w < 0.0f) { v = make_float4(0.f, 0.f, 0.f, 0.f); if (vt) *vt = v; return; }
     const bool pen = e.contact && x.z < 0.0f;
     float Fn = 0.f;
-    if (pen) { Fn = -e.k_c * x.z; f.z += Fn; }
-    // explicit fused operations: every inlined copy rounds the same way
+    // explicit fused operations: every inlined copy rounds the same way,
+    // whatever the compiler's contraction choices in its context
+    if (pen) { Fn = -e.k_c * x.z; f.z = fmaf(-e.k_c, x.z, f.z); }
     float vx = fmaf(e.dt, fmaf(f.x, w, e.gx), v.x);
     float vy = fmaf(e.dt, fmaf(f.y, w, e.gy), v.y);
     float vz = fmaf(e.dt, fmaf(f.z, w, e.gz), v.z);
