@@ -245,7 +245,7 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
               : p->kernel == 3 ? ms::kKernelPersistent
               : ms::kKernelTiled;
     const bool persistent = s->kernel == ms::kKernelPersistent;
-    if (persistent) s->kernel = ms::kKernelGather;     // same record layout; stepped by one persistent CTA
+    if (persistent) s->kernel = ms::kKernelGather;     // gather layout for the energy kernel; stepped by the cluster kernel
 
     // 1. mass order
     s->perm.resize(N); s->iperm.resize(N);

@@ -28,12 +28,11 @@ ms_status fail(ms_status st, const std::string &msg);
 // Device layout of one simulation (all pointers are device memory).
 //
 // Masses are stored in the library's internal order, double buffered (the
-// step reads buffer `cur` and writes `cur ^ 1`), one 32-byte sector per mass
-// so that a neighbour's whole state is one sector:
-//   st[2i]   = (x, y, z, w)   w = 1/m for a free mass, -1 for an anchored mass
-//   st[2i+1] = (vx, vy, vz, 0)
+// step reads buffer `cur` and writes `cur ^ 1`), packed as in StepArgs below:
+//   sa[i] = (x, y, z, vx), sb[i] = (vy, vz), and the constant w[i] = 1/m for
+//   a free mass, -m for an anchored one.
 //
-// Springs are stored once, in the row of their lower-indexed endpoint (the
+// Gather layout (kernel 1): springs are stored once, in the row of their lower-indexed endpoint (the
 // "owner"), in a sliced-ELL layout with slices of 32 masses (one warp):
 //   record (owner o, slot s) lives at  slice[o/32].fwd_off + 32*s + o%32
 // with arrays f_nbr (partner index, -1 = padding), f_kl = (k, L0) and
@@ -51,8 +50,7 @@ struct Slice {                 // 16 bytes, read as one uint4
 
 constexpr uint32_t kOwnerBits = 27;
 constexpr uint32_t kOwnerMask = (1u << kOwnerBits) - 1u;
-// Back references of robots (and of the persistent single-system kernel),
-// robot-local form: owner o (< 4096 masses) in the low 12 bits, the owner's
+// Back references of robots, robot-local form: owner o (< 4096 masses) in the low 12 bits, the owner's
 // record as an offset from the robot's first record above them (< 2^20
 // records per robot), or kBackPad.  One dependent load less than the
 // (owner, slot) form, which needs the owner's slice header.
@@ -64,7 +62,7 @@ constexpr int kMaxFwdDegree = 31;
 // Kernels of the single-system step.
 constexpr int kKernelGather = 1;   // one thread per mass, sliced-ELL rows + back references
 constexpr int kKernelTiled = 2;    // CTA per tile of masses, state + halo in shared memory
-constexpr int kKernelPersistent = 3; // small systems: all steps in one CTA, state in shared memory
+constexpr int kKernelPersistent = 3; // small systems: all steps in one cluster launch, state in shared memory
 constexpr int kTileMasses = 512;   // masses per tile (= threads per CTA)
 constexpr int kTileMaxLocal = 2048; // tile members + halo that fit the CTA's shared memory (24 B each)
 constexpr int kTileGroup = 3;      // spring slots per pipeline stage (one bulk copy per array)
