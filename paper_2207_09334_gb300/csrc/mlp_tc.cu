@@ -14,9 +14,9 @@
 //         K = 16 per instruction) into a 128 x BN fp32 accumulator in TMEM,
 //         then tcgen05.commit to the stage's "empty" mbarrier;
 //     so loads run kStages tiles ahead and the MMAs are issued back to back;
-//   * the eight warps read the accumulator back with tcgen05.ld (warp w owns
-//     TMEM lanes 32(w mod 4)..+31 = rows, and half w / 4 of the columns) and
-//     apply the fused epilogue: plain fp32 store, bias + GELU (forward), or
+//   * the epilogue warps (sixteen, or eight in the one-hot variant) read the
+//     accumulator back with tcgen05.ld (warp w owns TMEM lanes 32(w mod 4)..+31
+//     = rows, and one of the column parts) and apply the fused epilogue: plain fp32 store, bias + GELU (forward), or
 //     GELU' (backward), writing row-major and transposed bf16 copies as the
 //     next product needs.
 // Every wait is bounded by %globaltimer; on expiry the kernel records a
@@ -39,9 +39,15 @@ namespace {
 
 constexpr int kBM = 128, kBK = 64;
 constexpr int kStages = 4;
-constexpr int kGemmThreads = 320;   // warp 0 loads, warp 1 issues MMAs, warps 2..9 run the epilogue
-constexpr int kEpiThreads = 256;
-constexpr int kOnehotThreads = 448; // one-hot variant: warps 10..13 build the A tiles
+// Warp roles: warp 0 loads, warp 1 issues MMAs, the next epi_warps() warps run
+// the epilogue, and (one-hot variant) four more warps build the A tiles.
+// Sixteen epilogue warps when the K loop is short (the epilogue then sets the
+// pace: bias + erf-GELU of the whole tile against a few k-steps of MMAs);
+// eight in the one-hot variant, whose long K loop hides its epilogue.
+template <bool ONEHOT>
+constexpr int epi_warps() { return ONEHOT ? 8 : 16; }
+template <bool ONEHOT>
+constexpr int gemm_threads() { return 64 + 32 * epi_warps<ONEHOT>() + (ONEHOT ? 128 : 0); }
 constexpr uint32_t kTileBytes = kBM * kBK * 2;                  // 16 KB: one 128 x 64 bf16 box
 constexpr uint64_t kWaitNs = 2000000000ull;                       // 2 s
 
@@ -141,24 +147,25 @@ __device__ __forceinline__ float gelu_grad(float z)
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.3989422804014327f * expf(-0.5f * z * z);
 }
 
-// Epilogue of one 32-column chunk of a thread's row: r holds the fp32
-// accumulator C[row][nb .. nb + 31].
-__device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, const uint32_t (&r)[32], int row, int nb)
+// Epilogue of one CW-column chunk of a thread's row (CW = 16 or 32): r holds
+// the fp32 accumulator C[row][nb .. nb + CW - 1].
+template <int CW>
+__device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, const uint32_t (&r)[CW], int row, int nb)
 {
     if (g.epi == EPI_F32) {
         float *dst = g.C + (size_t)row * g.N + nb;
 #pragma unroll
-        for (int q = 0; q < 32; q += 4)
+        for (int q = 0; q < CW; q += 4)
             *reinterpret_cast<float4 *>(dst + q) = make_float4(__uint_as_float(r[q]), __uint_as_float(r[q + 1]),
                                                                __uint_as_float(r[q + 2]), __uint_as_float(r[q + 3]));
         return;
     }
-    __align__(16) __nv_bfloat16 hv[32], zv[32];
+    __align__(16) __nv_bfloat16 hv[CW], zv[CW];
     if (g.epi == EPI_BIAS_GELU) {
-        // bias offsets are multiples of 128 floats by construction: float4 loads
+        // bias offsets are multiples of 16 floats by construction: float4 loads
         const float4 *b4 = reinterpret_cast<const float4 *>(g.bias + nb);
 #pragma unroll
-        for (int q4 = 0; q4 < 8; ++q4) {
+        for (int q4 = 0; q4 < CW / 4; ++q4) {
             const float4 bq = __ldg(&b4[q4]);
             const float bb[4] = {bq.x, bq.y, bq.z, bq.w};
 #pragma unroll
@@ -171,22 +178,47 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, const uint32_t
     } else {
         const uint4 *zr = reinterpret_cast<const uint4 *>(g.Z + (size_t)row * g.N + nb);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) reinterpret_cast<uint4 *>(zv)[q] = zr[q];
+        for (int q = 0; q < CW / 8; ++q) reinterpret_cast<uint4 *>(zv)[q] = zr[q];
 #pragma unroll
-        for (int q = 0; q < 32; ++q)
+        for (int q = 0; q < CW; ++q)
             hv[q] = __float2bfloat16(__uint_as_float(r[q]) * gelu_grad(__bfloat162float(zv[q])));
     }
     uint4 *dh = reinterpret_cast<uint4 *>(g.H + (size_t)row * g.N + nb);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) dh[q] = reinterpret_cast<const uint4 *>(hv)[q];
+    for (int q = 0; q < CW / 8; ++q) dh[q] = reinterpret_cast<const uint4 *>(hv)[q];
     if (g.epi == EPI_BIAS_GELU && g.Z) {                    // pre-activation kept for the backward pass
         uint4 *dz = reinterpret_cast<uint4 *>(g.Z + (size_t)row * g.N + nb);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) dz[q] = reinterpret_cast<const uint4 *>(zv)[q];
+        for (int q = 0; q < CW / 8; ++q) dz[q] = reinterpret_cast<const uint4 *>(zv)[q];
     }
     if (g.Ht)
 #pragma unroll
-        for (int q = 0; q < 32; ++q) g.Ht[(size_t)(nb + q) * g.M + row] = hv[q];
+        for (int q = 0; q < CW; ++q) g.Ht[(size_t)(nb + q) * g.M + row] = hv[q];
+}
+
+// tcgen05.ld of CW consecutive fp32 columns of this warp's 32 TMEM lanes
+template <int CW>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&r)[CW]);
+
+template <>
+__device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                   "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *b)
@@ -197,7 +229,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *b)
 // Persistent tile loop.  Tiles are 128 x BN, numbered with N fastest (CTAs
 // that run at the same time share rows of A in L2); CTA c takes tiles c,
 // c + gridDim.x, ...  Warp 0 (one thread) loads, warp 1 (one thread) issues
-// the MMAs, warps 2..9 drain the accumulators.  Two accumulators of BN TMEM
+// the MMAs, the epilogue warps drain the accumulators.  Two accumulators of BN TMEM
 // columns alternate between tiles, so the epilogue of one tile overlaps the
 // main loop of the next:
 //   full[s] / empty[s]        shared-memory stage loaded / read by the MMAs
@@ -227,11 +259,13 @@ __device__ __forceinline__ void build_onehot_row(unsigned char *tile, int r, con
 }
 
 template <int BN, bool ONEHOT>
-__global__ void __launch_bounds__(ONEHOT ? kOnehotThreads : kGemmThreads, 1) k_gemm_tc(const __grid_constant__ CUtensorMap mapA,
+__global__ void __launch_bounds__(gemm_threads<ONEHOT>(), 1) k_gemm_tc(const __grid_constant__ CUtensorMap mapA,
                                                              const __grid_constant__ CUtensorMap mapB, const GemmArgs g)
 {
     constexpr uint32_t kStageBytes = kTileBytes * (1 + BN / kBM);   // A tile + BN/128 B boxes
     constexpr uint32_t kTxBytes = ONEHOT ? kStageBytes - kTileBytes : kStageBytes;   // bytes the TMA brings
+    constexpr int kEW = epi_warps<ONEHOT>();
+    static_assert(kEW % 4 == 0 && BN % (32 * (kEW / 4)) == 0, "epilogue split");
     extern __shared__ __align__(1024) unsigned char dyn[];
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_base;
@@ -248,7 +282,7 @@ __global__ void __launch_bounds__(ONEHOT ? kOnehotThreads : kGemmThreads, 1) k_g
     if (tid == 32) {
         // full[s]: the TMA thread's expect_tx arrival, plus the 128 builders after writing a one-hot tile
         for (int s = 0; s < kStages; ++s) { mbar_init(&full[s], ONEHOT ? 1 + kBM : 1); mbar_init(&empty[s], 1); }
-        for (int a = 0; a < 2; ++a) { mbar_init(&acc_full[a], 1); mbar_init(&acc_empty[a], kEpiThreads); }
+        for (int a = 0; a < 2; ++a) { mbar_init(&acc_full[a], 1); mbar_init(&acc_empty[a], 32 * kEW); }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -276,10 +310,10 @@ __global__ void __launch_bounds__(ONEHOT ? kOnehotThreads : kGemmThreads, 1) k_g
             }
             if (!ok) atomicOr(g.err, kErrTimeout);
         }
-    } else if (ONEHOT && warp >= kGemmThreads / 32) {
+    } else if (ONEHOT && warp >= 2 + kEW) {
         // one-hot builders: thread r writes row r of every A tile, with the
         // next k-step's material bytes loaded while the current row is built
-        const int r = tid - kGemmThreads;
+        const int r = tid - 32 * (2 + kEW);
         unsigned it = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
@@ -321,9 +355,10 @@ __global__ void __launch_bounds__(ONEHOT ? kOnehotThreads : kGemmThreads, 1) k_g
             }
             if (!ok) atomicOr(g.err, kErrTimeout);
         }
-    } else if (warp < kGemmThreads / 32) {
-        // epilogue: warp w drains TMEM lanes 32 (w mod 4).. and half (w - 2) / 4 of the columns
-        const int quarter = warp & 3, half = (warp - 2) >> 2;
+    } else if (warp < 2 + kEW) {
+        // epilogue: warp w drains TMEM lanes 32 (w mod 4).. and part (w - 2) / 4 of the columns
+        constexpr int kParts = kEW / 4, kCols = BN / kParts;
+        const int quarter = warp & 3, part = (warp - 2) >> 2;
         unsigned lt = 0;
         for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++lt) {
             const unsigned acc = lt & 1u;
@@ -334,18 +369,13 @@ __global__ void __launch_bounds__(ONEHOT ? kOnehotThreads : kGemmThreads, 1) k_g
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int m0 = (tile / tiles_n) * kBM, n0 = (tile % tiles_n) * BN;
             const int row = m0 + quarter * 32 + lane;
-            for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 32) {
-                uint32_t r[32];
-                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + acc * BN + (uint32_t)c0;
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                             "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                               "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-                               "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-                               "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                             : "r"(taddr));
+            // sixteen-column chunks where sixteen epilogue warps share the register file
+            constexpr int CW = kEW > 8 ? 16 : 32;
+            for (int c0 = part * kCols; c0 < (part + 1) * kCols; c0 += CW) {
+                uint32_t r[CW];
+                tmem_ld<CW>(tmem + ((uint32_t)(quarter * 32) << 16) + acc * BN + (uint32_t)c0, r);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                epilogue_chunk(g, r, row, n0 + c0);
+                epilogue_chunk<CW>(g, r, row, n0 + c0);
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(&acc_empty[acc]);                  // accumulator acc may be overwritten
@@ -542,11 +572,11 @@ ms_status gemm_any(const __nv_bfloat16 *A, const uint8_t *mats, const __nv_bfloa
     const int t256 = N % 256 == 0 ? (M / kBM) * (N / 256) : 0;
     const int t128 = (M / kBM) * (N / kBM);
     if (t256 >= n_sms) {
-        if (mats) k_gemm_tc<256, true><<<std::min(t256, n_sms), kOnehotThreads, gemm_smem<256>(), st>>>(ma, mb, g);
-        else k_gemm_tc<256, false><<<std::min(t256, n_sms), kGemmThreads, gemm_smem<256>(), st>>>(ma, mb, g);
+        if (mats) k_gemm_tc<256, true><<<std::min(t256, n_sms), gemm_threads<true>(), gemm_smem<256>(), st>>>(ma, mb, g);
+        else k_gemm_tc<256, false><<<std::min(t256, n_sms), gemm_threads<false>(), gemm_smem<256>(), st>>>(ma, mb, g);
     } else {
-        if (mats) k_gemm_tc<128, true><<<std::min(t128, n_sms), kOnehotThreads, gemm_smem<128>(), st>>>(ma, mb, g);
-        else k_gemm_tc<128, false><<<std::min(t128, n_sms), kGemmThreads, gemm_smem<128>(), st>>>(ma, mb, g);
+        if (mats) k_gemm_tc<128, true><<<std::min(t128, n_sms), gemm_threads<true>(), gemm_smem<128>(), st>>>(ma, mb, g);
+        else k_gemm_tc<128, false><<<std::min(t128, n_sms), gemm_threads<false>(), gemm_smem<128>(), st>>>(ma, mb, g);
     }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(MS_ERR_CUDA, std::string("gemm launch: ") + cudaGetErrorString(e));
