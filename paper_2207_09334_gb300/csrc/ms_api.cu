@@ -80,6 +80,7 @@ struct ms_sim {
     int n_slices = 0;
     int64_t n_slots = 0, n_back_slots = 0, n_records = 0;
     int max_fwd = 0, max_back = 0;
+    int n_sms = 0;                      // multiprocessors of the device the system lives on
     // state, packed and double buffered: sa = (x, y, z, vx), sb = (vy, vz);
     // w = 1/m, or -m for an anchored mass (constant)
     float4 *sa[2] = {nullptr, nullptr};
@@ -95,6 +96,8 @@ struct ms_sim {
     // tiled layout
     int kernel = 0;                     // ms::kKernelGather or ms::kKernelTiled (record layout)
     bool persistent = false;            // stepped by the persistent cluster kernel (ms_cluster.cu)
+    bool grid_persistent = false;       // tiled layout stepped by the persistent grid kernel (ms_step.cu)
+    unsigned *grid_bar = nullptr;       // its barrier: arrivals, generation
     uint16_t *cl_nbr = nullptr;         // its records (both directions, lane-interleaved per tile)
     float2 *cl_kl = nullptr, *cl_ab = nullptr;
     float *cl_c = nullptr;
@@ -237,15 +240,19 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
     s->c_uniform = c_uniform;
 
     if (p->kernel < 0 || p->kernel > 3 || p->reorder < 0 || p->reorder > 2) return fail(MS_ERR_ARG, "kernel must be 0..3 and reorder 0..2");
-    const bool small = N <= ms::kClMassesMax * ms::kClusterMax && p->integrator == 0;
-    if (p->kernel == 3 && !small)
-        return fail(MS_ERR_ARG, "the persistent kernel takes at most 8192 masses and symplectic Euler");
+    if (p->kernel == 3 && p->integrator != 0)
+        return fail(MS_ERR_ARG, "the persistent kernel integrates with symplectic Euler only");
+    // persistent: up to kClusterMax x kClMassesMax masses one thread-block
+    // cluster; above, the tiled layout in one cooperative launch (one wave of tiles)
+    const bool cluster_fits = N <= ms::kClMassesMax * ms::kClusterMax;
     s->kernel = p->kernel == 1 ? ms::kKernelGather
               : p->kernel == 2 ? ms::kKernelTiled
               : p->kernel == 3 ? ms::kKernelPersistent
               : ms::kKernelTiled;
     const bool persistent = s->kernel == ms::kKernelPersistent;
-    if (persistent) s->kernel = ms::kKernelGather;     // gather layout for the energy kernel; stepped by the cluster kernel
+    s->grid_persistent = persistent && !cluster_fits;
+    // the cluster kernel keeps the gather layout (for the energy kernel); the grid kernel steps the tiled one
+    if (persistent) s->kernel = cluster_fits ? ms::kKernelGather : ms::kKernelTiled;
 
     // 1. mass order
     s->perm.resize(N); s->iperm.resize(N);
@@ -441,7 +448,7 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
             const int nloc = nb + (int)halo.size();
             max_local = std::max(max_local, nloc);
             if (nloc > ms::kTileMaxLocal) {
-                if (s->p.kernel == ms::kKernelTiled)
+                if (s->p.kernel == ms::kKernelTiled || s->grid_persistent)
                     return fail(MS_ERR_ARG, "tile " + std::to_string(t) + " needs " + std::to_string(nloc) +
                                                 " shared-memory entries (> " + std::to_string(ms::kTileMaxLocal) + ")");
                 s->kernel = ms::kKernelGather;       // fall back to the gather layout
@@ -539,7 +546,7 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
             }
     }
     s->n_slots = n_slots;
-    s->persistent = persistent && s->kernel == ms::kKernelGather;
+    s->persistent = persistent && cluster_fits;
     s->rec_slot_a.swap(slot_a);
     s->rec_slot_b.swap(slot_b);
 
@@ -659,6 +666,21 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
         }
         if ((st = upload<float4>(s, &s->rk_acc, nullptr, 2 * (size_t)N)) != MS_OK) return st;
     }
+    {
+        int dev = 0;
+        MS_CUDA_TRY(cudaGetDevice(&dev));
+        MS_CUDA_TRY(cudaDeviceGetAttribute(&s->n_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    if (s->grid_persistent) {
+        if (s->n_tiles > s->n_sms)
+            return fail(MS_ERR_ARG, "the persistent kernel takes one tile of " + std::to_string(ms::kTileMasses) +
+                                        " masses per multiprocessor: " + std::to_string(s->n_tiles) + " tiles > " +
+                                        std::to_string(s->n_sms));
+        if (ms::grid_smem_bytes(s->max_tile_local, s->max_fwd, c != nullptr, false) > ms::kTileSmemMax)
+            return fail(MS_ERR_ARG, "the persistent kernel's tile records do not fit shared memory");
+        if ((st = upload<unsigned>(s, &s->grid_bar, nullptr, 2)) != MS_OK) return st;
+        MS_CUDA_TRY(cudaMemsetAsync(s->grid_bar, 0, 2 * sizeof(unsigned), s->stream));
+    }
     // err[0]: sticky device error flags; err[1]: scratch of ms_set_state's finiteness check
     if ((st = upload<int>(s, &s->err, nullptr, 2)) != MS_OK) return st;
     MS_CUDA_TRY(cudaMemsetAsync(s->err, 0, 2 * sizeof(int), s->stream));
@@ -687,7 +709,8 @@ ms_status ms_set_actuation(ms_sim *s, float freq_hz, const float *amp, const flo
     if (!amp) { s->actuated = false; s->freq = 0.0; return MS_OK; }
     if (!phase) return fail(MS_ERR_ARG, "phase is required with amp");
     if (!std::isfinite(freq_hz)) return fail(MS_ERR_ARG, "freq must be finite");
-    if (s->persistent && ms::cluster_smem_bytes(s->cl_tm, s->cl_slots, s->cl_c != nullptr, true) > 227 * 1024)
+    if ((s->persistent && ms::cluster_smem_bytes(s->cl_tm, s->cl_slots, s->cl_c != nullptr, true) > 227 * 1024) ||
+        (s->grid_persistent && ms::grid_smem_bytes(s->max_tile_local, s->max_fwd, s->f_c != nullptr, true) > ms::kTileSmemMax))
         return fail(MS_ERR_ARG, "the persistent kernel cannot hold the actuation coefficients of this system in "
                                 "shared memory; create it with the tiled kernel");
     const int64_t S = s->S, nrec = s->n_records, n = s->n_slots;
@@ -762,10 +785,33 @@ ms_status ms_step(ms_sim *s, int32_t nsteps)
     a.b_ent = s->b_ent; a.err = s->err; a.N = s->N; a.c_uniform = s->c_uniform;
     a.t_nbr = s->t_nbr; a.tiles = s->tiles; a.halo = s->halo; a.n_tiles = s->n_tiles;
     a.tile_local = s->max_tile_local; a.tiled = s->kernel == ms::kKernelTiled;
+    a.max_slots = s->max_fwd; a.n_sms = s->n_sms;
     a.dt = s->p.dt; a.gx = s->p.g[0]; a.gy = s->p.g[1]; a.gz = s->p.g[2];
     a.k_c = s->p.k_c; a.mu = s->p.mu; a.keep = 1.0f - s->p.vel_damping; a.contact = s->p.contact_on;
     a.integrator = s->p.integrator;
     a.rk_acc = s->rk_acc;
+    if (s->grid_persistent) {
+        if (nsteps == 0) return MS_OK;
+        const float2 *sc = nullptr;
+        if (s->actuated) {
+            if (nsteps > s->sc_cap) {
+                ms_status st = upload<float2>(s, &s->sc, nullptr, (size_t)nsteps);
+                if (st != MS_OK) return st;
+                s->sc_cap = nsteps;
+            }
+            ms::launch_sc_table_from(s->step_count, nsteps, (double)s->p.dt, two_pi_f, s->sc, s->stream);
+            MS_CUDA_TRY(cudaGetLastError());
+            sc = s->sc;
+        }
+        ms::GridArgs gr{};
+        gr.buf_a[0] = s->sa[s->cur]; gr.buf_a[1] = s->sa[s->cur ^ 1];
+        gr.buf_b[0] = s->sb[s->cur]; gr.buf_b[1] = s->sb[s->cur ^ 1];
+        gr.sc = sc; gr.nsteps = nsteps; gr.bar_count = s->grid_bar; gr.bar_gen = s->grid_bar + 1;
+        MS_CUDA_TRY(ms::launch_step_grid(a, gr, s->stream));
+        s->cur ^= nsteps & 1;
+        s->step_count += nsteps;
+        return MS_OK;
+    }
     for (int32_t n = 0; n < nsteps; ++n) {
         a.first_step = (s->step_count + n == 0) ? 1 : 0;
         const double t = (double)(s->step_count + n) * (double)s->p.dt;
@@ -889,7 +935,8 @@ ms_status ms_trace_set(ms_sim *s, const int32_t *masses, int32_t n_masses, int32
     if (!s) return fail(MS_ERR_ARG, "sim is NULL");
     if (n_masses < 0 || capacity < 0 || (n_masses > 0 && (!masses || capacity < 1)))
         return fail(MS_ERR_ARG, "need n_masses >= 0, and masses and capacity >= 1 when n_masses > 0");
-    if (n_masses > 0 && s->persistent) return fail(MS_ERR_ARG, "the persistent kernel records no per-step trace");
+    if (n_masses > 0 && (s->persistent || s->grid_persistent))
+        return fail(MS_ERR_ARG, "the persistent kernel records no per-step trace");
     if ((int64_t)n_masses * capacity * 3 >= ((int64_t)1 << 40)) return fail(MS_ERR_ARG, "trace too large");
     std::vector<int32_t> idx(n_masses);
     for (int32_t q = 0; q < n_masses; ++q) {
@@ -927,7 +974,7 @@ ms_status ms_get_info(const ms_sim *s, ms_info_t *out)
     out->n_slots = s->n_slots; out->n_back_slots = s->n_back_slots; out->device_bytes = s->device_bytes;
     out->step_count = s->step_count; out->stability_bound = s->stability;
     out->max_fwd_degree = s->max_fwd; out->max_back_degree = s->max_back;
-    out->kernel = s->persistent ? ms::kKernelPersistent : s->kernel;
+    out->kernel = (s->persistent || s->grid_persistent) ? ms::kKernelPersistent : s->kernel;
     out->n_tiles = s->n_tiles; out->max_tile_local = s->max_tile_local;
     return MS_OK;
 }

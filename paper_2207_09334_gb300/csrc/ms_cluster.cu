@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kClThreads) k_cluster(const ClusterArgs a)
                 const float2 pb = cl_load2(cl_map(cur_b + (pm << 3), pt));
                 const float2 kl = rkl[e];
                 float Lr = kl.y;
-                if (HAS_ACT) { const float2 ab = rab[e]; Lr = Lr * (1.0f + (ab.x * scn.x + ab.y * scn.y)); }
+                if (HAS_ACT) { const float2 ab = rab[e]; Lr = Lr * (1.0f + fmaf(ab.x, scn.x, ab.y * scn.y)); }
                 const float c = HAS_C ? rc[e] : a.c_uniform;
                 // Hooke term of eq. 2 plus the axial dashpot, d = x_partner - x_self
                 const float dx = pa.x - x.x, dy = pa.y - x.y, dz = pa.z - x.z;

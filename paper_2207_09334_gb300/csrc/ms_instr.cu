@@ -46,7 +46,7 @@ __device__ __forceinline__ float spring_pe(const EnergyArgs &a, const float4 xi,
 {
     const float2 kl = __ldg(&a.f_kl[r]);
     float L = kl.y;
-    if (a.f_ab) { const float2 ab = __ldg(&a.f_ab[r]); L = L * (1.0f + (ab.x * a.s_n + ab.y * a.c_n)); }
+    if (a.f_ab) { const float2 ab = __ldg(&a.f_ab[r]); L = L * (1.0f + fmaf(ab.x, a.s_n, ab.y * a.c_n)); }
     const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
     const float e = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - L;
     return kl.x * e * e;

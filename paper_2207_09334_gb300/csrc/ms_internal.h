@@ -67,6 +67,8 @@ constexpr int kTileMasses = 512;   // masses per tile (= threads per CTA)
 constexpr int kTileMaxLocal = 2048; // tile members + halo that fit the CTA's shared memory (24 B each)
 constexpr int kTileGroup = 3;      // spring slots per pipeline stage (one bulk copy per array)
 constexpr int kTileStages = 2;     // pipeline depth
+constexpr int kTileStagesDeep = 9; // small systems (one wave of tiles): one stage per slot group, up to 27 slots
+constexpr size_t kTileSmemMax = 226 * 1024;   // dynamic shared memory a tiled CTA opts in to (227 KB less its static part)
 constexpr int kErrNonFinite = 1;   // bits of the device error flag
 constexpr int kErrTimeout = 2;
 
@@ -98,6 +100,8 @@ struct StepArgs {
     const int32_t *halo;
     int n_tiles;
     int tile_local;      // max members + halo over the tiles (shared-memory entries)
+    int max_slots;       // max slots per member over the tiles
+    int n_sms;           // multiprocessors of the device (one wave of tiles when n_tiles <= n_sms)
     int tiled;           // 1: tiled layout
     int *err;            // non-finite flag (sticky)
     int N;
@@ -113,6 +117,19 @@ struct StepArgs {
     float4 *rk_acc;          // RK4: weighted sum of the stage slopes (2 float4 per mass)
     int rk_stage;            // RK4: stage 0..3
 };
+
+// Persistent grid step (ms_step.cu): nsteps steps of the tiled layout in one
+// cooperative launch; buffer n & 1 holds the state at step n of the call.
+struct GridArgs {
+    float4 *buf_a[2];
+    float2 *buf_b[2];
+    const float2 *sc;        // (sin, cos)(2 pi f t_n) per step, if actuated
+    int nsteps;
+    unsigned *bar_count;     // grid barrier: arrivals (zeroed before each launch)
+    unsigned *bar_gen;       //               generation
+};
+size_t grid_smem_bytes(int tile_local, int slots, bool has_c, bool has_act);
+cudaError_t launch_step_grid(const StepArgs &a, const GridArgs &g, cudaStream_t st);
 
 // Energy reduction (ms_instr.cu) over either record layout.
 struct EnergyArgs {

@@ -46,8 +46,6 @@ KERNELS = ["gather", "tiled", "persistent"]
 
 
 def gpu_run(ms, s, p, n, reorder=None, chunks=1, kernel=None):
-    if kernel == "persistent" and s["x"].shape[0] > 8192:
-        pytest.skip("the persistent kernel takes at most 8192 masses")
     with ms.Sim(s, p, reorder=reorder, kernel=kernel) as sim:
         done = 0
         for q in range(chunks):
@@ -371,6 +369,72 @@ def test_persistent_actuation_that_does_not_fit_shared_memory_is_refused(ms):
         sim.step(10)
         x, _ = sim.get_state()
         assert np.isfinite(x).all()
+
+
+def lattice24(seed, c_per_spring):
+    """24^3 lattice (13 824 masses: above the cluster kernel, 27 tiles of the
+    grid kernel) in the throughput lattice's style, resting on the ground."""
+    x, ij, L0 = synth.box_lattice(24, 24, 24, 1e-3, origin=(0, 0, -2e-5))
+    rng = np.random.default_rng(seed)
+    S = ij.shape[0]; N = x.shape[0]
+    return dict(x=x, v=(1e-3 * rng.standard_normal((N, 3))).astype(np.float32),
+                m=np.full(N, 1e-3, np.float32), fixed=np.zeros(N, np.uint8), ij=ij,
+                k=rng.uniform(5e3, 5e4, S).astype(np.float32),
+                c=rng.uniform(0.0, 0.1, S).astype(np.float32) if c_per_spring else np.float32(0.05), L0=L0)
+
+
+def test_persistent_grid_kernel_is_bit_identical_to_the_tiled_kernel(ms):
+    """Above 8192 masses the persistent kernel runs the tiled layout in one
+    cooperative launch: the same arithmetic in the same order as the per-step
+    tiled launches, so the states agree bit for bit (contact, friction,
+    per-spring damping, an odd and an even call length)."""
+    s = lattice24(31, True)
+    p = synth.params(dt=5e-5, g=(0, 0, -9.81), contact=True, k_c=1e5, mu=0.5)
+    out = []
+    for kernel in ("persistent", "tiled"):
+        with ms.Sim(s, p, kernel=kernel) as sim:
+            assert sim.info()["kernel"] == (3 if kernel == "persistent" else 2)
+            sim.step(151); sim.step(100)
+            out.append(sim.get_state())
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_persistent_grid_kernel_actuated_lattice_matches_oracle(ms, ora):
+    """22^3 masses (21 tiles) joined by edge and face-diagonal springs only
+    (degree <= 19 with compact rows, so the actuation coefficients fit the
+    grid kernel's shared memory), actuated, with an external force, against
+    the oracle."""
+    x, ij, L0 = synth.box_lattice(22, 22, 22, 1e-3, origin=(0, 0, 0.01))
+    keep = L0 < 1.6e-3                                   # a and a sqrt 2, not a sqrt 3
+    # plus one spring of length 2a beside an edge spring (mass 0 to mass 2): two
+    # springs of one mass in one direction, so rows are compact (19 slots), not
+    # one slot per lattice direction
+    ij = np.concatenate([ij[keep], np.array([[0, 2]], np.int32)])
+    L0 = np.concatenate([L0[keep], np.array([2e-3], np.float32)])
+    rng = np.random.default_rng(37)
+    S = ij.shape[0]; N = x.shape[0]
+    s = dict(x=x, v=(1e-3 * rng.standard_normal((N, 3))).astype(np.float32), m=np.full(N, 1e-3, np.float32),
+             fixed=(np.arange(N) < 22 * 22).astype(np.uint8), ij=ij, k=rng.uniform(5e3, 5e4, S).astype(np.float32),
+             c=np.float32(0.05), L0=L0, A=rng.uniform(0, 0.1, S).astype(np.float32),
+             phi=rng.uniform(0, 2 * np.pi, S).astype(np.float32), freq=40.0,
+             fext=(1e-4 * rng.standard_normal((N, 3))).astype(np.float32))
+    p = synth.params(dt=5e-5, g=(0, 0, -9.81), contact=False)
+    with ms.Sim(s, p, kernel="persistent") as sim:
+        assert sim.info()["kernel"] == 3
+        sim.step(120); sim.step(80)
+        xg, _ = sim.get_state()
+    xo, _ = ora.run(s, f32p(p), 200)
+    err = np.abs(xg.astype(np.float64) - xo).max()
+    assert err <= 1e-5 * body_size(s), (err, 1e-5 * body_size(s))
+
+
+def test_persistent_kernel_refuses_more_tiles_than_multiprocessors(ms):
+    """The grid kernel needs every tile resident at once: a 64^3 lattice
+    (512 tiles) is refused with a message, not launched."""
+    s = synth.throughput_lattice(n=64)
+    with pytest.raises(ms.MsError) as e:
+        ms.Sim(s, synth.throughput_params(), kernel="persistent")
+    assert e.value.code == 1 and "multiprocessor" in str(e.value)
 
 
 def test_set_state_rejects_non_finite_host_input_and_keeps_the_state(ms):
