@@ -71,14 +71,17 @@ typedef struct {
                                2 = caller order */
     int32_t kernel;         /* 0 = library default: tiled (gather when a tile's partners do not fit
                                shared memory); 1 = gather, 2 = tiled (MS_ERR_ARG if a tile does not fit),
-                               3 = persistent: all steps of one ms_step call in one launch of a
-                               thread-block cluster (at most 16 CTAs, one per tile of 64 to 512
-                               masses), with the state and the spring records in shared memory and
-                               partners in other CTAs read through distributed shared memory; for
-                               small systems.  MS_ERR_ARG beyond 8192 masses, when the records do
-                               not fit shared memory, or with an integrator other than symplectic
-                               Euler; ms_set_actuation returns MS_ERR_ARG when the actuation
-                               coefficients do not fit as well */
+                               3 = persistent: all steps of one ms_step call in one launch.  Up to
+                               8192 masses: a thread-block cluster (at most 16 CTAs, one per tile
+                               of 64 to 512 masses) with the state and the spring records in
+                               shared memory, partners in other CTAs read through distributed
+                               shared memory.  Above: the tiled layout in one cooperative launch
+                               (one CTA per 512-mass tile, at most one per multiprocessor), each
+                               tile's records in shared memory, a grid barrier per step.
+                               MS_ERR_ARG when the system has more tiles than multiprocessors,
+                               when the records do not fit shared memory, or with an integrator
+                               other than symplectic Euler; ms_set_actuation returns MS_ERR_ARG
+                               when the actuation coefficients do not fit as well */
 } ms_params;
 
 /* Optional device allocator (e.g. a framework's caching allocator).
