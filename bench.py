@@ -293,19 +293,25 @@ def run_ours(args, world, rank, local):
         xo = torch.empty_like(xh).pin_memory(); vo = torch.empty_like(vh).pin_memory()
         e2e_times = []
         reps.barrier()
-        for it in range(args.e2e_iters + 1):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            sim.set_state(xh, vh)
-            sim.step(e2e_steps)
-            sim.get_state(xo, vo)
-            el = time.perf_counter() - t0
-            if it > 0:
-                e2e_times.append(el)
-        e2e_val = reps.throughput((N + S) * e2e_steps, statistics.median(e2e_times))
-        e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_state,
-               "d2h_bytes_per_step": bytes_state,
-               "note": f"each e2e step = ms_set_state(pinned host) + ms_step({e2e_steps}) + ms_get_state(pinned host)"}
+        try:
+            for it in range(args.e2e_iters + 1):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                sim.set_state(xh, vh)
+                sim.step(e2e_steps)
+                sim.get_state(xo, vo)
+                el = time.perf_counter() - t0
+                if it > 0:
+                    e2e_times.append(el)
+            e2e_val = reps.throughput((N + S) * e2e_steps, statistics.median(e2e_times))
+            e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_state,
+                   "d2h_bytes_per_step": bytes_state,
+                   "note": f"each e2e step = ms_set_state(pinned host) + ms_step({e2e_steps}) + ms_get_state(pinned host)"}
+        except ms.MsError as err:
+            # forward Euler (eq. 4) amplifies every undamped mode: on this lattice
+            # the state leaves the finite range within the e2e leg's steps
+            e2e = {"value": None, "unit": UNIT, "h2d_bytes_per_step": bytes_state, "d2h_bytes_per_step": bytes_state,
+                   "note": f"not measured: {err}"}
 
     hbm, hbm_kind = peaks()
     alg_bytes = BYTES_PER_MASS * N + BYTES_PER_SPRING * S
