@@ -388,7 +388,7 @@ ms_status msa_destroy(msa_adjoint *a);
  * bf16 weights and activations, fp32 accumulation on the tensor cores
  * (tcgen05 + TMEM, operands staged by TMA).  It predicts a voxel design's
  * locomotion distance from its one-hot materials so that large candidate
- * populations can be pre-screened before the simulator (above) judges the
+ * populations can be pre-screened before the simulator (above) scores the
  * best.  The paper has no learned component; this serves the optimisation
  * loop the paper motivates (Introduction: simulation for design and
  * optimisation of soft robots).

@@ -5,7 +5,7 @@
 2. Train the MLP surrogate on (one-hot materials -> travel) with the
    tensor-core kernels.
 3. Screen a large candidate population with the surrogate, and re-simulate
-   the best fraction with the simulator, which stays the judge.
+   the best fraction with the simulator, which has the final word.
 
 Everything numerical runs in the library (Population, Surrogate); this
 module only orchestrates batches.
