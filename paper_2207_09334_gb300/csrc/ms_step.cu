@@ -500,8 +500,9 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
     return v;
 }
 
-// every CTA of the grid: global writes before it are visible after it; false
-// when the wait gave up
+// every CTA of the grid: global writes before it are visible after it (the
+// CTA barrier orders its threads' stores before thread 0's fence, which then
+// releases them with the arrival); false when the wait gave up
 __device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks, unsigned &my_gen,
                                              int *ok_sh)
 {
@@ -592,7 +593,6 @@ __global__ void __launch_bounds__(kTileMasses, 1) k_step_grid(const StepArgs a, 
             integrate_mass<HAS_FEXT, false>(a, i, xi, vi, fx, fy, fz, xn, vn);
             gr.buf_a[cur ^ 1][i] = make_float4(xn.x, xn.y, xn.z, vn.x);
             gr.buf_b[cur ^ 1][i] = make_float2(vn.y, vn.z);
-            __threadfence();                              // the writer orders its stores before the barrier
             xi = xn; vi = vn;
         }
         ok = grid_barrier(gr.bar_count, gr.bar_gen, gridDim.x, my_gen, &ok_sh);
