@@ -102,6 +102,17 @@ def test_tiled_kernel_rejects_tiles_that_overflow_shared_memory(lib):
     assert rc == 1 and "shared-memory" in lib.ms_last_error().decode()
 
 
+def test_persistent_kernel_takes_symplectic_euler_only(lib):
+    from paper_2207_09334_gb300._lib import MsParams
+    p = MsParams(); p.dt = 1e-3; p.kernel = 3; p.integrator = 2
+    x = np.array([[0, 0, 0], [1, 0, 0]], np.float32); v = np.zeros_like(x)
+    m = np.ones(2, np.float32); ij = np.array([[0, 1]], np.int32); k = np.ones(1, np.float32)
+    out = C.c_void_p()
+    rc = lib.ms_create(C.byref(p), 2, x.ctypes.data, v.ctypes.data, m.ctypes.data, None, None,
+                       1, ij.ctypes.data, k.ctypes.data, None, 0.0, None, None, None, C.byref(out))
+    assert rc == 1 and "symplectic Euler" in lib.ms_last_error().decode()
+
+
 def test_bad_kernel_choice(lib):
     rc, _ = _create(lib, kernel=7)
     assert rc == 1 and "kernel" in lib.ms_last_error().decode()
