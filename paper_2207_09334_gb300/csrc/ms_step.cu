@@ -1,11 +1,19 @@
-// ms_step.cu -- the explicit mass-spring step on sm_103a.
+// ms_step.cu -- the explicit mass-spring step on sm_103a: three kernels over
+// the same arithmetic (spring_term_packed, integrate_mass).
+//   * k_step (gather layout, kernel = 1): one thread per mass, one launch per
+//     time step (below).
+//   * k_step_tiled (tiled layout, the default): one CTA per 512-mass tile
+//     with its halo staged in shared memory and the spring rows streamed by
+//     TMA bulk copies; one launch per time step.
+//   * k_step_grid (tiled layout, kernel = 3 above the cluster kernel's size):
+//     all steps of a call in one cooperative launch with a grid barrier.
 //
-// One thread per mass (internal order), one launch per time step.  Each
-// thread gathers every spring attached to its mass -- the springs it owns
-// from its own sliced-ELL row, the others through back references into the
-// owners' rows -- evaluates eq. 2's Hooke term plus the axial dashpot with the
-// partner's state at t_n, adds gravity, external force and ground contact,
-// and integrates (symplectic Euler) into the other state buffer.
+// The gather kernel: each thread gathers every spring attached to its mass --
+// the springs it owns from its own sliced-ELL row, the others through back
+// references into the owners' rows -- evaluates eq. 2's Hooke term plus the
+// axial dashpot with the partner's state at t_n, adds gravity, external force
+// and ground contact, and integrates (symplectic Euler) into the other state
+// buffer.
 //
 // This replaces Algorithm 1's two passes (spring pass appending forces to
 // per-mass slots reserved with an integer atomicAdd, grid-wide sync, mass
@@ -567,8 +575,10 @@ __global__ void __launch_bounds__(kTileMasses, 1) k_step_grid(const StepArgs a, 
     bool ok = true;
     for (int step = 0; step < gr.nsteps && ok; ++step) {
         const int cur = step & 1;
-        // stage members (from registers) and halo (written by other CTAs, read through L2)
-        __syncthreads();                                  // the previous step's shared reads are done
+        // stage members (from registers) and halo (written by other CTAs, read
+        // through L2); the grid barrier's CTA barriers ordered the previous
+        // step's shared reads before these writes, and each thread reads back
+        // only the halo indices it wrote itself
         if (active) { spa[tid] = make_float4(xi.x, xi.y, xi.z, vi.x); spb[tid] = make_float2(vi.y, vi.z); }
         for (int h = tid; h < nh; h += kTileMasses) {
             const int g = hidx[h];
