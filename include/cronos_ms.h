@@ -180,9 +180,30 @@ ms_status ms_step(ms_sim *sim, int32_t nsteps);
 ms_status ms_get_state(ms_sim *sim, float *x, float *v, int32_t on_device);
 ms_status ms_set_state(ms_sim *sim, const float *x, const float *v, int32_t on_device);
 
-/* ms_sync -- wait for the object's stream; returns MS_ERR_NONFINITE if a
- * step produced a non-finite value since creation (sticky), else MS_OK. */
+/* ms_sync -- wait for the object's stream (paper: "GPU Implementation" --
+ * the host waits for the device before it reads results back); returns
+ * MS_ERR_TIMEOUT if a bounded device-side wait gave up, MS_ERR_NONFINITE if a
+ * step produced a non-finite value since creation (both sticky), else MS_OK. */
 ms_status ms_sync(ms_sim *sim);
+
+/*
+ * ms_set_wait_limit -- polls of each bounded device-side wait of the
+ * persistent grid kernel (its grid barrier, Algorithm 1's synchronisation
+ * between steps) before the waiting CTA gives up, leaves its step loop and
+ * flags MS_ERR_TIMEOUT for the next synchronising call.  0 restores the
+ * default, 2^22 polls with a short sleep each (well over a second).  A limit
+ * shorter than one step's work reports timeouts on a healthy run; the state
+ * is then only partly advanced.
+ *
+ * ms_test_barrier_deficit -- failure-detection test hook with no counterpart
+ * in the paper: the grid barrier of later ms_step calls waits for `missing`
+ * arrivals beyond the CTAs that exist (0 = off, at most 1024), so no wait can
+ * complete and every CTA gives up after the wait limit.  Only a sim stepped
+ * by the persistent grid kernel accepts missing > 0 (MS_ERR_ARG otherwise).
+ * Nothing faults or hangs: every wait is bounded and no copy is in flight.
+ */
+ms_status ms_set_wait_limit(ms_sim *sim, int32_t max_polls);
+ms_status ms_test_barrier_deficit(ms_sim *sim, int32_t missing);
 
 /*
  * ms_energy -- energy of the current state at t_n = step_count dt, reduced on
@@ -434,14 +455,14 @@ ms_status mlp_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int32_t 
 /* ------------------------------------------------------------------------
  * Stepping without allocating.
  *
- * The paper has no counterpart to this entry point; it exists for callers
- * that must not allocate device memory when they advance a system: code
- * running while a CUDA graph is being captured (allocation calls are not
- * capturable), plugins inside a host framework that owns every device
- * allocation, and real-time loops that forbid allocator calls.  The caller
- * owns every input and output; the only working memory is a fixed array
- * that the library declares in its own device memory, so every GPU that
- * loads the library holds it (16 MiB) until the process exits.
+ * The paper has no counterpart to this entry point.  It exists for callers
+ * that cannot allocate device memory when they advance a system: plugins
+ * inside a host application that owns every device allocation and hands the
+ * plugin only the buffers it needs, and real-time loops whose latency budget
+ * forbids allocator calls (which may synchronise the device or take a lock).
+ * The caller owns every input and output; the only working memory is a
+ * fixed array that the library declares in its own device memory, so every
+ * GPU that loads the library holds it (16 MiB) until the process exits.
  * ---------------------------------------------------------------------- */
 #define MS_NOALLOC_MAX_MASSES 262144
 
@@ -461,12 +482,18 @@ ms_status mlp_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int32_t 
  *   x_out, v_out (N,3) device, state after nsteps; must not alias the inputs.
  *   stream       cudaStream_t (NULL = legacy default stream); asynchronous.
  * The intermediate states of a multi-step call live in the library's fixed
- * scratch array, which every call shares: calls whose work overlaps on the
- * GPU (on different streams, or from different threads) race on it and must
- * be serialised by the caller.  The first call on each device looks up the
- * array's device address (with that device current) and caches it; make
- * that first call before any stream capture begins.  Non-finite results are
- * not flagged by this entry point.
+ * scratch array, which every call shares and which keeps the last call's
+ * contents (each call writes a buffer in full before reading it): calls whose
+ * work overlaps on the GPU (on different streams, or from different threads)
+ * race on it and must be serialised by the caller.  The first call in a CUDA
+ * context (per device, and again after a device reset creates a new
+ * context) looks up the array's device address with that device current and
+ * caches it; make that first call before any stream capture begins.
+ * Preconditions that are NOT checked (the arrays are device memory and are
+ * not copied to the host): mass > 0 for masses that are not anchored,
+ * 0 <= partner < N, row_ptr non-decreasing with row_ptr[0] = 0 and row_ptr[N]
+ * the number of entries, every entry's k, c, rest_len finite.  Non-finite
+ * results are not flagged by this entry point.
  */
 ms_status ms_step_csr_noalloc(const ms_params *p, int32_t N, const float *x_in, const float *v_in,
                               const float *mass, const uint8_t *fixed, const int32_t *row_ptr,

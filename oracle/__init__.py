@@ -5,8 +5,8 @@ legs may import this package.  The GPU library never does, and this package
 never imports the library: the two share no code.  The numerical work lives
 in ``ms_oracle.c`` (plain C, FP64, springs summed in index order); this file
 builds it with gcc, marshals numpy arrays into it and adds the small plain
-definitions that sit around the step: the voxel-robot lattice, energies,
-centre-of-mass travel, finite differences and the MLP of the surrogate.
+definitions that sit around the step: energies, the centre of mass and the
+voxel-robot lattice.  ``oracle/mlp.py`` holds the MLP of the surrogate.
 """
 from __future__ import annotations
 
@@ -38,8 +38,12 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                "-o", tmp, _SRC, "-lm"]
+        try:        # OpenMP only serves ora_run_threads (timing on all host cores)
+            subprocess.check_call(base + ["-fopenmp"], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _SO)
     return _SO
 
@@ -54,10 +58,8 @@ def lib():
             l.ora_run.argtypes = [C.POINTER(OraParams), C.c_int64, dp, dp, dp, C.c_void_p, C.c_void_p,
                                   C.c_int64, C.c_void_p, dp, dp, dp, C.c_void_p, C.c_void_p,
                                   C.c_int64, C.c_int64]
-            l.ora_force.restype = C.c_int
-            l.ora_force.argtypes = [C.POINTER(OraParams), C.c_int64, dp, dp, dp, C.c_void_p, C.c_void_p,
-                                    C.c_int64, C.c_void_p, dp, dp, dp, C.c_void_p, C.c_void_p,
-                                    C.c_double, dp]
+            l.ora_run_threads.restype = C.c_int
+            l.ora_run_threads.argtypes = l.ora_run.argtypes + [C.c_int32, C.POINTER(C.c_int32)]
             _lib = l
     return _lib
 
@@ -131,19 +133,24 @@ def run(system: dict, params: dict, nsteps: int, n0: int = 0, x=None, v=None,
     return x, v
 
 
-def force(system: dict, params: dict, x, v, t: float, arrays: _Arrays | None = None):
-    """Total force of eq. 2 (plus dashpot and ground normal) at (x, v, t)."""
+def run_threads(system: dict, params: dict, nsteps: int, threads: int, n0: int = 0, x=None, v=None,
+                arrays: _Arrays | None = None):
+    """run() on `threads` host threads (symplectic Euler only), for timing the
+    oracle on all cores.  Each thread owns a block of masses and sums their
+    springs in spring-index order, so the result equals run() bit for bit.
+    Returns (x, v, threads actually used)."""
     ar = arrays or _Arrays(system)
     N = ar.N
-    x = _f64(x, (N, 3)); v = _f64(v, (N, 3))
-    F = np.zeros((N, 3))
+    x = _f64(system["x"] if x is None else x, (N, 3)).copy()
+    v = _f64(system["v"] if v is None else v, (N, 3)).copy()
     p = make_params(params, ar.freq)
-    rc = lib().ora_force(C.byref(p), N, _dptr(x), _dptr(v), _dptr(ar.m), _ptr(ar.fixed), _ptr(ar.fext),
-                         ar.S, _ptr(ar.ij), _dptr(ar.k), _dptr(ar.c), _dptr(ar.L0), _ptr(ar.A), _ptr(ar.phi),
-                         float(t), _dptr(F))
+    used = C.c_int32(0)
+    rc = lib().ora_run_threads(C.byref(p), N, _dptr(x), _dptr(v), _dptr(ar.m), _ptr(ar.fixed), _ptr(ar.fext),
+                               ar.S, _ptr(ar.ij), _dptr(ar.k), _dptr(ar.c), _dptr(ar.L0), _ptr(ar.A),
+                               _ptr(ar.phi), int(n0), int(nsteps), int(threads), C.byref(used))
     if rc != 0:
-        raise RuntimeError(f"ora_force failed with code {rc}")
-    return F
+        raise RuntimeError(f"ora_run_threads failed with code {rc}")
+    return x, v, int(used.value)
 
 
 # ---------------------------------------------------------------------------
@@ -245,10 +252,3 @@ def voxel_system(mat, phase, materials, freq: float, a: float, voxel_mass: float
         spring_voxel=np.asarray(sv, np.int64), corner_of=cid_used,
     )
     return sysd
-
-
-def com_travel_x(system: dict, params: dict, nsteps: int, integrator="symplectic_euler"):
-    """Centre-of-mass x travel of a system after nsteps steps (FP64)."""
-    x1, _ = run(system, params, nsteps, integrator=integrator)
-    m = _f64(system["m"])
-    return float(centre_of_mass(m, x1)[0] - centre_of_mass(m, system["x"])[0])

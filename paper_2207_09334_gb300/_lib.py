@@ -67,6 +67,8 @@ SIGNATURES = {
     "ms_get_state": (C.c_int, [VP, VP, VP, I32]),
     "ms_set_state": (C.c_int, [VP, VP, VP, I32]),
     "ms_sync": (C.c_int, [VP]),
+    "ms_set_wait_limit": (C.c_int, [VP, I32]),
+    "ms_test_barrier_deficit": (C.c_int, [VP, I32]),
     "ms_get_info": (C.c_int, [VP, C.POINTER(MsInfo)]),
     "ms_energy": (C.c_int, [VP, VP, I32]),
     "ms_trace_set": (C.c_int, [VP, VP, I32, I32]),

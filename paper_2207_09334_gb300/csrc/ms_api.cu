@@ -98,6 +98,8 @@ struct ms_sim {
     bool persistent = false;            // stepped by the persistent cluster kernel (ms_cluster.cu)
     bool grid_persistent = false;       // tiled layout stepped by the persistent grid kernel (ms_step.cu)
     unsigned *grid_bar = nullptr;       // its barrier: arrivals, generation
+    unsigned grid_polls = ms::kGridPollsDefault;   // polls of a barrier wait before it gives up
+    unsigned grid_missing = 0;          // arrivals the barrier waits for beyond the CTAs (timeout test hook)
     uint16_t *cl_nbr = nullptr;         // its records (both directions, lane-interleaved per tile)
     float2 *cl_kl = nullptr, *cl_ab = nullptr;
     float *cl_c = nullptr;
@@ -807,6 +809,8 @@ ms_status ms_step(ms_sim *s, int32_t nsteps)
         gr.buf_a[0] = s->sa[s->cur]; gr.buf_a[1] = s->sa[s->cur ^ 1];
         gr.buf_b[0] = s->sb[s->cur]; gr.buf_b[1] = s->sb[s->cur ^ 1];
         gr.sc = sc; gr.nsteps = nsteps; gr.bar_count = s->grid_bar; gr.bar_gen = s->grid_bar + 1;
+        gr.expected = (unsigned)s->n_tiles + s->grid_missing;
+        gr.max_polls = s->grid_polls;
         MS_CUDA_TRY(ms::launch_step_grid(a, gr, s->stream));
         s->cur ^= nsteps & 1;
         s->step_count += nsteps;
@@ -897,8 +901,26 @@ ms_status ms_sync(ms_sim *s)
     MS_CUDA_TRY(cudaStreamSynchronize(s->stream));
     int flag = 0;
     MS_CUDA_TRY(cudaMemcpy(&flag, s->err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (flag & ms::kErrTimeout) return fail(MS_ERR_TIMEOUT, "a bounded device-side wait gave up (bulk copy never completed)");
+    if (flag & ms::kErrTimeout) return fail(MS_ERR_TIMEOUT, "a bounded device-side wait gave up (a bulk copy or a grid barrier never completed)");
     if (flag & ms::kErrNonFinite) return fail(MS_ERR_NONFINITE, "a step produced a non-finite position or velocity");
+    return MS_OK;
+}
+
+ms_status ms_set_wait_limit(ms_sim *s, int32_t max_polls)
+{
+    if (!s) return fail(MS_ERR_ARG, "sim is NULL");
+    if (max_polls < 0) return fail(MS_ERR_ARG, "max_polls must be >= 0");
+    s->grid_polls = max_polls == 0 ? ms::kGridPollsDefault : (unsigned)max_polls;
+    return MS_OK;
+}
+
+ms_status ms_test_barrier_deficit(ms_sim *s, int32_t missing)
+{
+    if (!s) return fail(MS_ERR_ARG, "sim is NULL");
+    if (missing < 0 || missing > 1024) return fail(MS_ERR_ARG, "missing must be in [0, 1024]");
+    if (missing > 0 && !s->grid_persistent)
+        return fail(MS_ERR_ARG, "only the persistent grid kernel has a grid barrier");
+    s->grid_missing = (unsigned)missing;
     return MS_OK;
 }
 

@@ -127,7 +127,10 @@ struct GridArgs {
     int nsteps;
     unsigned *bar_count;     // grid barrier: arrivals (zeroed before each launch)
     unsigned *bar_gen;       //               generation
+    unsigned expected;       // arrivals that complete the barrier (= CTAs; more only in a timeout test)
+    unsigned max_polls;      // polls of a barrier wait before the CTA gives up (MS_ERR_TIMEOUT)
 };
+constexpr unsigned kGridPollsDefault = 1u << 22;
 size_t grid_smem_bytes(int tile_local, int slots, bool has_c, bool has_act);
 cudaError_t launch_step_grid(const StepArgs &a, const GridArgs &g, cudaStream_t st);
 

@@ -29,7 +29,12 @@ constexpr int kMaxDevices = 64;
 __device__ __align__(256) float4 noalloc_scratch[4 * kNoallocMaxMasses];
 
 std::mutex g_mu;
-float4 *g_scratch[kMaxDevices] = {};
+// per device: the context the address was looked up in, and the address
+struct ScratchAddr {
+    unsigned long long ctx_id;
+    float4 *ptr;
+};
+ScratchAddr g_scratch[kMaxDevices] = {};
 
 struct CsrArgs {
     const float4 *st;    // state at t_n (2 float4 per mass); nullptr on the first step
@@ -97,10 +102,40 @@ __global__ void k_step_csr(const CsrArgs a)
     }
 }
 
-// Device address of the scratch array on the current device.  Host code
+// Unique id of the calling thread's current CUDA context (0 when none is
+// current), through driver entry points that the runtime hands out, so the
+// library links no driver library.  A context that is destroyed and created
+// again (a device reset) gets a new id.
+typedef int (*CtxGetCurrentFn)(void **ctx);
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
+
+ms_status current_context_id(unsigned long long *id)
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        cudaError_t e1 = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        cudaError_t e2 = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || q1 != cudaDriverEntryPointSuccess ||
+            q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return fail(MS_ERR_CUDA, "driver entry points cuCtxGetCurrent / cuCtxGetId not available");
+        get_current = (CtxGetCurrentFn)f1;
+        get_id = (CtxGetIdFn)f2;
+    }
+    void *ctx = nullptr;
+    if (get_current(&ctx) != 0) return fail(MS_ERR_CUDA, "cuCtxGetCurrent failed");
+    *id = 0;
+    if (ctx && get_id(ctx, id) != 0) return fail(MS_ERR_CUDA, "cuCtxGetId failed");
+    return MS_OK;
+}
+
+// Device address of the scratch array in the current context.  Host code
 // only has a stand-in symbol for a __device__ array, so the real address is
-// looked up with cudaGetSymbolAddress, once per device, with that device
-// current, and cached.
+// looked up with cudaGetSymbolAddress, with the device current, and cached
+// per device together with the id of the context it belongs to; a call in a
+// different context (after a device reset) looks the address up again.
 ms_status scratch_for_current_device(float4 **scratch)
 {
     int dev = 0;
@@ -108,13 +143,17 @@ ms_status scratch_for_current_device(float4 **scratch)
     if (e != cudaSuccess) return fail(MS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return fail(MS_ERR_ARG, "device index out of range");
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch[dev]) {
+    unsigned long long id = 0;
+    ms_status st = current_context_id(&id);
+    if (st != MS_OK) return st;
+    if (id == 0 || g_scratch[dev].ctx_id != id || !g_scratch[dev].ptr) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, noalloc_scratch);
+        e = cudaGetSymbolAddress(&p, noalloc_scratch);    // makes the device's primary context current if none is
         if (e != cudaSuccess) return fail(MS_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_scratch[dev] = (float4 *)p;
+        if ((st = current_context_id(&id)) != MS_OK) return st;
+        g_scratch[dev] = ScratchAddr{id, (float4 *)p};
     }
-    *scratch = g_scratch[dev];
+    *scratch = g_scratch[dev].ptr;
     return MS_OK;
 }
 

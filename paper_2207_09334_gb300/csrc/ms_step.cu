@@ -494,12 +494,10 @@ cudaError_t launch_step(const StepArgs &a, cudaStream_t st)
 // the other global buffer and meets the other CTAs at a grid barrier.  The
 // members' own state stays in registers across steps.
 // The barrier is a counter and a generation word in global memory; every
-// wait on it is bounded (kMaxGridSpins polls), after which the CTA records
-// kErrTimeout and leaves its step loop.
+// wait on it is bounded (GridArgs::max_polls polls, 2^22 by default), after
+// which the CTA records kErrTimeout and leaves its step loop.
 // ---------------------------------------------------------------------------
 namespace {
-
-constexpr unsigned kMaxGridSpins = 1u << 22;
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
 {
@@ -511,8 +509,8 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
 // every CTA of the grid: global writes before it are visible after it (the
 // CTA barrier orders its threads' stores before thread 0's fence, which then
 // releases them with the arrival); false when the wait gave up
-__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks, unsigned &my_gen,
-                                             int *ok_sh)
+__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks, unsigned max_polls,
+                                             unsigned &my_gen, int *ok_sh)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -526,7 +524,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned *gen, uns
         } else {
             unsigned spins = 0;
             while (ld_acquire_gpu(gen) == g0) {
-                if (++spins > kMaxGridSpins) { ok = false; break; }
+                if (++spins > max_polls) { ok = false; break; }
                 __nanosleep(32);
             }
         }
@@ -605,7 +603,7 @@ __global__ void __launch_bounds__(kTileMasses, 1) k_step_grid(const StepArgs a, 
             gr.buf_b[cur ^ 1][i] = make_float2(vn.y, vn.z);
             xi = xn; vi = vn;
         }
-        ok = grid_barrier(gr.bar_count, gr.bar_gen, gridDim.x, my_gen, &ok_sh);
+        ok = grid_barrier(gr.bar_count, gr.bar_gen, gr.expected, gr.max_polls, my_gen, &ok_sh);
     }
     if (!ok && tid == 0) atomicOr(a.err, kErrTimeout);
 }
@@ -620,7 +618,8 @@ size_t grid_smem_bytes(int tile_local, int slots, bool has_c, bool has_act)
 cudaError_t launch_step_grid(const StepArgs &a, const GridArgs &gr, cudaStream_t st)
 {
     if (a.N <= 0 || gr.nsteps <= 0) return cudaSuccess;
-    if (!a.tiled || a.integrator != 0 || a.n_tiles > a.n_sms) return cudaErrorInvalidValue;
+    if (!a.tiled || a.integrator != 0 || a.n_tiles > a.n_sms || gr.expected < (unsigned)a.n_tiles)
+        return cudaErrorInvalidValue;
     const bool hc = a.f_c != nullptr, ha = a.f_ab != nullptr, hf = a.fext != nullptr;
     const size_t smem = grid_smem_bytes(a.tile_local, a.max_slots, hc, ha);
     if (smem > kTileSmemMax) return cudaErrorInvalidValue;

@@ -181,6 +181,16 @@ class Sim:
     def sync(self):
         check(self._lib.ms_sync(self.h))
 
+    def set_wait_limit(self, max_polls: int = 0):
+        """Polls of a bounded device-side wait (the persistent grid kernel's
+        barrier) before it gives up; 0 = the default."""
+        check(self._lib.ms_set_wait_limit(self.h, int(max_polls)))
+
+    def test_barrier_deficit(self, missing: int):
+        """Failure-detection test hook: the grid barrier waits for `missing`
+        arrivals that never come, so its bounded waits run out."""
+        check(self._lib.ms_test_barrier_deficit(self.h, int(missing)))
+
     def energy(self, out=None):
         """(kinetic, elastic, gravitational, ground) energy of the current
         state, reduced on the device.  With a CUDA float64 tensor `out` of 4

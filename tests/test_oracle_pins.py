@@ -287,6 +287,87 @@ def test_coulomb_friction_stopping(ora):
         np.testing.assert_allclose(x[0, :2], dt * speeds.sum() * v0[:2] / s0, rtol=0, atol=1e-12)
 
 
+# ------------------------------------------------------ energy potentials
+def test_gravitational_energy_is_the_potential_of_free_fall(ora):
+    """Energy Conservation Tests (gravitational energy): along the exact
+    free-fall trajectory x(t) = x0 + v0 t + g t^2/2, v(t) = v0 + g t, the sum
+    kinetic + gravitational energy is constant.  A gravity vector with three
+    non-zero components checks every axis; a flipped sign or a wrong factor
+    in the gravitational term leaves a remainder that grows with t."""
+    m = np.array([2e-3, 5e-3])
+    g = np.array([0.7, -1.3, -9.81])
+    x0 = np.array([[0.1, 0.2, 0.5], [-0.3, 0.0, 1.0]]); v0 = np.array([[0.2, -0.1, 1.5], [0.0, 0.4, -0.2]])
+    s = dict(x=x0, v=v0, m=m, fixed=np.zeros(2, np.uint8), ij=np.zeros((0, 2), np.int32),
+             k=np.zeros(0), c=np.zeros(0), L0=np.zeros(0))
+    p = synth.params(g=tuple(g))
+    E = []
+    for t in np.linspace(0.0, 0.6, 13):
+        ke, pe, gpe, cpe = ora.energy(s, p, x0 + v0 * t + 0.5 * g * t * t, v0 + g * t)
+        assert pe == 0.0 and cpe == 0.0
+        E.append(ke + gpe)
+    ke0 = ora.energy(s, p, x0, v0)[0]
+    assert ke0 > 0 and np.ptp(E) <= 1e-12 * ke0 * 10, np.ptp(E)
+    # and the potential falls along g: a mass moved by +g/|g| loses m |g| per metre
+    step = g / np.linalg.norm(g)
+    d = ora.energy(s, p, x0 + step, v0)[2] - ora.energy(s, p, x0, v0)[2]
+    assert abs(d + m.sum() * np.linalg.norm(g)) <= 1e-12
+
+
+def test_ground_energy_is_the_potential_of_the_penalty_force(ora):
+    """Reading R4's penalty k_c max(0, -z): a mass entering the ground at v0
+    with gravity off moves as z(t) = -(v0/w) sin(w t), v = -v0 cos(w t),
+    w = sqrt(k_c/m), while z < 0; kinetic + ground energy stays m v0^2/2.
+    Above the plane, and with contact off, the ground term is zero."""
+    m, kc, v0 = 3e-3, 2e4, 0.8
+    w = math.sqrt(kc / m)
+    s = dict(x=np.zeros((1, 3)), v=np.zeros((1, 3)), m=np.array([m]), fixed=np.zeros(1, np.uint8),
+             ij=np.zeros((0, 2), np.int32), k=np.zeros(0), c=np.zeros(0), L0=np.zeros(0))
+    p = synth.params(g=(0, 0, 0), k_c=kc, contact=True)
+    for t in np.linspace(0.01, 0.99, 9) * math.pi / w:
+        x = np.array([[0.3, -0.2, -(v0 / w) * math.sin(w * t)]])
+        v = np.array([[0.0, 0.0, -v0 * math.cos(w * t)]])
+        ke, pe, gpe, cpe = ora.energy(s, p, x, v)
+        assert cpe > 0
+        assert abs(ke + cpe - 0.5 * m * v0 * v0) <= 1e-14
+    assert ora.energy(s, p, np.array([[0, 0, 1e-3]]), np.zeros((1, 3)))[3] == 0.0
+    assert ora.energy(s, synth.params(g=(0, 0, 0), k_c=kc, contact=False),
+                      np.array([[0, 0, -1e-3]]), np.zeros((1, 3)))[3] == 0.0
+
+
+def test_resting_penetration_is_the_minimum_of_the_potential(ora):
+    """Gravity plus the ground penalty: the total potential of a resting mass
+    is stationary at the penetration the oracle's dynamics settle at,
+    z* = -m g / k_c (test_resting_penetration), and curves up with k_c.
+    A sign slip in either term, or a factor 2 in the ground term, moves the
+    stationary point away from z*."""
+    m, kc, g = 1e-3, 1e5, 9.81
+    s = dict(x=np.zeros((1, 3)), v=np.zeros((1, 3)), m=np.array([m]), fixed=np.zeros(1, np.uint8),
+             ij=np.zeros((0, 2), np.int32), k=np.zeros(0), c=np.zeros(0), L0=np.zeros(0))
+    p = synth.params(g=(0, 0, -g), k_c=kc, contact=True)
+    V = lambda z: sum(ora.energy(s, p, np.array([[0.0, 0.0, z]]), np.zeros((1, 3)))[2:])
+    zs, h = -m * g / kc, 1e-9
+    dV = (V(zs + h) - V(zs - h)) / (2 * h)
+    d2V = (V(zs + h) - 2 * V(zs) + V(zs - h)) / (h * h)
+    assert abs(dV) <= 1e-6 * m * g, dV
+    assert abs(d2V - kc) <= 1e-3 * kc, d2V
+
+
+# --------------------------------------------------------- threaded oracle
+def test_threaded_oracle_equals_the_serial_oracle_bit_for_bit(ora):
+    """The all-cores timing variant sums each mass's springs in the serial
+    order, so its states equal ora_run's exactly: an actuated, damped, anchored
+    lattice with ground contact and friction, on 1, 3 and 8 threads."""
+    s = random_lattice(seed=11)
+    s["fixed"] = (np.arange(s["x"].shape[0]) % 7 == 0).astype(np.uint8)
+    s["x"][:, 2] -= 0.004                      # part of it starts inside the ground
+    p = synth.params(dt=1e-4, k_c=1e4, mu=0.4, contact=True, vel_damping=1e-4)
+    xs, vs = ora.run(s, p, 300)
+    for T in (1, 3, 8):
+        xt, vt, used = ora.run_threads(s, p, 300, T)
+        assert 1 <= used <= T
+        assert np.array_equal(xt, xs) and np.array_equal(vt, vs), T
+
+
 # ------------------------------------------------------------- cantilever
 def _stiffness_matrix(s):
     """Linear-elastic stiffness of a spring network about its start geometry."""
