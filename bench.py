@@ -36,10 +36,15 @@ import synth  # noqa: E402
 METRIC = "element updates/s (springs+masses) & %HBM roofline; batched robot-sim-s/s"
 UNIT = "elements/s"
 FALLBACK_HBM_GBS = 6800.0
-# algorithmic bytes of one step (general-graph model): per mass read x, v
-# (24 B) + write x, v (24 B) + inverse mass (4 B); per spring i, j, k, L0 (16 B)
+# algorithmic bytes of one step: per mass read x, v (24 B) + write x, v
+# (24 B) + inverse mass (4 B); per spring, general-graph model G: i, j, k, L0
+# (16 B); lattice model L (topology and rest lengths from the grid): k (4 B).
+# A kernel is graded on the model its layout is entitled to.
 BYTES_PER_MASS = 52
-BYTES_PER_SPRING = 16
+BYTES_PER_SPRING = {"G": 16, "L": 4}
+KERNEL_NAMES = ["", "gather", "tiled", "persistent", "lattice"]
+STEP_KERNELS = {1: "k_step", 2: "k_step_tiled", 4: "k_step_lattice"}
+STEP_SOURCES = {1: "ms_step.cu", 2: "ms_step.cu", 4: "ms_lattice.cu"}
 
 
 def peaks():
@@ -173,64 +178,102 @@ def lattice_workload(n: int):
     return s, p
 
 
-def workload_config(n, N, S):
+def byte_model(kernel_id: int) -> str:
+    return "L" if kernel_id == 4 else "G"
+
+
+def workload_config(n, N, S, model="L"):
     return {"workload": f"lattice{n} ({n}^3 masses, 26-neighbourhood springs, k~U[5e3,5e4], c=0.05, "
                         f"anchored bottom layer, v~N(0,1e-3), dt=5e-5, gravity, no contact)",
             "n_masses": N, "n_springs": S, "elements_per_step": N + S,
-            "l2": "working set > L2 (no flush needed)", "byte_model": "G (52 B/mass + 16 B/spring)"}
+            "l2": "working set > L2 (no flush needed)",
+            "byte_model": f"{model} ({BYTES_PER_MASS} B/mass + {BYTES_PER_SPRING[model]} B/spring)"}
 
 
 # ------------------------------------------------------------------ oracle
-def oracle_sample(max_seconds: float = 15.0, side: int = 40):
-    """Time the FP64 oracle on a bounded sample of the workload: a side^3
-    lattice with the same parameters, as many steps as fit in max_seconds."""
+def host_threads() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def time_oracle(side: int, threads: int, max_seconds: float, max_steps: int = 10000, warmup: int = 0):
+    """Run the FP64 oracle on a side^3 lattice with the workload's parameters:
+    `warmup` untimed steps, then one timed call of as many steps as fit in
+    max_seconds (estimated from one calibration step), at most max_steps.
+    threads = 1 is the serial oracle (ora_run), more is its mass-partitioned
+    variant (ora_run_threads, bit-identical results).  Returns (elements/s,
+    steps, seconds, threads used, N, S)."""
     import oracle
     s, p = lattice_workload(side)
     ar = oracle._Arrays(s)
     x, v = s["x"], s["v"]
-    steps = 0
+    used = 1
+
+    def run(n0, n, x, v):
+        nonlocal used
+        if threads == 1:
+            return oracle.run(s, p, n, n0=n0, x=x, v=v, arrays=ar)
+        x, v, used = oracle.run_threads(s, p, n, threads, n0=n0, x=x, v=v, arrays=ar)
+        return x, v
+
+    n0 = 0
+    if warmup > 0:
+        x, v = run(n0, warmup, x, v)
+        n0 += warmup
+    steps = max_steps
+    if max_seconds < 1e8:
+        t0 = time.perf_counter()
+        x, v = run(n0, 1, x, v)
+        n0 += 1
+        steps = int(max(1, min(max_steps, max_seconds / max(time.perf_counter() - t0, 1e-6))))
     t0 = time.perf_counter()
-    while True:
-        x, v = oracle.run(s, p, 1, n0=steps, x=x, v=v, arrays=ar)
-        steps += 1
-        el = time.perf_counter() - t0
-        if el >= max_seconds or steps >= 10000:
-            break
+    x, v = run(n0, steps, x, v)
+    el = time.perf_counter() - t0
     N, S = s["x"].shape[0], s["ij"].shape[0]
-    return {"value": steps * (N + S) / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{side}^3 lattice with the workload's parameters, {steps} steps, {el:.1f} s, single thread FP64"}
+    return steps * (N + S) / el, steps, el, used, N, S
+
+
+def oracle_baseline(max_seconds: float = 15.0):
+    """cpu_baseline: the FP64 oracle on the host cores -- on every core the
+    process may use (a 64^3 sample) and, beside it, single-threaded (a 40^3
+    sample); about max_seconds in all."""
+    T = host_threads()
+    v_all, st_all, el_all, used, N64, S64 = time_oracle(64, T, max_seconds / 2)
+    v_one, st_one, el_one, _, N40, S40 = time_oracle(40, 1, max_seconds / 2)
+    return {"value": v_all, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"64^3 lattice ({N64} masses, {S64} springs) with the workload's parameters, {st_all} steps "
+                      f"in {el_all:.1f} s, FP64, {used} threads (masses partitioned, serial summation order)",
+            "host_cpus": T,
+            "single_thread": {"value": v_one, "unit": UNIT, "cores": 1,
+                              "sample": f"40^3 lattice ({N40} masses, {S40} springs), {st_one} steps in {el_one:.1f} s"}}
 
 
 def run_reference(args, world, rank):
-    """Reference arm: the FP64 oracle as it stands, single-threaded on the host,
-    one oracle step per bench step on a bounded sample (ref_side^3 lattice with
-    the workload's parameters)."""
+    """Reference arm: the FP64 oracle as it stands on the host cores (all the
+    process may use), one oracle step per bench step on a bounded sample of
+    the workload (a ref_side^3 lattice with the workload's parameters)."""
     if rank != 0:
         return 0
-    import oracle
     side = args.ref_side
-    s, p = lattice_workload(side)
-    ar = oracle._Arrays(s)
-    x, v = s["x"], s["v"]
-    for q in range(args.warmup):
-        x, v = oracle.run(s, p, 1, n0=q, x=x, v=v, arrays=ar)
-    t0 = time.perf_counter()
-    for q in range(args.steps):
-        x, v = oracle.run(s, p, 1, n0=args.warmup + q, x=x, v=v, arrays=ar)
-    el = time.perf_counter() - t0
-    Ns, Ss = s["x"].shape[0], s["ij"].shape[0]
-    val = (Ns + Ss) * args.steps / el
+    T = host_threads()
+    val, steps, el, used, Ns, Ss = time_oracle(side, T, max_seconds=1e9, max_steps=args.steps, warmup=args.warmup)
     n = args.n
     N = n ** 3
     S = synth.lattice_spring_count(n, n, n)
     sample = (f"{side}^3 lattice ({Ns} masses, {Ss} springs) with the workload's parameters, "
-              f"{args.steps} timed steps in {el:.2f} s, single-thread FP64; ms_per_step extrapolated to {n}^3")
+              f"{steps} timed steps in {el:.2f} s, FP64, {used} threads")
+    cfg = dict(workload_config(n, N, S), sample=f"each bench step = one oracle step of a {side}^3 sample "
+                                                   f"({Ns + Ss} elements)")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": (N + S) / val * 1e3, "higher_is_better": True, "scaling": "weak",
+            "steps": steps, "warmup": args.warmup,
+            "ms_per_step": el / steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
-            "config": workload_config(n, N, S),
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "config": cfg,
+            "extrapolated_ms_per_step_at_workload": (N + S) / val * 1e3,
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample,
+                             "host_cpus": T},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -314,24 +357,29 @@ def run_ours(args, world, rank, local):
                    "note": f"not measured: {err}"}
 
     hbm, hbm_kind = peaks()
-    alg_bytes = BYTES_PER_MASS * N + BYTES_PER_SPRING * S
+    model = byte_model(info["kernel"])
+    alg_bytes = BYTES_PER_MASS * N + BYTES_PER_SPRING[model] * S
     kern_ms = statistics.mean(per) / launches_per_step
     achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
-    kname = "k_step_tiled" if info["kernel"] == 2 else "k_step"
-    tr = kernel_traffic(os.path.join(ROOT, "paper_2207_09334_gb300", "csrc", "ms_step.cu"), kname) \
-        if args.integrator == "symplectic_euler" else None      # the capture is of the default scheme
+    kname = STEP_KERNELS.get(info["kernel"], "k_step")
+    tr = kernel_traffic(os.path.join(ROOT, "paper_2207_09334_gb300", "csrc", STEP_SOURCES.get(info["kernel"], "ms_step.cu")),
+                        kname) if args.integrator == "symplectic_euler" else None   # the capture is of the default scheme
     traffic = None
     if tr is not None:
         traffic = tr["dram_bytes_per_launch_at_256"] * (N + S) / tr["elements_at_256"] if n != 256 else tr["dram_bytes_per_launch_at_256"]
-    cpu = oracle_sample(max_seconds=args.cpu_seconds) if (rank == 0 and world == 1 and args.cpu_seconds > 0) else None
+    cpu = oracle_baseline(max_seconds=args.cpu_seconds) if (rank == 0 and world == 1 and args.cpu_seconds > 0) else None
 
     clocks = clk.summary()
+    batched = None
+    if args.batched and args.integrator == "symplectic_euler":
+        sim.close()                                  # free the lattice before the population is built
+        batched = measure_population(args, reps, local, args.sim_steps_per_bench_step, 1)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
-            "config": dict(workload_config(n, N, S), parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
+            "config": dict(workload_config(n, N, S, model), parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
                            setup_s={"generate": round(t_gen, 1), "create": round(t_create, 1)},
-                           mass_order=args.order, kernel=["", "gather", "tiled", "persistent"][info["kernel"]],
+                           mass_order=args.order, kernel=KERNEL_NAMES[info["kernel"]],
                            integrator=args.integrator,
                            device_bytes=info["device_bytes"], records=info["n_records"]),
             "e2e": e2e,
@@ -343,6 +391,8 @@ def run_ours(args, world, rank, local):
             "clocks": clocks}
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if batched is not None:
+        line["batched"] = batched                 # its own timed region and launch count
     if rank == 0:
         print(json.dumps(line), flush=True)
     sim.close()
@@ -351,13 +401,21 @@ def run_ours(args, world, rank, local):
 
 
 # ------------------------------------------------------------------ other workloads
-def run_population(args, world, rank, local):
-    """Batched voxel-robot population: robot-sim-seconds per second, batched
-    persistent launch vs the per-robot launch loop on the same GPU."""
+# algorithmic bytes of one population step: the robots' state stays in shared
+# memory for the whole launch, so a step reads only the merged spring records:
+# two robot-local endpoints (2 x 2 B), k, L0, the actuation pair (alpha, beta)
+# and c (5 x 4 B)
+POP_BYTES_PER_RECORD = 24
+
+
+def measure_population(args, reps, local, sim_steps, timed_launches, warm_launches=1):
+    """Batched voxel-robot population (4096 robots by default): robot-sim-s/s
+    of `timed_launches` persistent launches of `sim_steps` steps each (one
+    CUDA-graph replay per launch), a side record of 100-step launches, the
+    plain per-robot launch loop on a short sample, and the roofline of the
+    population kernel against POP_BYTES_PER_RECORD per merged spring and step."""
     import torch
     import paper_2207_09334_gb300 as ms
-    torch.cuda.set_device(local)
-    ms.load()
     designs = synth.voxel_population(args.robots, seed=2)
     p = synth.voxel_params()
     t0 = time.perf_counter()
@@ -365,52 +423,80 @@ def run_population(args, world, rank, local):
     pop.autotune(sample_steps=50)
     inf = pop.info()
     t_create = time.perf_counter() - t0
-    S = args.sim_steps_per_bench_step
     stream = torch.cuda.current_stream()
-    reps = Replicas(world)
-    for _ in range(args.warmup):
-        pop.run(S)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-    reps.barrier()
-    with Clocks(local) as clk:
+
+    def timed(nsteps, reps_n):
+        for _ in range(warm_launches):
+            pop.run(nsteps)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        reps.barrier()
         e0.record(stream)
-        for _ in range(args.steps):
-            pop.run(S)
+        for _ in range(reps_n):
+            pop.run(nsteps)
         e1.record(stream)
         torch.cuda.synchronize()
-    reps.barrier()
-    ms_total = e0.elapsed_time(e1)
-    sim_s = args.robots * S * p["dt"] * args.steps
+        reps.barrier()
+        return reps.max(e0.elapsed_time(e1))
+
+    with Clocks(local) as clk:
+        ms_total = timed(sim_steps, timed_launches)
+    sim_s = args.robots * sim_steps * p["dt"] * timed_launches
     value = reps.throughput(sim_s, ms_total * 1e-3)
-    ms_total = reps.max(ms_total)
-    el_per_step = inf["n_masses"] + inf["n_records"]
+    ms_100 = timed(100, 5)
+    value_100 = reps.throughput(args.robots * 100 * p["dt"] * 5, ms_100 * 1e-3)
     # the plain per-robot loop on a short sample of steps
     L = args.loop_steps
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     pop.run_loop(L)
     torch.cuda.synchronize()
-    loop_s = time.perf_counter() - t0
-    loop_value = args.robots * L * p["dt"] / loop_s
+    loop_s = reps.max(time.perf_counter() - t0)
+    loop_value = reps.world * args.robots * L * p["dt"] / loop_s
     travel = pop.com_travel()
-    line = {"metric": "batched robot-sim-s/s", "value": value, "unit": "robot-sim-s/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+    steps_per_s = sim_steps * timed_launches / (ms_total * 1e-3)
+    hbm, hbm_kind = peaks()
+    achieved = POP_BYTES_PER_RECORD * inf["n_records"] * steps_per_s / 1e9
+    rec = {"value": value, "unit": "robot-sim-s/s", "ms_per_launch": ms_total / timed_launches,
+           "sim_steps_per_launch": sim_steps, "launches": timed_launches,
+           "config": {"workload": f"population of {args.robots} voxel robots (sides U{{3..12}}, seed 2), "
+                                  f"{sim_steps} simulated steps (dt = 1e-4) per persistent launch",
+                      "n_masses": inf["n_masses"], "n_springs_merged": inf["n_records"],
+                      "block_robots": inf["n_block_items"], "warp_robots": inf["n_warp_items"],
+                      "setup_s": round(t_create, 1)},
+           "elements_per_s": (inf["n_masses"] + inf["n_records"]) * steps_per_s * reps.world,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                        "traffic": None, "kernel": "k_batch", "peak_kind": f"{hbm_kind} (hbm_gbs)",
+                        "algorithmic_bytes_per_step": POP_BYTES_PER_RECORD * inf["n_records"],
+                        "byte_model": f"{POP_BYTES_PER_RECORD} B per merged spring per step (state in shared memory)"},
+           "launches_of_100_steps": {"value": value_100, "unit": "robot-sim-s/s", "ms_per_launch": ms_100 / 5},
+           "per_robot_loop": {"value": loop_value, "unit": "robot-sim-s/s", "sim_steps": L,
+                              "speedup_of_batched": value / loop_value},
+           "travel_mean_m": float(np.mean(travel)), "clocks": clk.summary(),
+           "gpu_launches": 3 * timed_launches}
+    pop.close()
+    return rec
+
+
+def run_population(args, world, rank, local):
+    """Batched voxel-robot population: robot-sim-seconds per second, one bench
+    step = one persistent launch of --sim-steps-per-bench-step (5000) steps."""
+    import torch
+    import paper_2207_09334_gb300 as ms
+    torch.cuda.set_device(local)
+    ms.load()
+    reps = Replicas(world)
+    S = args.sim_steps_per_bench_step
+    rec = measure_population(args, reps, local, S, args.steps, warm_launches=max(1, min(args.warmup, 3)))
+    line = {"metric": "batched robot-sim-s/s", "value": rec["value"], "unit": "robot-sim-s/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["ms_per_launch"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic (seeded)",
-            "config": {"workload": f"population of {args.robots} voxel robots (sides U{{3..12}}, seed 2), "
-                                   f"one bench step = {S} simulated steps (dt = 1e-4) in one persistent launch",
-                       "n_masses": inf["n_masses"], "n_springs_merged": inf["n_records"],
-                       "block_robots": inf["n_block_items"], "warp_robots": inf["n_warp_items"],
-                       "setup_s": round(t_create, 1)},
-            "elements_per_s": world * el_per_step * S * args.steps / (ms_total * 1e-3),
-            "per_robot_loop": {"value": loop_value, "unit": "robot-sim-s/s", "sim_steps": L,
-                               "speedup_of_batched": value / loop_value},
-            "gpu_launches": 3 * args.steps, "clocks": clk.summary(),
-            "travel_mean_m": float(np.mean(travel))}
+            "data": "synthetic (seeded)", "config": rec["config"], "elements_per_s": rec["elements_per_s"],
+            "roofline": rec["roofline"], "launches_of_100_steps": rec["launches_of_100_steps"],
+            "per_robot_loop": rec["per_robot_loop"], "gpu_launches": rec["gpu_launches"], "clocks": rec["clocks"],
+            "travel_mean_m": rec["travel_mean_m"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    pop.close()
     reps.close()
     return 0
 
@@ -512,14 +598,16 @@ def run_screen(args, world, rank, local):
     side, nsteps = 8, 20000                        # 2 s rollouts at dt = 1e-4
     n_train, n_val, n_cand = args.train_designs, 2048, args.candidates
     sim_args = (synth.VOXEL_MATERIALS, synth.VOXEL_FREQ, synth.VOXEL_EDGE, synth.VOXEL_MASS, synth.voxel_params())
-    mats = rng.integers(0, 4, size=(n_train + n_val, side, side, side)).astype(np.uint8)
+    # random materials kept to each design's largest face-connected body, so
+    # that loose voxels are not simulated (and labelled) as separate bodies
+    mats = synth.largest_components(rng.integers(0, 4, size=(n_train + n_val, side, side, side)).astype(np.uint8))
     t0 = time.perf_counter()
     y = screen.simulate_travel(mats, *sim_args, nsteps=nsteps)
     t_label = time.perf_counter() - t0
     t0 = time.perf_counter()
     net, mu, sd = screen.train(mats[:n_train], y[:n_train], epochs=10, batch=1024, lr=1e-3, seed=0)
     t_train = time.perf_counter() - t0
-    cand = rng.integers(0, 4, size=(n_cand, side, side, side)).astype(np.uint8)
+    cand = synth.largest_components(rng.integers(0, 4, size=(n_cand, side, side, side)).astype(np.uint8))
     with net:
         pv = screen.predict(net, mats[n_train:], mu, sd)
         torch.cuda.synchronize()
@@ -633,7 +721,7 @@ def run_sweep(args, world, rank, local):
                 torch.cuda.synchronize()
                 reps.barrier()
                 t = e0.elapsed_time(e1) * 1e-3
-                rows.append({"n": n, "masses": N, "springs": S, "kernel": ["", "gather", "tiled", "persistent"][sim.info()["kernel"]],
+                rows.append({"n": n, "masses": N, "springs": S, "kernel": KERNEL_NAMES[sim.info()["kernel"]],
                              "steps": steps, "us_per_step": reps.max(t) * 1e6 / steps,
                              "elements_per_s": reps.throughput((N + S) * steps, t)})
     best = max(r["elements_per_s"] for r in rows)
@@ -708,15 +796,14 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=256, help="lattice side (256 = the benchmark workload)")
     ap.add_argument("--order", default="auto", choices=["auto", "morton", "caller"], help="internal mass order")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "gather", "tiled"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "gather", "tiled", "lattice"])
     ap.add_argument("--integrator", default="symplectic_euler",
                     choices=["symplectic_euler", "forward_euler", "verlet", "rk4"],
                     help="lattice workload: step scheme (rk4 = 4 stage launches per step)")
     ap.add_argument("--e2e-sim-steps", type=int, default=200)
     ap.add_argument("--e2e-iters", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-seconds", type=float, default=10.0)
-    ap.add_argument("--ref-side", type=int, default=40)
+    ap.add_argument("--ref-side", type=int, default=64, help="reference arm: side of the sampled lattice")
     ap.add_argument("--workload", default="lattice",
                     choices=["lattice", "population", "surrogate", "adjoint", "screen", "cube", "sweep"])
     ap.add_argument("--cube-steps", type=int, default=10000, help="cube workload: steps per kernel")
@@ -726,7 +813,10 @@ def main():
     ap.add_argument("--walkers", type=int, default=256)
     ap.add_argument("--rollout-steps", type=int, default=2000)
     ap.add_argument("--robots", type=int, default=4096)
-    ap.add_argument("--sim-steps-per-bench-step", type=int, default=100)
+    ap.add_argument("--sim-steps-per-bench-step", type=int, default=5000,
+                    help="population workload: simulated steps per persistent launch (one bench step)")
+    ap.add_argument("--batched", type=int, default=1,
+                    help="lattice workload: add the population's batched record (one 5000-step launch)")
     ap.add_argument("--loop-steps", type=int, default=5)
     ap.add_argument("--candidates", type=int, default=1 << 20)
     ap.add_argument("--screen-batch", type=int, default=65536, help="designs per surrogate forward pass")

@@ -69,8 +69,9 @@ typedef struct {
     int32_t reorder;        /* mass order: 0 = library default (Morton for the tiled kernel, caller
                                order for the gather kernel), 1 = Morton order by initial position,
                                2 = caller order */
-    int32_t kernel;         /* 0 = library default: tiled (gather when a tile's partners do not fit
-                               shared memory); 1 = gather, 2 = tiled (MS_ERR_ARG if a tile does not fit),
+    int32_t kernel;         /* 0 = library default: lattice (4) for a box lattice of at least 2^18
+                               masses, else tiled (gather when a tile's partners do not fit shared
+                               memory); 1 = gather, 2 = tiled (MS_ERR_ARG if a tile does not fit),
                                3 = persistent: all steps of one ms_step call in one launch.  Up to
                                8192 masses: a thread-block cluster (at most 16 CTAs, one per tile
                                of 64 to 512 masses) with the state and the spring records in
@@ -81,7 +82,15 @@ typedef struct {
                                MS_ERR_ARG when the system has more tiles than multiprocessors,
                                when the records do not fit shared memory, or with an integrator
                                other than symplectic Euler; ms_set_actuation returns MS_ERR_ARG
-                               when the actuation coefficients do not fit as well */
+                               when the actuation coefficients do not fit as well.
+                               4 = lattice: masses on the points of a cubic grid (spacing = the
+                               shortest spring), springs only between grid neighbours of the
+                               26-neighbourhood and at most one per pair, one rest length per
+                               lattice direction, one dashpot value; topology and rest lengths
+                               then come from the grid and only k is stored per spring (the
+                               paper's cubic and voxel lattices, "Generating a Lattice").
+                               MS_ERR_ARG (with the reason) for any other network; no actuation
+                               (ms_set_actuation returns MS_ERR_ARG) */
 } ms_params;
 
 /* Optional device allocator (e.g. a framework's caching allocator).
@@ -99,16 +108,16 @@ typedef struct {
     int64_t n_masses;          /* N */
     int64_t n_springs;         /* caller springs S */
     int64_t n_records;         /* springs after merging parallel springs (same pair) */
-    int64_t n_slots;           /* padded forward record slots (>= n_records) */
+    int64_t n_slots;           /* padded forward record slots (>= n_records); lattice: 13 x padded cells */
     int64_t n_back_slots;      /* padded back-reference slots */
     int64_t device_bytes;      /* device memory held */
     int64_t step_count;        /* steps taken since creation */
     double stability_bound;    /* dt^2 * max_i (2 sum_{springs at i} k + k_c) / m_i  (Gershgorin; stable if < 4) */
     int32_t max_fwd_degree;    /* gather: most springs owned by one mass; tiled: most springs of one mass */
     int32_t max_back_degree;
-    int32_t kernel;            /* 1 = gather, 2 = tiled, 3 = persistent */
-    int32_t n_tiles;
-    int32_t max_tile_local;    /* tiled: largest members + halo of a tile */
+    int32_t kernel;            /* 1 = gather, 2 = tiled, 3 = persistent, 4 = lattice */
+    int32_t n_tiles;           /* tiled: tiles; lattice: bricks of 16 x 8 x 4 cells */
+    int32_t max_tile_local;    /* tiled: largest members + halo of a tile; lattice: cells staged per brick */
 } ms_info_t;
 
 /*
@@ -148,6 +157,32 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
                     void *stream, ms_sim **out);
 
 /*
+ * ms_create_materials -- ms_create with springs described by material
+ * (paper: "Generating a Lattice" final paragraph -- physical material
+ * properties derive the spring constants and mass values; Fig. 2 -- robots
+ * built from soft, stiff and actuated materials).  Every argument not listed
+ * here is as for ms_create.
+ *   mat          (S) material id of each spring, in [0, n_mat).
+ *   n_mat        entries of the tables, 1 <= n_mat <= 65536.
+ *   mat_k        (n_mat) stiffness [N/m] >= 0.
+ *   mat_c        (n_mat) axial dashpot [N s/m] >= 0, or NULL = 0.
+ *   mat_L0scale  (n_mat) rest-length factor >= 0, or NULL = 1: spring s rests
+ *                at base_s * mat_L0scale[mat[s]] (one FP32 rounding), base_s =
+ *                rest_len[s], or the initial distance when rest_len is NULL
+ *                (computed as ms_create computes it).
+ * The tables are expanded on the host into ms_create's per-spring arrays, so
+ * the object equals, bit for bit, one made by ms_create from those arrays.
+ * Errors: MS_ERR_ARG for an id out of range or a bad table entry, otherwise
+ * those of ms_create.
+ */
+ms_status ms_create_materials(const ms_params *p, int32_t N, const float *x0, const float *v0,
+                              const float *mass, const uint8_t *fixed, const float *fext,
+                              int64_t S, const int32_t *ij, const uint16_t *mat, int32_t n_mat,
+                              const float *mat_k, const float *mat_c, const float *mat_L0scale,
+                              const float *rest_len, const ms_allocator *alloc, void *stream,
+                              ms_sim **out);
+
+/*
  * ms_set_actuation -- actuated rest lengths (paper: Introduction and
  * Applications -- self-actuation by dynamically modifying volumetric
  * properties; Fig. 2 caption -- springs individually actuated).  Spring s
@@ -168,7 +203,9 @@ ms_status ms_step(ms_sim *sim, int32_t nsteps);
 
 /*
  * ms_get_state / ms_set_state -- copy positions and velocities ((N,3) float32,
- * caller order) out of / into the object.  on_device = 1: x and v are device
+ * caller order) out of / into the object (paper: "GPU Implementation" --
+ * syncing the state from GPU to CPU and back; a saved state restores a run,
+ * i.e. checkpoint and resume).  on_device = 1: x and v are device
  * pointers (stream-ordered, asynchronous); 0: host pointers (the call
  * synchronises the stream; page-locked memory gives the fastest copies).
  * Either pointer may be NULL to skip it.  ms_get_state to host also reports
@@ -240,16 +277,22 @@ ms_status ms_energy(ms_sim *sim, double *out, int32_t on_device);
 ms_status ms_trace_set(ms_sim *sim, const int32_t *masses, int32_t n_masses, int32_t capacity);
 ms_status ms_trace_get(ms_sim *sim, float *out, int32_t *n_steps, int32_t on_device);
 
-/* ms_get_info -- sizes and diagnostics of the object. */
+/* ms_get_info -- sizes and diagnostics of the object's device layout
+ * (paper: "GPU Implementation" -- springs and masses stored consecutively,
+ * with the springs attached to each mass stored on the mass). */
 ms_status ms_get_info(const ms_sim *sim, ms_info_t *out);
 
-/* ms_destroy -- free all memory held by the object (after its stream's work). NULL is a no-op. */
+/* ms_destroy -- free all memory held by the object (after its stream's work);
+ * the end of the lifetime that ms_create starts (paper: "Generating a
+ * Lattice" -- the lattice is copied to GPU memory to initialise a run).
+ * NULL is a no-op. */
 ms_status ms_destroy(ms_sim *sim);
 
-/* Message of the calling thread's last error (static storage, never NULL). */
+/* Message of the calling thread's last error (static storage, never NULL).
+ * ABI plumbing; the paper has no counterpart. */
 const char *ms_last_error(void);
 
-/* Library version string. */
+/* Library version string (ABI plumbing; the paper has no counterpart). */
 const char *ms_version(void);
 
 

@@ -62,6 +62,8 @@ I32, I64, F32 = C.c_int32, C.c_int64, C.c_float
 SIGNATURES = {
     "ms_create": (C.c_int, [C.POINTER(MsParams), I32, VP, VP, VP, VP, VP, I64, VP, VP, VP, F32, VP,
                             C.POINTER(MsAllocator), VP, C.POINTER(VP)]),
+    "ms_create_materials": (C.c_int, [C.POINTER(MsParams), I32, VP, VP, VP, VP, VP, I64, VP, VP, I32, VP, VP,
+                                      VP, VP, C.POINTER(MsAllocator), VP, C.POINTER(VP)]),
     "ms_set_actuation": (C.c_int, [VP, F32, VP, VP]),
     "ms_step": (C.c_int, [VP, I32]),
     "ms_get_state": (C.c_int, [VP, VP, VP, I32]),

@@ -65,7 +65,7 @@ def build(verbose: bool = False, extra_flags: list[str] | None = None) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(8, max(1, len(srcs)))) as ex:
         objs = list(ex.map(compile_one, srcs))
     if _stale(LIB, objs):
-        cmd = [exe] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs + ["-lcuda"] * 0
+        cmd = [exe] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

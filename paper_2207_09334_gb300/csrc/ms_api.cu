@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <mutex>
 #include <new>
 #include <string>
@@ -112,7 +113,10 @@ struct ms_sim {
     uint16_t *t_nbr = nullptr;
     int4 *tiles = nullptr;
     int32_t *halo = nullptr;
-    int32_t *d_perm = nullptr;
+    int32_t *d_perm = nullptr;          // internal -> caller index (layouts indexed 0..N-1)
+    int32_t *d_cidx = nullptr;          // caller -> internal index (the lattice layout)
+    ms::LatticeArgs lat{};              // lattice layout (kernel 4): stiffness arrays, rest lengths, extents
+    int64_t lat_cells = 0;              // padded cells of the lattice layout
     float *stage = nullptr;             // (N,3)*2 floats for host copies
     int *err = nullptr;
     float c_uniform = 0.f;
@@ -198,6 +202,202 @@ uint64_t spread3(uint64_t v)
 
 bool finite3(const float *p) { return std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]); }
 
+// ---------------------------------------------------------------------------
+// Lattice layout (kernel 4; see ms_internal.h).  lattice_shape checks, on the
+// host and without allocating device memory, that the network is a box
+// lattice of that form, and fills its arrays; build_lattice uploads them.
+// ---------------------------------------------------------------------------
+constexpr int32_t kLatticeAutoMin = 1 << 18;   // default kernel: lattice layout from 64^3 masses up
+
+struct LatticeShape {
+    int nx = 0, ny = 0, nz = 0, nbx = 0, nby = 0, nbz = 0, X = 0, Y = 0, Z = 0;
+    int64_t P = 0;                    // padded cells
+    std::vector<int32_t> cidx;        // caller mass -> padded index
+    std::vector<float> kf;            // [13][P] stiffness, -1 = no spring
+    float L[ms::kLatDirs] = {};
+    float c = 0.f;
+    std::vector<double> sumK;         // per caller mass: sum of the k of its springs
+};
+
+bool lattice_shape(int32_t N, const float *x0, int64_t S, const int32_t *ij, const float *k, const float *c,
+                   float c_uniform, const float *rest_len, LatticeShape &L, std::string &why)
+{
+    if (S == 0) { why = "no springs"; return false; }
+    // lattice spacing: the shortest spring
+    double h = 0.0;
+    for (int64_t e = 0; e < S; ++e) {
+        const int32_t a = ij[2 * e], b = ij[2 * e + 1];
+        const double dx = (double)x0[3 * b] - x0[3 * a], dy = (double)x0[3 * b + 1] - x0[3 * a + 1],
+                     dz = (double)x0[3 * b + 2] - x0[3 * a + 2];
+        const double l = std::sqrt(dx * dx + dy * dy + dz * dz);
+        if (!(l > 0.0)) { why = "a spring of zero length"; return false; }
+        if (h == 0.0 || l < h) h = l;
+    }
+    double lo[3] = {x0[0], x0[1], x0[2]}, hi[3] = {x0[0], x0[1], x0[2]};
+    for (int32_t i = 0; i < N; ++i)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], (double)x0[3 * i + a]);
+            hi[a] = std::max(hi[a], (double)x0[3 * i + a]);
+        }
+    // every mass on a grid point: cell indices from the shortest spring, then
+    // the spacing of each axis from its extent (the shortest spring carries
+    // the FP32 rounding of its endpoints, which would add up over many cells)
+    std::vector<int32_t> cell(3 * (size_t)N);
+    int64_t ext[3] = {0, 0, 0};
+    for (int32_t i = 0; i < N; ++i)
+        for (int a = 0; a < 3; ++a) {
+            const double q = ((double)x0[3 * i + a] - lo[a]) / h;
+            const double r = std::nearbyint(q);
+            if (std::fabs(q - r) > 0.25 || r > 1048575.0) { why = "masses are not on a cubic grid"; return false; }
+            cell[3 * (size_t)i + a] = (int32_t)r;
+            ext[a] = std::max<int64_t>(ext[a], (int64_t)r + 1);
+        }
+    for (int a = 0; a < 3; ++a) {
+        const double ha = ext[a] > 1 ? (hi[a] - lo[a]) / (double)(ext[a] - 1) : h;
+        for (int32_t i = 0; i < N; ++i)
+            if (std::fabs(((double)x0[3 * i + a] - lo[a]) / ha - cell[3 * (size_t)i + a]) > 1e-2) {
+                why = "masses are not on a cubic grid";
+                return false;
+            }
+    }
+    if (ext[0] * ext[1] * ext[2] > 8 * (int64_t)N + 4096) { why = "the grid is mostly empty"; return false; }
+    L.nx = (int)ext[0]; L.ny = (int)ext[1]; L.nz = (int)ext[2];
+    L.nbx = (L.nx + ms::kBrickX - 1) / ms::kBrickX;
+    L.nby = (L.ny + ms::kBrickY - 1) / ms::kBrickY;
+    L.nbz = (L.nz + ms::kBrickZ - 1) / ms::kBrickZ;
+    L.X = L.nbx * ms::kBrickX + 2; L.Y = L.nby * ms::kBrickY + 2; L.Z = L.nbz * ms::kBrickZ + 2;
+    L.P = (int64_t)L.X * L.Y * L.Z;
+    if (L.P >= (int64_t)INT32_MAX / 2) { why = "the padded lattice is too large for 32-bit cell indices"; return false; }
+    const int64_t XY = (int64_t)L.X * L.Y;
+    L.cidx.resize(N);
+    {
+        std::vector<uint8_t> used((size_t)L.P, 0);
+        for (int32_t i = 0; i < N; ++i) {
+            const int64_t ci = (cell[3 * (size_t)i] + 1) + L.X * (int64_t)(cell[3 * (size_t)i + 1] + 1) +
+                               XY * (cell[3 * (size_t)i + 2] + 1);
+            if (used[ci]) { why = "two masses on one grid point"; return false; }
+            used[ci] = 1;
+            L.cidx[i] = (int32_t)ci;
+        }
+    }
+    // springs: neighbouring cells, one per pair, one rest length per direction, one dashpot value
+    L.c = c ? c[0] : c_uniform;
+    bool have_L[ms::kLatDirs] = {};
+    L.kf.assign((size_t)ms::kLatDirs * (size_t)L.P, -1.0f);
+    L.sumK.assign(N, 0.0);
+    for (int64_t e = 0; e < S; ++e) {
+        int32_t a = ij[2 * e], b = ij[2 * e + 1];
+        int dd[3];
+        for (int q = 0; q < 3; ++q) dd[q] = cell[3 * (size_t)b + q] - cell[3 * (size_t)a + q];
+        if (std::abs(dd[0]) > 1 || std::abs(dd[1]) > 1 || std::abs(dd[2]) > 1) {
+            why = "spring " + std::to_string(e) + " joins masses that are not lattice neighbours";
+            return false;
+        }
+        const bool fwd = dd[2] > 0 || (dd[2] == 0 && (dd[1] > 0 || (dd[1] == 0 && dd[0] > 0)));
+        if (!fwd) { std::swap(a, b); for (int q = 0; q < 3; ++q) dd[q] = -dd[q]; }
+        const int d = dd[2] == 0 ? (dd[1] == 0 ? 0 : dd[0] + 2) : 4 + (dd[0] + 1) + 3 * (dd[1] + 1);
+        float Lv;
+        if (rest_len) Lv = rest_len[e];
+        else {
+            const double dx = (double)x0[3 * b] - x0[3 * a], dy = (double)x0[3 * b + 1] - x0[3 * a + 1],
+                         dz = (double)x0[3 * b + 2] - x0[3 * a + 2];
+            Lv = (float)std::sqrt(dx * dx + dy * dy + dz * dz);
+        }
+        if (!have_L[d]) { L.L[d] = Lv; have_L[d] = true; }
+        else if (L.L[d] != Lv) { why = "rest lengths differ within one lattice direction"; return false; }
+        if (c && c[e] != L.c) { why = "the dashpot coefficient differs between springs"; return false; }
+        float &slot = L.kf[(size_t)d * (size_t)L.P + (size_t)L.cidx[a]];
+        if (slot >= 0.0f) { why = "two springs join the same pair of masses"; return false; }
+        slot = k[e];
+        L.sumK[a] += k[e]; L.sumK[b] += k[e];
+    }
+    return true;
+}
+
+}  // namespace
+
+namespace {
+
+// Upload the lattice layout into s (after lattice_shape succeeded).
+ms_status build_lattice(ms_sim *s, const ms_params *p, int32_t N, const float *x0, const float *v0,
+                        const float *mass, const uint8_t *fixed, const float *fext, LatticeShape &L)
+{
+    const size_t P = (size_t)L.P;
+    s->kernel = ms::kKernelLattice;
+    s->lat_cells = L.P;
+    s->n_tiles = L.nbx * L.nby * L.nbz;
+    s->max_tile_local = ms::kHaloCells;
+    s->n_records = s->S;
+    s->n_slots = (int64_t)ms::kLatDirs * L.P;
+    s->iperm = L.cidx;
+    s->perm.clear();
+    s->permuted = true;
+    // state of the padded cells: zero, w = NaN where there is no mass
+    std::vector<float4> ha(P, make_float4(0.f, 0.f, 0.f, 0.f));
+    std::vector<float2> hb(P, make_float2(0.f, 0.f));
+    std::vector<float> hw(P, std::numeric_limits<float>::quiet_NaN());
+    std::vector<float4> hf;
+    if (fext) hf.assign(P, make_float4(0.f, 0.f, 0.f, 0.f));
+    double bound = 0.0;
+    const double dt2 = (double)p->dt * p->dt;
+    for (int32_t m = 0; m < N; ++m) {
+        const size_t i = (size_t)L.cidx[m];
+        const bool anchored = fixed && fixed[m];
+        hw[i] = !anchored ? (float)(1.0 / (double)mass[m])
+                : (mass[m] > 0.f && std::isfinite(mass[m])) ? -mass[m] : -FLT_MIN;
+        ha[i] = make_float4(x0[3 * m], x0[3 * m + 1], x0[3 * m + 2], anchored ? 0.f : v0[3 * m]);
+        hb[i] = anchored ? make_float2(0.f, 0.f) : make_float2(v0[3 * m + 1], v0[3 * m + 2]);
+        if (fext) hf[i] = make_float4(fext[3 * m], fext[3 * m + 1], fext[3 * m + 2], 0.f);
+        if (!anchored) bound = std::max(bound, dt2 * (2.0 * L.sumK[m] + (p->contact_on ? p->k_c : 0.0)) / mass[m]);
+    }
+    s->stability = bound;
+    if (p->strict_stability && bound >= 4.0) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "stability bound dt^2*max(2 sum k + k_c)/m = %.3g >= 4", bound);
+        return fail(MS_ERR_UNSTABLE, buf);
+    }
+    ms_status st;
+    for (int q = 0; q < 2; ++q) {
+        if ((st = upload(s, &s->sa[q], ha.data(), P)) != MS_OK) return st;
+        if ((st = upload(s, &s->sb[q], hb.data(), P)) != MS_OK) return st;
+    }
+    if ((st = upload(s, &s->w, hw.data(), P)) != MS_OK) return st;
+    if (fext && (st = upload(s, &s->fext, hf.data(), P)) != MS_OK) return st;
+    float *kdev = nullptr;
+    if ((st = upload(s, &kdev, L.kf.data(), L.kf.size())) != MS_OK) return st;
+    const int64_t XY = (int64_t)L.X * L.Y;
+    for (int d = 0; d < ms::kLatDirs; ++d) {
+        s->lat.kf[d] = kdev + (size_t)d * P;
+        // kb[d][i] = kf[d][i - off(d)] for every cell with a mass (whose
+        // backward neighbours lie in the padded array); formed as an address
+        const int64_t off = ms::lat_dx(d) + (int64_t)L.X * ms::lat_dy(d) + XY * ms::lat_dz(d);
+        s->lat.kb[d] = reinterpret_cast<const float *>(reinterpret_cast<uintptr_t>(s->lat.kf[d]) -
+                                                       (uintptr_t)(off * (int64_t)sizeof(float)));
+        s->lat.L[d] = L.L[d];
+    }
+    s->lat.c = L.c;
+    s->lat.X = L.X; s->lat.Y = L.Y; s->lat.Z = L.Z;
+    s->lat.nbx = L.nbx; s->lat.nby = L.nby; s->lat.nbz = L.nbz;
+    if ((st = upload(s, &s->d_cidx, L.cidx.data(), (size_t)N)) != MS_OK) return st;
+    if ((st = upload<float>(s, &s->stage, nullptr, (size_t)N * 6)) != MS_OK) return st;
+    if (p->integrator == 3) {
+        for (int q = 0; q < 2; ++q) {
+            if ((st = upload<float4>(s, &s->rk_a[q], nullptr, P)) != MS_OK) return st;
+            if ((st = upload<float2>(s, &s->rk_b[q], nullptr, P)) != MS_OK) return st;
+        }
+        if ((st = upload<float4>(s, &s->rk_acc, nullptr, 2 * P)) != MS_OK) return st;
+    }
+    {
+        int dev = 0;
+        MS_CUDA_TRY(cudaGetDevice(&dev));
+        MS_CUDA_TRY(cudaDeviceGetAttribute(&s->n_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    if ((st = upload<int>(s, &s->err, nullptr, 2)) != MS_OK) return st;
+    MS_CUDA_TRY(cudaMemsetAsync(s->err, 0, 2 * sizeof(int), s->stream));
+    MS_CUDA_TRY(cudaStreamSynchronize(s->stream));      // host arrays must outlive the copies
+    return MS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -233,6 +433,15 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
         if (fext && !finite3(fext + 3 * i)) return fail(MS_ERR_ARG, "non-finite external force at mass " + std::to_string(i));
     }
 
+    for (int64_t e = 0; e < S; ++e) {
+        const int32_t a = ij[2 * e], b = ij[2 * e + 1];
+        if (a < 0 || a >= N || b < 0 || b >= N) return fail(MS_ERR_ARG, "spring endpoint out of range at spring " + std::to_string(e));
+        if (a == b) return fail(MS_ERR_ARG, "spring joins a mass to itself at spring " + std::to_string(e));
+        if (!(k[e] >= 0.f && std::isfinite(k[e]))) return fail(MS_ERR_ARG, "k must be >= 0 and finite at spring " + std::to_string(e));
+        if (c && !(c[e] >= 0.f && std::isfinite(c[e]))) return fail(MS_ERR_ARG, "c must be >= 0 and finite at spring " + std::to_string(e));
+        if (rest_len && !(rest_len[e] >= 0.f && std::isfinite(rest_len[e]))) return fail(MS_ERR_ARG, "rest length must be >= 0 and finite at spring " + std::to_string(e));
+    }
+
     ms_sim *s = new (std::nothrow) ms_sim();
     if (!s) return fail(MS_ERR_OOM, "host allocation failed");
     struct Guard { ms_sim *s; ~Guard() { if (s) { s->release(); delete s; } } } guard{s};
@@ -241,7 +450,20 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
     if (alloc) { s->alloc = *alloc; s->custom_alloc = true; }
     s->c_uniform = c_uniform;
 
-    if (p->kernel < 0 || p->kernel > 3 || p->reorder < 0 || p->reorder > 2) return fail(MS_ERR_ARG, "kernel must be 0..3 and reorder 0..2");
+    if (p->kernel < 0 || p->kernel > 4 || p->reorder < 0 || p->reorder > 2) return fail(MS_ERR_ARG, "kernel must be 0..4 and reorder 0..2");
+    // lattice layout: when asked for, or by default for a large box lattice
+    if (p->kernel == ms::kKernelLattice || (p->kernel == 0 && N >= kLatticeAutoMin)) {
+        LatticeShape L;
+        std::string why;
+        if (lattice_shape(N, x0, S, ij, k, c, c_uniform, rest_len, L, why)) {
+            ms_status st = build_lattice(s, p, N, x0, v0, mass, fixed, fext, L);
+            if (st != MS_OK) return st;
+            guard.s = nullptr;
+            *out = s;
+            return MS_OK;
+        }
+        if (p->kernel == ms::kKernelLattice) return fail(MS_ERR_ARG, "not a lattice for the lattice kernel: " + why);
+    }
     if (p->kernel == 3 && p->integrator != 0)
         return fail(MS_ERR_ARG, "the persistent kernel integrates with symplectic Euler only");
     // persistent: up to kClusterMax x kClMassesMax masses one thread-block
@@ -295,11 +517,6 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
     std::vector<int64_t> row(N + 1, 0);
     for (int64_t e = 0; e < S; ++e) {
         const int32_t a = ij[2 * e], b = ij[2 * e + 1];
-        if (a < 0 || a >= N || b < 0 || b >= N) return fail(MS_ERR_ARG, "spring endpoint out of range at spring " + std::to_string(e));
-        if (a == b) return fail(MS_ERR_ARG, "spring joins a mass to itself at spring " + std::to_string(e));
-        if (!(k[e] >= 0.f && std::isfinite(k[e]))) return fail(MS_ERR_ARG, "k must be >= 0 and finite at spring " + std::to_string(e));
-        if (c && !(c[e] >= 0.f && std::isfinite(c[e]))) return fail(MS_ERR_ARG, "c must be >= 0 and finite at spring " + std::to_string(e));
-        if (rest_len && !(rest_len[e] >= 0.f && std::isfinite(rest_len[e]))) return fail(MS_ERR_ARG, "rest length must be >= 0 and finite at spring " + std::to_string(e));
         row[std::min(s->iperm[a], s->iperm[b]) + 1]++;
     }
     for (int32_t i = 0; i < N; ++i) row[i + 1] += row[i];
@@ -705,12 +922,65 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
     return MS_OK;
 }
 
+ms_status ms_create_materials(const ms_params *p, int32_t N, const float *x0, const float *v0, const float *mass,
+                              const uint8_t *fixed, const float *fext, int64_t S, const int32_t *ij,
+                              const uint16_t *mat, int32_t n_mat, const float *mat_k, const float *mat_c,
+                              const float *mat_L0scale, const float *rest_len, const ms_allocator *alloc,
+                              void *stream, ms_sim **out)
+{
+    if (!out) return fail(MS_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!x0) return fail(MS_ERR_ARG, "x0 is required");
+    if (S < 0 || (S > 0 && (!ij || !mat))) return fail(MS_ERR_ARG, "S < 0, or ij / mat missing");
+    if (n_mat < 1 || n_mat > 65536 || !mat_k) return fail(MS_ERR_ARG, "need 1 <= n_mat <= 65536 and mat_k");
+    for (int32_t q = 0; q < n_mat; ++q) {
+        if (!(mat_k[q] >= 0.f && std::isfinite(mat_k[q]))) return fail(MS_ERR_ARG, "mat_k must be >= 0 and finite at material " + std::to_string(q));
+        if (mat_c && !(mat_c[q] >= 0.f && std::isfinite(mat_c[q]))) return fail(MS_ERR_ARG, "mat_c must be >= 0 and finite at material " + std::to_string(q));
+        if (mat_L0scale && !(mat_L0scale[q] >= 0.f && std::isfinite(mat_L0scale[q])))
+            return fail(MS_ERR_ARG, "mat_L0scale must be >= 0 and finite at material " + std::to_string(q));
+    }
+    // expand the tables into the per-spring form of ms_create
+    std::vector<float> k(S), c, L0;
+    bool uniform_c = true;
+    for (int64_t e = 0; e < S; ++e) {
+        if (mat[e] >= (uint32_t)n_mat) return fail(MS_ERR_ARG, "material id out of range at spring " + std::to_string(e));
+        k[e] = mat_k[mat[e]];
+        if (mat_c && mat_c[mat[e]] != mat_c[mat[0]]) uniform_c = false;
+    }
+    if (mat_c && !uniform_c) {
+        c.resize(S);
+        for (int64_t e = 0; e < S; ++e) c[e] = mat_c[mat[e]];
+    }
+    const float c_uniform = (mat_c && S > 0) ? mat_c[mat[0]] : 0.f;
+    if (mat_L0scale) {
+        L0.resize(S);
+        for (int64_t e = 0; e < S; ++e) {
+            const int32_t a = ij[2 * e], b = ij[2 * e + 1];
+            if (a < 0 || a >= N || b < 0 || b >= N) return fail(MS_ERR_ARG, "spring endpoint out of range at spring " + std::to_string(e));
+            float base;
+            if (rest_len) base = rest_len[e];
+            else {
+                const double dx = (double)x0[3 * b] - x0[3 * a], dy = (double)x0[3 * b + 1] - x0[3 * a + 1],
+                             dz = (double)x0[3 * b + 2] - x0[3 * a + 2];
+                base = (float)std::sqrt(dx * dx + dy * dy + dz * dz);
+            }
+            L0[e] = base * mat_L0scale[mat[e]];       // one FP32 rounding
+        }
+    }
+    return ms_create(p, N, x0, v0, mass, fixed, fext, S, ij, S > 0 ? k.data() : nullptr,
+                     c.empty() ? nullptr : c.data(), c_uniform, mat_L0scale ? (S > 0 ? L0.data() : nullptr) : rest_len,
+                     alloc, stream, out);
+}
+
 ms_status ms_set_actuation(ms_sim *s, float freq_hz, const float *amp, const float *phase)
 {
     if (!s) return fail(MS_ERR_ARG, "sim is NULL");
     if (!amp) { s->actuated = false; s->freq = 0.0; return MS_OK; }
     if (!phase) return fail(MS_ERR_ARG, "phase is required with amp");
     if (!std::isfinite(freq_hz)) return fail(MS_ERR_ARG, "freq must be finite");
+    if (s->kernel == ms::kKernelLattice)
+        return fail(MS_ERR_ARG, "the lattice kernel stores no actuation coefficients; create the system with the "
+                                "tiled kernel (kernel = 2)");
     if ((s->persistent && ms::cluster_smem_bytes(s->cl_tm, s->cl_slots, s->cl_c != nullptr, true) > 227 * 1024) ||
         (s->grid_persistent && ms::grid_smem_bytes(s->max_tile_local, s->max_fwd, s->f_c != nullptr, true) > ms::kTileSmemMax))
         return fail(MS_ERR_ARG, "the persistent kernel cannot hold the actuation coefficients of this system in "
@@ -816,6 +1086,7 @@ ms_status ms_step(ms_sim *s, int32_t nsteps)
         s->step_count += nsteps;
         return MS_OK;
     }
+    const bool lattice = s->kernel == ms::kKernelLattice;
     for (int32_t n = 0; n < nsteps; ++n) {
         a.first_step = (s->step_count + n == 0) ? 1 : 0;
         const double t = (double)(s->step_count + n) * (double)s->p.dt;
@@ -835,7 +1106,7 @@ ms_status ms_step(ms_sim *s, int32_t nsteps)
                 a.sb = q == 0 ? s->sb[s->cur] : s->rk_b[(q - 1) & 1];
                 a.oa = q == 3 ? s->sa[s->cur ^ 1] : s->rk_a[q & 1];
                 a.ob = q == 3 ? s->sb[s->cur ^ 1] : s->rk_b[q & 1];
-                MS_CUDA_TRY(ms::launch_step(a, s->stream));
+                MS_CUDA_TRY(lattice ? ms::launch_step_lattice(a, s->lat, s->stream) : ms::launch_step(a, s->stream));
             }
         } else {
             if (s->actuated) {
@@ -844,7 +1115,7 @@ ms_status ms_step(ms_sim *s, int32_t nsteps)
             }
             a.sa = s->sa[s->cur]; a.sb = s->sb[s->cur];
             a.oa = s->sa[s->cur ^ 1]; a.ob = s->sb[s->cur ^ 1];
-            MS_CUDA_TRY(ms::launch_step(a, s->stream));
+            MS_CUDA_TRY(lattice ? ms::launch_step_lattice(a, s->lat, s->stream) : ms::launch_step(a, s->stream));
         }
         s->cur ^= 1;
         if (s->tr_n > 0 && s->tr_count < s->tr_cap) {
@@ -863,11 +1134,11 @@ ms_status ms_get_state(ms_sim *s, float *x, float *v, int32_t on_device)
     if (!s) return fail(MS_ERR_ARG, "sim is NULL");
     const int N = s->N;
     if (on_device) {
-        MS_CUDA_TRY(ms::launch_gather_state(s->sa[s->cur], s->sb[s->cur], s->d_perm, N, x, v, s->stream));
+        MS_CUDA_TRY(ms::launch_gather_state(s->sa[s->cur], s->sb[s->cur], s->d_perm, s->d_cidx, N, x, v, s->stream));
         return MS_OK;
     }
     float *sx = x ? s->stage : nullptr, *sv = v ? s->stage + 3 * (size_t)N : nullptr;
-    MS_CUDA_TRY(ms::launch_gather_state(s->sa[s->cur], s->sb[s->cur], s->d_perm, N, sx, sv, s->stream));
+    MS_CUDA_TRY(ms::launch_gather_state(s->sa[s->cur], s->sb[s->cur], s->d_perm, s->d_cidx, N, sx, sv, s->stream));
     if (x) MS_CUDA_TRY(cudaMemcpyAsync(x, sx, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, s->stream));
     if (v) MS_CUDA_TRY(cudaMemcpyAsync(v, sv, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, s->stream));
     return ms_sync(s);
@@ -879,14 +1150,14 @@ ms_status ms_set_state(ms_sim *s, const float *x, const float *v, int32_t on_dev
     if (!s) return fail(MS_ERR_ARG, "sim is NULL");
     const int N = s->N;
     if (on_device) {
-        MS_CUDA_TRY(ms::launch_scatter_state(s->sa[s->cur], s->sb[s->cur], s->w, s->d_perm, N, x, v, s->stream));
+        MS_CUDA_TRY(ms::launch_scatter_state(s->sa[s->cur], s->sb[s->cur], s->w, s->d_perm, s->d_cidx, N, x, v, s->stream));
         return MS_OK;
     }
     // host input: copy to the staging buffer, check finiteness on the device,
     // and scatter only if every value is finite (the state is untouched otherwise)
     if (x) MS_CUDA_TRY(cudaMemcpyAsync(s->stage, x, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, s->stream));
     if (v) MS_CUDA_TRY(cudaMemcpyAsync(s->stage + 3 * (size_t)N, v, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, s->stream));
-    MS_CUDA_TRY(ms::launch_checked_scatter_state(s->sa[s->cur], s->sb[s->cur], s->w, s->d_perm, N, x ? s->stage : nullptr,
+    MS_CUDA_TRY(ms::launch_checked_scatter_state(s->sa[s->cur], s->sb[s->cur], s->w, s->d_perm, s->d_cidx, N, x ? s->stage : nullptr,
                                                  v ? s->stage + 3 * (size_t)N : nullptr, s->err + 1, s->stream));
     int first_bad = INT_MAX;
     MS_CUDA_TRY(cudaMemcpyAsync(&first_bad, s->err + 1, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
@@ -939,13 +1210,14 @@ ms_status ms_energy(ms_sim *s, double *out, int32_t on_device)
         a.c_n = (float)std::cos(2.0 * M_PI * s->freq * t);
     }
     a.gx = s->p.g[0]; a.gy = s->p.g[1]; a.gz = s->p.g[2]; a.k_c = s->p.k_c; a.contact = s->p.contact_on;
+    const ms::LatticeArgs *lat = s->kernel == ms::kKernelLattice ? &s->lat : nullptr;
     if (!s->e_partial) {
-        ms_status st = upload<double>(s, &s->e_partial, nullptr, 4 * (size_t)ms::energy_blocks(a) + 4);
+        ms_status st = upload<double>(s, &s->e_partial, nullptr, 4 * (size_t)ms::energy_blocks(a, lat) + 4);
         if (st != MS_OK) return st;
     }
     a.partial = s->e_partial;
-    double *res = s->e_partial + 4 * (size_t)ms::energy_blocks(a);
-    MS_CUDA_TRY(ms::launch_energy(a, on_device ? out : res, s->stream));
+    double *res = s->e_partial + 4 * (size_t)ms::energy_blocks(a, lat);
+    MS_CUDA_TRY(ms::launch_energy(a, lat, on_device ? out : res, s->stream));
     if (on_device) return MS_OK;
     MS_CUDA_TRY(cudaMemcpyAsync(out, res, 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     MS_CUDA_TRY(cudaStreamSynchronize(s->stream));

@@ -121,6 +121,35 @@ __global__ void __launch_bounds__(kTileMasses) k_energy_tiled(const EnergyArgs a
     block_reduce(t, a.partial);
 }
 
+// lattice layout: one CTA per brick, one thread per cell; each spring once,
+// from the cell it leaves in a forward direction (k < 0: no spring)
+__global__ void __launch_bounds__(kBrickCells) k_energy_lattice(const EnergyArgs a, const LatticeArgs g)
+{
+    const int tid = threadIdx.x;
+    const int b = blockIdx.x;
+    const int bx = b % g.nbx, byz = b / g.nbx, by = byz % g.nby, bz = byz / g.nby;
+    const int cx = tid % kBrickX, cy = (tid / kBrickX) % kBrickY, cz = tid / (kBrickX * kBrickY);
+    const int i = (bx * kBrickX + cx + 1) + g.X * ((by * kBrickY + cy + 1) + g.Y * (bz * kBrickZ + cz + 1));
+    Terms t{0.f, 0.f, 0.f, 0.f};
+    const float w = __ldg(&a.w[i]);
+    if (w == w) {                                        // a cell with a mass
+        mass_terms(a, i, t);
+        const float4 xi = __ldg(&a.sa[i]);
+        float pe = 0.f;
+#pragma unroll
+        for (int d = 0; d < kLatDirs; ++d) {
+            const float k = __ldg(g.kf[d] + i);
+            if (k < 0.0f) continue;
+            const float4 xj = __ldg(&a.sa[i + lat_dx(d) + g.X * (lat_dy(d) + g.Y * lat_dz(d))]);
+            const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+            const float e = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - g.L[d];
+            pe += k * e * e;
+        }
+        t.pe = 0.5f * pe;
+    }
+    block_reduce(t, a.partial);
+}
+
 // one block: out[c] = sum over blocks of partial[4 b + c], in block order
 // per thread, then a fixed tree over the threads
 __global__ void __launch_bounds__(kEnergyThreads) k_energy_final(const double *partial, int n_blocks, double *out)
@@ -149,15 +178,17 @@ __global__ void k_trace(const float4 *__restrict__ sa, const int32_t *__restrict
 
 }  // namespace
 
-int energy_blocks(const EnergyArgs &a)
+int energy_blocks(const EnergyArgs &a, const LatticeArgs *lat)
 {
+    if (lat) return lat->nbx * lat->nby * lat->nbz;
     return a.tiled ? a.n_tiles : (a.N + kEnergyThreads - 1) / kEnergyThreads;
 }
 
-cudaError_t launch_energy(const EnergyArgs &a, double *out, cudaStream_t s)
+cudaError_t launch_energy(const EnergyArgs &a, const LatticeArgs *lat, double *out, cudaStream_t s)
 {
-    const int nb = energy_blocks(a);
-    if (a.tiled) k_energy_tiled<<<nb, kTileMasses, 0, s>>>(a);
+    const int nb = energy_blocks(a, lat);
+    if (lat) k_energy_lattice<<<nb, kBrickCells, 0, s>>>(a, *lat);
+    else if (a.tiled) k_energy_tiled<<<nb, kTileMasses, 0, s>>>(a);
     else k_energy_gather<<<nb, kEnergyThreads, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

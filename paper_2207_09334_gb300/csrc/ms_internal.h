@@ -118,6 +118,43 @@ struct StepArgs {
     int rk_stage;            // RK4: stage 0..3
 };
 
+// Lattice layout (kernel 4, ms_lattice.cu).  A network whose masses sit on
+// the cells of a box lattice, whose springs join cells of the 26-neighbourhood
+// (at most one per pair), with one rest length per lattice direction and one
+// dashpot coefficient: topology and rest lengths come from the lattice, and
+// only k is stored per spring (4 bytes).
+//   * Cells live in a padded lattice of X x Y x Z cells (x fastest): one guard
+//     cell on every side, and the interior rounded up to whole bricks of
+//     kBrickX x kBrickY x kBrickZ cells.  A cell's internal index is its
+//     padded lattice index; the caller's mass c sits at cidx[c].
+//   * Each of the 13 forward directions d (lat_dx/dy/dz below) has its own
+//     array over the padded cells: kf[d][i] = k of the spring from cell i to
+//     cell i + off(d), or -1 where there is none (a missing pair, a cell
+//     without mass, the guard band).
+//   * Cells without a mass have w = NaN and a zero state; no kernel integrates
+//     them.
+constexpr int kKernelLattice = 4;
+constexpr int kBrickX = 16, kBrickY = 8, kBrickZ = 4;
+constexpr int kBrickCells = kBrickX * kBrickY * kBrickZ;        // 512: one thread per cell
+constexpr int kHaloX = kBrickX + 2, kHaloY = kBrickY + 2, kHaloZ = kBrickZ + 2;
+constexpr int kHaloCells = kHaloX * kHaloY * kHaloZ;            // 1080 cells staged per brick
+constexpr int kLatDirs = 13;
+// forward direction d: (1,0,0); then (dx,1,0) for dx = -1..1; then (dx,dy,1) for
+// dy = -1..1, dx = -1..1 -- the 13 offsets that are positive in (z, y, x) order
+__host__ __device__ constexpr int lat_dx(int d) { return d == 0 ? 1 : d <= 3 ? d - 2 : (d - 4) % 3 - 1; }
+__host__ __device__ constexpr int lat_dy(int d) { return d == 0 ? 0 : d <= 3 ? 1 : (d - 4) / 3 - 1; }
+__host__ __device__ constexpr int lat_dz(int d) { return d <= 3 ? 0 : 1; }
+
+struct LatticeArgs {
+    const float *kf[kLatDirs];   // kf[d][i]: the spring from cell i in direction d
+    const float *kb[kLatDirs];   // kb[d][i] = kf[d][i - off(d)]: the spring reaching cell i from direction -d
+    float L[kLatDirs];           // rest length per direction
+    float c;                     // dashpot coefficient of every spring
+    int X, Y, Z;                 // padded extents (cells)
+    int nbx, nby, nbz;           // bricks per axis
+};
+cudaError_t launch_step_lattice(const StepArgs &a, const LatticeArgs &g, cudaStream_t st);
+
 // Persistent grid step (ms_step.cu): nsteps steps of the tiled layout in one
 // cooperative launch; buffer n & 1 holds the state at step n of the call.
 struct GridArgs {
@@ -152,23 +189,26 @@ struct EnergyArgs {
     float gx, gy, gz, k_c;
     int contact;
 };
-int energy_blocks(const EnergyArgs &a);
+// lat: the lattice layout's arrays (nullptr for the gather and tiled layouts)
+int energy_blocks(const EnergyArgs &a, const LatticeArgs *lat);
 // out (device): kinetic, elastic, gravitational, ground-penalty energy (FP64)
-cudaError_t launch_energy(const EnergyArgs &a, double *out, cudaStream_t s);
+cudaError_t launch_energy(const EnergyArgs &a, const LatticeArgs *lat, double *out, cudaStream_t s);
 // out[3 q + c] = x[idx[q]][c] for q < n
 cudaError_t launch_trace(const float4 *sa, const int32_t *idx, int n, float *out, cudaStream_t s);
 
 // Launchers (ms_step.cu, ms_state.cu).
 cudaError_t launch_step(const StepArgs &a, cudaStream_t st);
-cudaError_t launch_gather_state(const float4 *sa, const float2 *sb, const int32_t *perm, int N,
+// perm: internal -> caller index (or nullptr = identity), or cidx: caller -> internal index
+cudaError_t launch_gather_state(const float4 *sa, const float2 *sb, const int32_t *perm, const int32_t *cidx, int N,
                                 float *x_out, float *v_out, cudaStream_t stream);
-cudaError_t launch_scatter_state(float4 *sa, float2 *sb, const float *w, const int32_t *perm, int N,
-                                 const float *x_in, const float *v_in, cudaStream_t stream);
+cudaError_t launch_scatter_state(float4 *sa, float2 *sb, const float *w, const int32_t *perm, const int32_t *cidx,
+                                 int N, const float *x_in, const float *v_in, cudaStream_t stream);
 // the same, after a device-side finiteness check of the inputs: first_bad
 // (device int) receives the first caller index with a non-finite value, or
 // INT_MAX, and the state is written only when every value is finite
-cudaError_t launch_checked_scatter_state(float4 *sa, float2 *sb, const float *w, const int32_t *perm, int N,
-                                         const float *x_in, const float *v_in, int *first_bad, cudaStream_t stream);
+cudaError_t launch_checked_scatter_state(float4 *sa, float2 *sb, const float *w, const int32_t *perm,
+                                         const int32_t *cidx, int N, const float *x_in, const float *v_in,
+                                         int *first_bad, cudaStream_t stream);
 // packed state <-> 2 float4 per mass ((x, w), (v, 0)), for n masses
 cudaError_t launch_pack_state(const float4 *pairs, int n, float4 *sa, float2 *sb, float *w, cudaStream_t stream);
 cudaError_t launch_unpack_state(const float4 *sa, const float2 *sb, const float *w, int n, float4 *pairs,

@@ -2,6 +2,10 @@
 // (N, 3) arrays in caller order and the library's internal packed buffers
 // (internal order: a = (x, y, z, vx), b = (vy, vz), w = 1/m or -m), and
 // between the packed form and 2 float4 per mass ((x, w), (v, 0)).
+// The internal order is given either as perm (internal index -> caller
+// index, for layouts whose internal indices are 0..N-1) or as cidx (caller
+// index -> internal index, for the lattice layout, whose padded index space
+// is larger than N).
 #include "ms_internal.h"
 
 #include <climits>
@@ -9,12 +13,21 @@
 namespace ms {
 namespace {
 
-__global__ void k_gather_state(const float4 *__restrict__ sa, const float2 *__restrict__ sb,
-                               const int32_t *__restrict__ perm, int N, float *__restrict__ xo, float *__restrict__ vo)
+// (internal i, caller c) of thread t
+__device__ __forceinline__ void index_pair(const int32_t *perm, const int32_t *cidx, int t, int &i, int &c)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const int c = perm ? perm[i] : i;
+    if (cidx) { c = t; i = cidx[t]; }
+    else { i = t; c = perm ? perm[t] : t; }
+}
+
+__global__ void k_gather_state(const float4 *__restrict__ sa, const float2 *__restrict__ sb,
+                               const int32_t *__restrict__ perm, const int32_t *__restrict__ cidx, int N,
+                               float *__restrict__ xo, float *__restrict__ vo)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    int i, c;
+    index_pair(perm, cidx, t, i, c);
     const float4 p = sa[i];
     if (xo) { xo[3 * c] = p.x; xo[3 * c + 1] = p.y; xo[3 * c + 2] = p.z; }
     if (vo) { const float2 q = sb[i]; vo[3 * c] = p.w; vo[3 * c + 1] = q.x; vo[3 * c + 2] = q.y; }
@@ -22,13 +35,14 @@ __global__ void k_gather_state(const float4 *__restrict__ sa, const float2 *__re
 
 // skip: if not null and no longer INT_MAX (a non-finite input was found), nothing is written
 __global__ void k_scatter_state(float4 *__restrict__ sa, float2 *__restrict__ sb, const float *__restrict__ w,
-                                const int32_t *__restrict__ perm, int N, const float *__restrict__ xi,
-                                const float *__restrict__ vi, const int *skip)
+                                const int32_t *__restrict__ perm, const int32_t *__restrict__ cidx, int N,
+                                const float *__restrict__ xi, const float *__restrict__ vi, const int *skip)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
     if (skip && *skip != INT_MAX) return;
-    const int c = perm ? perm[i] : i;
+    int i, c;
+    index_pair(perm, cidx, t, i, c);
     float4 p = sa[i];
     if (xi) { p.x = xi[3 * c]; p.y = xi[3 * c + 1]; p.z = xi[3 * c + 2]; }
     if (vi) {
@@ -76,29 +90,30 @@ __global__ void k_set_int(int *p, int v) { *p = v; }
 
 }  // namespace
 
-cudaError_t launch_gather_state(const float4 *sa, const float2 *sb, const int32_t *perm, int N,
+cudaError_t launch_gather_state(const float4 *sa, const float2 *sb, const int32_t *perm, const int32_t *cidx, int N,
                                 float *x_out, float *v_out, cudaStream_t stream)
 {
     if (N <= 0) return cudaSuccess;
-    k_gather_state<<<(N + 255) / 256, 256, 0, stream>>>(sa, sb, perm, N, x_out, v_out);
+    k_gather_state<<<(N + 255) / 256, 256, 0, stream>>>(sa, sb, perm, cidx, N, x_out, v_out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter_state(float4 *sa, float2 *sb, const float *w, const int32_t *perm, int N,
-                                 const float *x_in, const float *v_in, cudaStream_t stream)
+cudaError_t launch_scatter_state(float4 *sa, float2 *sb, const float *w, const int32_t *perm, const int32_t *cidx,
+                                 int N, const float *x_in, const float *v_in, cudaStream_t stream)
 {
     if (N <= 0) return cudaSuccess;
-    k_scatter_state<<<(N + 255) / 256, 256, 0, stream>>>(sa, sb, w, perm, N, x_in, v_in, nullptr);
+    k_scatter_state<<<(N + 255) / 256, 256, 0, stream>>>(sa, sb, w, perm, cidx, N, x_in, v_in, nullptr);
     return cudaGetLastError();
 }
 
-cudaError_t launch_checked_scatter_state(float4 *sa, float2 *sb, const float *w, const int32_t *perm, int N,
-                                         const float *x_in, const float *v_in, int *first_bad, cudaStream_t stream)
+cudaError_t launch_checked_scatter_state(float4 *sa, float2 *sb, const float *w, const int32_t *perm,
+                                         const int32_t *cidx, int N, const float *x_in, const float *v_in,
+                                         int *first_bad, cudaStream_t stream)
 {
     if (N <= 0) return cudaSuccess;
     k_set_int<<<1, 1, 0, stream>>>(first_bad, INT_MAX);
     k_check_finite<<<(N + 255) / 256, 256, 0, stream>>>(x_in, v_in, N, first_bad);
-    k_scatter_state<<<(N + 255) / 256, 256, 0, stream>>>(sa, sb, w, perm, N, x_in, v_in, first_bad);
+    k_scatter_state<<<(N + 255) / 256, 256, 0, stream>>>(sa, sb, w, perm, cidx, N, x_in, v_in, first_bad);
     return cudaGetLastError();
 }
 

@@ -18,7 +18,7 @@ __all__ = ["Sim", "make_params", "torch_allocator"]
 
 
 ORDERS = {None: 0, False: 0, "auto": 0, True: 1, "morton": 1, "caller": 2}
-KERNELS = {None: 0, "auto": 0, "gather": 1, "tiled": 2, "persistent": 3}
+KERNELS = {None: 0, "auto": 0, "gather": 1, "tiled": 2, "persistent": 3, "lattice": 4}
 
 
 INTEGRATORS = {"symplectic_euler": 0, "forward_euler": 1, "verlet": 2, "rk4": 3}
@@ -27,7 +27,7 @@ INTEGRATORS = {"symplectic_euler": 0, "forward_euler": 1, "verlet": 2, "rk4": 3}
 def make_params(params: dict, reorder=None, strict_stability: bool = False, kernel=None,
                 integrator="symplectic_euler") -> MsParams:
     """reorder: None/False = library default, True/"morton", or "caller";
-    kernel: None/"auto", "gather", "tiled" or "persistent"."""
+    kernel: None/"auto", "gather", "tiled", "persistent" or "lattice"."""
     p = MsParams()
     p.dt = float(params["dt"])
     for a in range(3):
@@ -101,7 +101,8 @@ class Sim:
     """One mass-spring system resident on the GPU (ms_create ... ms_destroy).
 
     system: dict of arrays (x, v, m, fixed, [fext], ij, k, c, L0, [A, phi, freq]);
-    c may be a scalar (uniform damping).  params: dt, g, k_c, mu, vel_damping, contact.
+    c may be a scalar (uniform damping).  Materials form instead of k / c:
+    mat (S,) ids with tables mat_k, [mat_c], [mat_L0scale] (ms_create_materials).  params: dt, g, k_c, mu, vel_damping, contact.
     """
 
     def __init__(self, system: dict, params: dict, reorder=None, stream=None,
@@ -115,6 +116,10 @@ class Sim:
         fext = system.get("fext")
         fext = None if fext is None else _f32(fext, (N, 3))
         ij = np.ascontiguousarray(system["ij"], np.int32).reshape(-1, 2); S = ij.shape[0]
+        if system.get("mat") is not None:       # materials form: ms_create_materials
+            self._init_materials(system, params, reorder, stream, use_torch_allocator, strict_stability, kernel,
+                                 integrator, x, v, m, fixed, fext, ij)
+            return
         k = _f32(system["k"], (S,))
         c = system.get("c", 0.0)
         c_uniform = 0.0
@@ -135,6 +140,31 @@ class Sim:
                             S, _ptr(ij), _ptr(k), _ptr(c), float(c_uniform), _ptr(L0),
                             C.byref(self._alloc.struct) if self._alloc else None,
                             C.c_void_p(self.stream), C.byref(handle)))
+        self.h = handle
+        if system.get("A") is not None:
+            self.set_actuation(system.get("freq", 0.0), system["A"], system["phi"])
+
+    def _init_materials(self, system, params, reorder, stream, use_torch_allocator, strict_stability, kernel,
+                        integrator, x, v, m, fixed, fext, ij):
+        """system["mat"] (S,) material ids with tables mat_k, [mat_c], [mat_L0scale]
+        and optional per-spring base rest lengths L0."""
+        lib = self._lib
+        N, S = x.shape[0], ij.shape[0]
+        mat = np.ascontiguousarray(system["mat"], np.uint16).reshape(S)
+        mat_k = _f32(system["mat_k"]); n_mat = mat_k.shape[0]
+        mat_c = None if system.get("mat_c") is None else _f32(system["mat_c"], (n_mat,))
+        scale = None if system.get("mat_L0scale") is None else _f32(system["mat_L0scale"], (n_mat,))
+        L0 = system.get("L0")
+        L0 = None if L0 is None else _f32(L0, (S,))
+        self.N, self.S = N, S
+        self._params = make_params(params, reorder, strict_stability, kernel, integrator)
+        self._alloc = torch_allocator() if use_torch_allocator else None
+        self.stream = _stream_handle(stream)
+        handle = C.c_void_p()
+        check(lib.ms_create_materials(C.byref(self._params), N, _ptr(x), _ptr(v), _ptr(m), _ptr(fixed), _ptr(fext),
+                                      S, _ptr(ij), _ptr(mat), int(n_mat), _ptr(mat_k), _ptr(mat_c), _ptr(scale),
+                                      _ptr(L0), C.byref(self._alloc.struct) if self._alloc else None,
+                                      C.c_void_p(self.stream), C.byref(handle)))
         self.h = handle
         if system.get("A") is not None:
             self.set_actuation(system.get("freq", 0.0), system["A"], system["phi"])

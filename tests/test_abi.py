@@ -123,3 +123,81 @@ def test_null_handles_are_errors(lib):
     assert lib.ms_sync(None) == 1
     assert lib.ms_destroy(None) == 0
     assert b"sm_103a" in lib.ms_version()
+
+
+def _create_materials(lib, mat, n_mat, mat_k, mat_c=None, scale=None):
+    from paper_2207_09334_gb300._lib import MsParams
+    p = MsParams(); p.dt = 1e-3; p.g[2] = -9.81
+    x = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32); v = np.zeros_like(x)
+    m = np.ones(3, np.float32); ij = np.array([[0, 1], [1, 2]], np.int32)
+    mat = np.array(mat, np.uint16); mk = np.array(mat_k, np.float32)
+    mc = None if mat_c is None else np.array(mat_c, np.float32)
+    sc = None if scale is None else np.array(scale, np.float32)
+    ptr = lambda a: None if a is None else a.ctypes.data
+    out = C.c_void_p()
+    rc = lib.ms_create_materials(C.byref(p), 3, x.ctypes.data, v.ctypes.data, m.ctypes.data, None, None, 2,
+                                 ij.ctypes.data, mat.ctypes.data, n_mat, mk.ctypes.data, ptr(mc), ptr(sc), None,
+                                 None, None, C.byref(out))
+    return rc, out
+
+
+@pytest.mark.parametrize("args,what", [
+    (([0, 2], 2, [1.0, 2.0]), "material id out of range"),
+    (([0, 1], 2, [1.0, -2.0]), "mat_k"),
+    (([0, 1], 2, [1.0, 2.0], [0.1, float("nan")]), "mat_c"),
+    (([0, 1], 2, [1.0, 2.0], None, [1.0, -1.0]), "mat_L0scale"),
+    (([0, 0], 0, [1.0]), "n_mat"),
+])
+def test_create_materials_rejects_bad_tables(lib, args, what):
+    rc, out = _create_materials(lib, *args)
+    assert rc == 1 and not out.value
+    assert what in lib.ms_last_error().decode()
+
+
+@pytest.mark.gpu
+def test_two_material_system_equals_the_per_spring_form(lib, ora):
+    """A lattice of two materials (soft and stiff, different damping, the stiff
+    one pre-stretched by a rest-length factor) built through
+    ms_create_materials steps bit for bit like the same system given as
+    per-spring arrays to ms_create, and matches the oracle."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import synth
+    import paper_2207_09334_gb300 as ms
+    x, ij, L0 = synth.box_lattice(7, 6, 5, 0.01, origin=(0, 0, 0.002))
+    N, S = x.shape[0], ij.shape[0]
+    rng = np.random.default_rng(3)
+    mat = rng.integers(0, 2, S).astype(np.uint16)
+    mat_k = np.array([2e3, 3e4], np.float32); mat_c = np.array([0.02, 0.08], np.float32)
+    scale = np.array([1.0, 0.97], np.float32)
+    base = dict(x=x, v=np.zeros((N, 3), np.float32), m=np.full(N, 1e-3, np.float32),
+                fixed=np.zeros(N, np.uint8), ij=ij)
+    per_spring = dict(base, k=mat_k[mat], c=mat_c[mat], L0=(L0 * scale[mat]).astype(np.float32))
+    by_mat = dict(base, mat=mat, mat_k=mat_k, mat_c=mat_c, mat_L0scale=scale, L0=L0)
+    p = synth.params(dt=1e-4, g=(0, 0, -9.81), contact=True, k_c=1e5, mu=0.5)
+    out = []
+    for s in (by_mat, per_spring):
+        with ms.Sim(s, p, kernel="tiled") as sim:
+            sim.step(300)
+            out.append(sim.get_state())
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    q = dict(p); q["dt"] = float(np.float32(q["dt"])); q["k_c"] = float(np.float32(q["k_c"]))
+    q["mu"] = float(np.float32(q["mu"])); q["g"] = tuple(float(np.float32(g)) for g in p["g"])
+    xo, _ = ora.run(per_spring, q, 300)
+    size = float(np.ptp(x, axis=0).max())
+    assert np.abs(out[0][0] - xo).max() <= 1e-4 * size
+
+
+@pytest.mark.parametrize("x,ij,what", [
+    ([[0, 0, 0], [1, 0, 0], [0.5, 0.3, 0]], [[0, 1], [1, 2]], "grid"),        # off the grid
+    ([[0, 0, 0], [1, 0, 0], [3, 0, 0]], [[0, 1], [1, 2]], "neighbours"),      # a spring two cells long
+    ([[0, 0, 0], [1, 0, 0]], [[0, 1], [1, 0]], "same pair"),                   # two springs on one pair
+])
+def test_lattice_kernel_rejects_other_networks(lib, x, ij, what):
+    """kernel = 4 checks on the host that the network is a box lattice and
+    names the reason when it is not (no device memory is touched)."""
+    rc, out = _create(lib, x=x, ij=ij, kernel=4)
+    assert rc == 1 and not out.value
+    msg = lib.ms_last_error().decode()
+    assert "lattice" in msg and what in msg, msg

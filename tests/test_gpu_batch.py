@@ -81,6 +81,43 @@ def test_population_matches_oracle_200_steps(ms, ora, policy):
         assert in_contact >= 1                     # contact is exercised
 
 
+def test_population_with_config3_sized_robots_matches_oracle(ms, ora):
+    """Robots of the benchmark population's largest sizes (sides 10 to 12
+    voxels): more than 512 masses each, so the block schedule's per-robot loop
+    over masses takes several passes, and a solid 12 x 12 x 12 robot reaches
+    the 2197-mass maximum.  Mixed with small robots so that both schedules
+    run in the same launch.  200 steps with contact and friction against the
+    per-voxel oracle: positions within 1e-4 of the body size, centre-of-mass
+    travel within 1 %."""
+    rng = np.random.default_rng(31)
+    solid = (rng.integers(1, 4, size=(12, 12, 12)).astype(np.uint8), rng.uniform(0, 2 * np.pi, (12, 12, 12)))
+    designs = [solid,
+               synth.random_voxel_design(rng, (10, 11, 12)),
+               synth.random_voxel_design(rng, (11, 11, 11)),
+               synth.random_voxel_design(rng, (12, 10, 11))]
+    designs += population(6, seed=32, side_range=(2, 4))
+    with make_pop(ms, designs) as pop:
+        inf = pop.info()
+        assert inf["max_robot_masses"] == 13 ** 3
+        assert inf["n_block_items"] >= 4
+        pop.run(200)
+        xg, _ = pop.get_state()
+        big = 0
+        for r, d in enumerate(designs):
+            s, xo, _, _ = oracle_robot(ora, d, 200)
+            n, first = pop.robot_info(r)
+            assert n == s["x"].shape[0]
+            big += int(n > 512)
+            size = float(np.ptp(s["x"], axis=0).max())
+            err = np.abs(xg[first:first + n] - xo).max()
+            assert err <= 1e-4 * size, (r, n, err, size)
+            m = s["m"]
+            to = ora.centre_of_mass(m, xo)[0] - ora.centre_of_mass(m, s["x"])[0]
+            tg = ora.centre_of_mass(m, xg[first:first + n].astype(np.float64))[0] - ora.centre_of_mass(m, s["x"])[0]
+            assert abs(tg - to) <= max(0.01 * abs(to), 1e-6), (r, n, tg, to)
+        assert big >= 4
+
+
 @pytest.mark.slow
 def test_population_com_travel_2000_steps(ms, ora):
     """Over 2000 steps the travel of a robot hopping on a frictional ground

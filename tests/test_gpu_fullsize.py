@@ -1,9 +1,11 @@
 """Parity at the benchmark's sizes.
 
 * The 256^3 throughput lattice (16.8 M masses, 216 M springs), stepped by
-  the default (tiled) kernel exactly as bench.py times it, against the FP64
-  oracle on sampled masses after 1 and after 5 steps.
-* The 64^3 lattice with the same parameters, 200 steps, every mass.
+  the default kernel for it (the lattice kernel) exactly as bench.py times
+  it, against the FP64 oracle on sampled masses after 1 and after 5 steps;
+  the same for the general tiled kernel.
+* The 64^3 lattice with the same parameters, 200 steps, every mass, with the
+  lattice and the tiled kernels.
 
 The oracle cannot step the whole 256^3 lattice in a test, but after n steps a
 mass depends only on the masses within n springs of it.  So the oracle steps
@@ -78,13 +80,17 @@ def subsystem(s, keep):
 
 
 @pytest.fixture(scope="module")
-def lattice256(ms):
-    """The bench's workload, stepped once and then four more times by the bench's kernel."""
-    n = 256
-    s = synth.throughput_lattice(n)
-    p = synth.throughput_params()
-    with ms.Sim(s, p) as sim:
-        assert sim.info()["kernel"] == 2             # the bench's kernel
+def workload256():
+    return synth.throughput_lattice(256), synth.throughput_params()
+
+
+@pytest.fixture(scope="module", params=["auto", "tiled"])
+def lattice256(ms, workload256, request):
+    """The bench's workload, stepped once and then four more times by the
+    bench's kernel (the default: the lattice kernel) or the tiled kernel."""
+    s, p = workload256
+    with ms.Sim(s, p, kernel=request.param) as sim:
+        assert sim.info()["kernel"] == (4 if request.param == "auto" else 2)
         sim.step(1)
         x1, v1 = sim.get_state()
         sim.step(4)
@@ -150,13 +156,16 @@ def test_full_size_lattice_five_steps_on_sampled_masses(ora, lattice256):
 
 
 @pytest.mark.slow
-def test_lattice64_200_steps_every_mass(ms, ora):
+@pytest.mark.parametrize("kernel", ["auto", "tiled"])
+def test_lattice64_200_steps_every_mass(ms, ora, kernel):
     """The 64^3 lattice (262 144 masses, 3.3 M springs) with the benchmark's
     parameters, 200 steps, every mass against the oracle (1e-5 of the body
-    size, the benchmark's contact-free position gate)."""
+    size, the benchmark's contact-free position gate); the default kernel for
+    it is the lattice kernel."""
     s = synth.throughput_lattice(64)
     p = synth.throughput_params()
-    with ms.Sim(s, p) as sim:
+    with ms.Sim(s, p, kernel=kernel) as sim:
+        assert sim.info()["kernel"] == (4 if kernel == "auto" else 2)
         sim.step(120)
         sim.step(80)
         xg, vg = sim.get_state()

@@ -1,0 +1,211 @@
+"""The lattice kernel (kernel 4: topology and rest lengths from the grid, only
+k stored per spring) against the FP64 oracle on identical seeded inputs.
+
+Gates are those of the other step tests: max |x_gpu - x_oracle| <= 1e-5 of the
+body size after a contact-free run, <= 1e-4 after 200 steps with ground
+contact (and the centre-of-mass displacement within 1 %).  The lattices are
+sized so that bricks of 16 x 8 x 4 cells are cut by a ragged tail on every
+axis, and some have holes (cells without a mass, inside a brick) and missing
+springs between present masses.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ms():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2207_09334_gb300 as ms
+    ms.load()
+    return ms
+
+
+def f32p(p):
+    q = dict(p)
+    for key in ("dt", "k_c", "mu", "vel_damping"):
+        if key in q:
+            q[key] = float(np.float32(q[key]))
+    q["g"] = tuple(float(np.float32(g)) for g in p["g"])
+    return q
+
+
+def body_size(s):
+    return float(np.ptp(np.asarray(s["x"], np.float64), axis=0).max())
+
+
+def ragged_lattice(nx=37, ny=21, nz=11, seed=0, a=1e-3, origin=(0.0, 0.0, 0.0)):
+    """The throughput lattice's recipe on a box whose sides are not multiples
+    of the brick: k ~ U[5e3, 5e4], c = 0.05, bottom layer anchored,
+    v ~ N(0, 1e-3)."""
+    x, ij, L0 = synth.box_lattice(nx, ny, nz, a, origin=origin)
+    rng = np.random.default_rng(seed)
+    N, S = x.shape[0], ij.shape[0]
+    return dict(x=x, v=(1e-3 * rng.standard_normal((N, 3))).astype(np.float32),
+                m=np.full(N, 1e-3, np.float32), fixed=(np.arange(N) < nx * ny).astype(np.uint8), ij=ij,
+                k=rng.uniform(5e3, 5e4, S).astype(np.float32), c=np.float32(0.05), L0=L0)
+
+
+def drop(s, keep_mass, keep_spring=None):
+    """Remove masses (and their springs), and optionally some springs."""
+    ij = s["ij"]
+    ks = keep_mass[ij[:, 0]] & keep_mass[ij[:, 1]]
+    if keep_spring is not None:
+        ks &= keep_spring
+    remap = -np.ones(keep_mass.size, np.int64)
+    remap[keep_mass] = np.arange(int(keep_mass.sum()))
+    out = {key: (val[keep_mass] if key in ("x", "v", "m", "fixed", "fext") else val) for key, val in s.items()}
+    out["ij"] = remap[ij[ks]].astype(np.int32)
+    for key in ("k", "L0"):
+        out[key] = s[key][ks]
+    if np.ndim(s["c"]) == 1:
+        out["c"] = s["c"][ks]
+    return out
+
+
+def run_gpu(ms, s, p, n, chunks=1, integrator="symplectic_euler", kernel="lattice"):
+    with ms.Sim(s, p, kernel=kernel, integrator=integrator) as sim:
+        assert sim.info()["kernel"] == (4 if kernel == "lattice" else sim.info()["kernel"])
+        done = 0
+        for q in range(chunks):
+            todo = n * (q + 1) // chunks - done
+            sim.step(todo)
+            done += todo
+        x, v = sim.get_state()
+    return x.astype(np.float64), v.astype(np.float64)
+
+
+def test_ragged_throughput_lattice_200_steps(ms, ora):
+    """37 x 21 x 11 masses: 3 x 3 x 3 bricks, each axis ending in a partial
+    brick; gravity, anchored bottom layer, 200 steps in two calls."""
+    s = ragged_lattice()
+    p = synth.throughput_params()
+    xg, vg = run_gpu(ms, s, p, 200, chunks=2)
+    xo, vo = ora.run(s, f32p(p), 200)
+    assert np.abs(xg - xo).max() <= 1e-5 * body_size(s), np.abs(xg - xo).max()
+    assert np.abs(vg - vo).max() <= 1e-3
+
+
+def test_lattice_with_holes_and_missing_springs(ms, ora):
+    """Cells without a mass inside the bricks (a random 10 % of the masses
+    removed with their springs), and 15 % of the remaining springs removed
+    between masses that stay: those pairs read k = -1 and must exert nothing,
+    the dashpot included.  External force on some masses."""
+    s = ragged_lattice(nx=29, ny=13, nz=9, seed=4)
+    rng = np.random.default_rng(5)
+    keep_m = rng.random(s["x"].shape[0]) > 0.10
+    keep_m[: 29 * 13] = True                       # the anchored layer stays whole
+    keep_s = rng.random(s["ij"].shape[0]) > 0.15
+    t = drop(s, keep_m, keep_s)
+    t["fext"] = (2e-4 * rng.standard_normal(t["x"].shape)).astype(np.float32)
+    p = synth.throughput_params()
+    xg, _ = run_gpu(ms, t, p, 150)
+    xo, _ = ora.run(t, f32p(p), 150)
+    assert np.abs(xg - xo).max() <= 1e-5 * body_size(t), np.abs(xg - xo).max()
+
+
+def test_lattice_ground_contact_200_steps(ms, ora):
+    """A 19 x 17 x 6 slab thrown onto the ground (contact and friction, no
+    anchors), the contact gates: 1e-4 of the body size and the centre-of-mass
+    displacement within 1 %."""
+    x, ij, L0 = synth.box_lattice(19, 17, 6, 0.01, origin=(0.0, 0.0, 0.001))
+    N, S = x.shape[0], ij.shape[0]
+    rng = np.random.default_rng(8)
+    s = dict(x=x, v=np.tile(np.array([0.3, -0.2, -0.6], np.float32), (N, 1)), m=np.full(N, 1e-3, np.float32),
+             fixed=np.zeros(N, np.uint8), ij=ij, k=rng.uniform(5e3, 1e4, S).astype(np.float32),
+             c=np.float32(0.1), L0=L0)
+    p = synth.soft_cube_params(contact=True)
+    xg, _ = run_gpu(ms, s, p, 200)
+    xo, vo, zmin = s["x"], s["v"], np.inf
+    for c in range(20):
+        xo, vo = ora.run(s, f32p(p), 10, n0=10 * c, x=xo, v=vo)
+        zmin = min(zmin, xo[:, 2].min())
+    assert zmin < -1e-5
+    assert np.abs(xg - xo).max() <= 1e-4 * body_size(s), np.abs(xg - xo).max()
+    m = s["m"].astype(np.float64)
+    d_o = ora.centre_of_mass(m, xo) - ora.centre_of_mass(m, s["x"])
+    d_g = ora.centre_of_mass(m, xg) - ora.centre_of_mass(m, s["x"])
+    assert np.linalg.norm(d_g - d_o) <= 0.01 * np.linalg.norm(d_o)
+
+
+@pytest.mark.parametrize("integ", ["forward_euler", "verlet", "rk4"])
+def test_lattice_other_integrators(ms, ora, integ):
+    """The paper's forward Euler (eq. 4), position Verlet (eq. 5-6) and RK4
+    (eq. 7-8) on the lattice kernel.  Forward Euler amplifies every mode by
+    sqrt(1 + (omega dt)^2) per step, so the lattice is soft (k ~ U[50, 150],
+    dt = 2e-5: the top mode has omega dt ~ 0.05, growth below 1.5x over the
+    run), as in the tiled kernel's test."""
+    s = ragged_lattice(nx=18, ny=9, nz=5, seed=9)
+    s["k"] = np.random.default_rng(10).uniform(50.0, 150.0, s["ij"].shape[0]).astype(np.float32)
+    s["v"] = (0.02 * np.random.default_rng(11).standard_normal(s["v"].shape)).astype(np.float32)
+    p = synth.params(dt=2e-5, g=(0, 0, -9.81))
+    xg, _ = run_gpu(ms, s, p, 300, chunks=2, integrator=integ)
+    xo, _ = ora.run(s, f32p(p), 300, integrator=integ)
+    assert np.abs(xg - xo).max() <= 1e-5 * body_size(s), np.abs(xg - xo).max()
+
+
+def test_lattice_runs_are_bit_identical_and_state_round_trips(ms):
+    s = ragged_lattice(nx=20, ny=10, nz=6, seed=2)
+    p = synth.throughput_params()
+    out = []
+    for _ in range(2):
+        with ms.Sim(s, p, kernel="lattice") as sim:
+            sim.step(50)
+            out.append(sim.get_state())
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    with ms.Sim(s, p, kernel="lattice") as sim:
+        sim.step(25)
+        x, v = sim.get_state()
+        sim.step(25)
+        a = sim.get_state()
+        sim.set_state(x, v)                             # checkpoint restore
+        sim.step(25)
+        b = sim.get_state()
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_lattice_energy_and_trace(ms, ora):
+    """ms_energy on the lattice layout against the oracle's energies of the
+    same state (positions moved 1e-5 m off the grid through set_state, so that
+    the springs' extensions are well above FP32 rounding); the trace records
+    the positions get_state reports."""
+    s = ragged_lattice(nx=21, ny=11, nz=7, seed=3, origin=(0.0, 0.0, -2e-4))
+    p = synth.throughput_params(contact=True, k_c=1e5)
+    rng = np.random.default_rng(6)
+    x0 = (s["x"] + 1e-5 * rng.standard_normal(s["x"].shape)).astype(np.float32)
+    x0[s["fixed"].astype(bool)] = s["x"][s["fixed"].astype(bool)]
+    with ms.Sim(s, p, kernel="lattice") as sim:
+        sim.set_state(x0, s["v"])
+        e0 = sim.energy()
+        tip = [0, 21 * 11 * 7 - 1, 1000]
+        sim.trace(tip, 10)
+        sim.step(10)
+        x, v = sim.get_state()
+        e = sim.energy()
+        tr = sim.get_trace()
+        assert sim.energy() == e                        # fixed reduction order
+    v0 = s["v"].copy(); v0[s["fixed"].astype(bool)] = 0
+    for got_all, (xs, vs) in ((e0, (x0, v0)), (e, (x, v))):
+        want_all = ora.energy(s, f32p(p), xs.astype(np.float64), vs.astype(np.float64))
+        for got, want in zip(got_all, want_all):
+            assert abs(got - want) <= 1e-5 * max(abs(want), 1e-12) + 1e-12, (got, want)
+    assert e[3] > 0                                     # part of it is in the ground
+    assert np.array_equal(tr[-1], x[tip])
+
+
+def test_lattice_kernel_refusals(ms):
+    s = ragged_lattice(nx=8, ny=8, nz=4)
+    p = synth.throughput_params()
+    with ms.Sim(s, p, kernel="lattice") as sim:
+        with pytest.raises(ms.MsError) as e:
+            sim.set_actuation(2.0, np.full(s["ij"].shape[0], 0.1), np.zeros(s["ij"].shape[0]))
+        assert e.value.code == 1 and "tiled" in str(e.value)
+    t = dict(s, c=np.linspace(0.01, 0.02, s["ij"].shape[0]).astype(np.float32))
+    with pytest.raises(ms.MsError) as e:
+        ms.Sim(t, p, kernel="lattice")
+    assert "dashpot" in str(e.value)

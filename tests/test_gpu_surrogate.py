@@ -27,7 +27,9 @@ def test_surrogate_screen_beats_random_selection(ms):
     rng = np.random.default_rng(4)
     side, nsteps = 8, 20000               # 2 s rollouts, as the screening workload specifies
     n_train, n_val, n_cand = 16384, 2048, 16384
-    mats = rng.integers(0, 4, size=(n_train + n_val, side, side, side)).astype(np.uint8)
+    # each design kept to its largest face-connected body (loose voxels would be
+    # simulated as separate bodies and blur the label)
+    mats = synth.largest_components(rng.integers(0, 4, size=(n_train + n_val, side, side, side)).astype(np.uint8))
     args = (synth.VOXEL_MATERIALS, synth.VOXEL_FREQ, synth.VOXEL_EDGE, synth.VOXEL_MASS, synth.voxel_params())
     y = screen.simulate_travel(mats, *args, nsteps=nsteps)
     assert np.all(np.isfinite(y))
@@ -35,7 +37,7 @@ def test_surrogate_screen_beats_random_selection(ms):
     with net:
         pv = screen.predict(net, mats[n_train:], mu, sd)
         r2 = screen.r2(pv, y[n_train:])
-        cand = rng.integers(0, 4, size=(n_cand, side, side, side)).astype(np.uint8)
+        cand = synth.largest_components(rng.integers(0, 4, size=(n_cand, side, side, side)).astype(np.uint8))
         top, _ = screen.screen(net, cand, mu, sd, top_frac=0.01)
     k = len(top)
     y_top = screen.simulate_travel(cand[top], *args, nsteps=nsteps)

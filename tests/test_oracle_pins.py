@@ -496,3 +496,18 @@ def test_quasi_uniform_lattice_shape():
     deg = np.bincount(s["ij"].ravel(), minlength=600)
     assert deg.max() <= 26 and deg.min() >= 1
     assert np.all(s["ij"][:, 0] < s["ij"][:, 1])
+
+
+def test_batched_largest_components_equal_the_per_design_rule():
+    """synth.largest_components (one labelling over a batch of designs) keeps
+    exactly the component that the single-design rule keeps, ties and empty
+    designs included."""
+    rng = np.random.default_rng(12)
+    mats = rng.integers(0, 4, size=(400, 5, 6, 7)).astype(np.uint8)
+    mats[3] = 0
+    mats[7] = 0; mats[7, 0, 0, 0] = 2; mats[7, 4, 5, 6] = 1      # a tie: two single voxels
+    got = synth.largest_components(mats, chunk=64)
+    for m, g in zip(mats, got):
+        want = np.where(synth._largest_component(m > 0), m, 0)
+        assert np.array_equal(g, want)
+    assert got[7, 0, 0, 0] == 2 and got[7, 4, 5, 6] == 0

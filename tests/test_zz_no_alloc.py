@@ -94,9 +94,14 @@ def test_noalloc_matches_oracle_and_regular_step_on_two_calls_in_a_row(ms, ora):
     xa, va = step_noalloc(ms, s, p, 100, x0, v0)                  # first call
     xb, vb = step_noalloc(ms, s, p, 100, torch.tensor(xa, dtype=torch.float32, device="cuda"),
                           torch.tensor(va, dtype=torch.float32, device="cuda"))   # second call
-    xo1, vo1 = ora.run(s, f32p(p), 100)
-    xo2, vo2 = ora.run(s, f32p(p), 100, n0=100, x=xo1, v=vo1)
-    assert xo2[:, 2].min() < -1e-5 or xo1[:, 2].min() < -1e-5     # contact really happened
+    xo, vo, zmin, snaps = s["x"], s["v"], np.inf, []
+    for c in range(20):                                           # oracle in chunks, watching contact
+        xo, vo = ora.run(s, f32p(p), 10, n0=10 * c, x=xo, v=vo)
+        zmin = min(zmin, xo[:, 2].min())
+        if c in (9, 19):
+            snaps.append((xo, vo))
+    (xo1, vo1), (xo2, vo2) = snaps
+    assert zmin < -1e-5                                           # contact really happened
     m = s["m"].astype(np.float64)
     for got, want in ((xa, xo1), (xb, xo2)):
         assert np.abs(got - want).max() <= 1e-4 * size, (np.abs(got - want).max(), size)
@@ -132,10 +137,12 @@ def test_noalloc_anchored_cantilever_matches_oracle(ms, ora, nsteps):
     assert np.array_equal(xg[anchored], s["x"][anchored].astype(np.float64))
     assert np.all(vg[anchored] == 0.0)
     assert np.abs(xg - xo).max() <= 1e-5 * body_size(s), np.abs(xg - xo).max()
-    # velocities: the first steps start from identical FP32 positions, so only
-    # the force arithmetic rounds; later the FP32 rounding of the 0.4 m
-    # coordinates (ulp 3e-8 m) feeds the stiffest mode (w ~ 1.3e4 1/s)
-    vgate = 1e-5 if nsteps <= 2 else 2e-3
+    # velocities: the first step starts from identical FP32 positions, so only
+    # the force arithmetic rounds; from the second step on, the FP32 rounding
+    # of the 0.4 m coordinates (ulp 3e-8 m) is felt through up to 26 springs of
+    # 1e4 N/m on 1e-3 kg masses (about 2e-4 m/s per step) and then through the
+    # stiffest mode (w ~ 1.3e4 1/s)
+    vgate = 1e-5 if nsteps == 1 else 2e-3
     assert np.abs(vg - vo).max() <= vgate, np.abs(vg - vo).max()
 
 
