@@ -116,6 +116,7 @@ struct ms_sim {
     int32_t *d_perm = nullptr;          // internal -> caller index (layouts indexed 0..N-1)
     int32_t *d_cidx = nullptr;          // caller -> internal index (the lattice layout)
     ms::LatticeArgs lat{};              // lattice layout (kernel 4): stiffness arrays, rest lengths, extents
+    ms::LatticeMaps lat_maps;           // its tensor maps (TMA descriptors) per state buffer
     int64_t lat_cells = 0;              // padded cells of the lattice layout
     float *stage = nullptr;             // (N,3)*2 floats for host copies
     int *err = nullptr;
@@ -213,7 +214,7 @@ struct LatticeShape {
     int nx = 0, ny = 0, nz = 0, nbx = 0, nby = 0, nbz = 0, X = 0, Y = 0, Z = 0;
     int64_t P = 0;                    // padded cells
     std::vector<int32_t> cidx;        // caller mass -> padded index
-    std::vector<float> kf;            // [13][P] stiffness, -1 = no spring
+    std::vector<float> kf;            // [13][P] stiffness, NaN = no spring
     float L[ms::kLatDirs] = {};
     float c = 0.f;
     std::vector<double> sumK;         // per caller mass: sum of the k of its springs
@@ -265,7 +266,9 @@ bool lattice_shape(int32_t N, const float *x0, int64_t S, const int32_t *ij, con
     L.nbx = (L.nx + ms::kBrickX - 1) / ms::kBrickX;
     L.nby = (L.ny + ms::kBrickY - 1) / ms::kBrickY;
     L.nbz = (L.nz + ms::kBrickZ - 1) / ms::kBrickZ;
-    L.X = L.nbx * ms::kBrickX + 2; L.Y = L.nby * ms::kBrickY + 2; L.Z = L.nbz * ms::kBrickZ + 2;
+    // one guard cell below each axis; above, one in y and z and three in x, so
+    // that a row of the float arrays is a multiple of 16 bytes (tensor copies)
+    L.X = L.nbx * ms::kBrickX + 4; L.Y = L.nby * ms::kBrickY + 2; L.Z = L.nbz * ms::kBrickZ + 2;
     L.P = (int64_t)L.X * L.Y * L.Z;
     if (L.P >= (int64_t)INT32_MAX / 2) { why = "the padded lattice is too large for 32-bit cell indices"; return false; }
     const int64_t XY = (int64_t)L.X * L.Y;
@@ -283,7 +286,7 @@ bool lattice_shape(int32_t N, const float *x0, int64_t S, const int32_t *ij, con
     // springs: neighbouring cells, one per pair, one rest length per direction, one dashpot value
     L.c = c ? c[0] : c_uniform;
     bool have_L[ms::kLatDirs] = {};
-    L.kf.assign((size_t)ms::kLatDirs * (size_t)L.P, -1.0f);
+    L.kf.assign((size_t)ms::kLatDirs * (size_t)L.P, std::numeric_limits<float>::quiet_NaN());
     L.sumK.assign(N, 0.0);
     for (int64_t e = 0; e < S; ++e) {
         int32_t a = ij[2 * e], b = ij[2 * e + 1];
@@ -307,7 +310,7 @@ bool lattice_shape(int32_t N, const float *x0, int64_t S, const int32_t *ij, con
         else if (L.L[d] != Lv) { why = "rest lengths differ within one lattice direction"; return false; }
         if (c && c[e] != L.c) { why = "the dashpot coefficient differs between springs"; return false; }
         float &slot = L.kf[(size_t)d * (size_t)L.P + (size_t)L.cidx[a]];
-        if (slot >= 0.0f) { why = "two springs join the same pair of masses"; return false; }
+        if (slot == slot) { why = "two springs join the same pair of masses"; return false; }
         slot = k[e];
         L.sumK[a] += k[e]; L.sumK[b] += k[e];
     }
@@ -381,9 +384,13 @@ ms_status build_lattice(ms_sim *s, const ms_params *p, int32_t N, const float *x
     if ((st = upload(s, &s->d_cidx, L.cidx.data(), (size_t)N)) != MS_OK) return st;
     if ((st = upload<float>(s, &s->stage, nullptr, (size_t)N * 6)) != MS_OK) return st;
     if (p->integrator == 3) {
+        // stage states: cells without a mass are never written, and the next
+        // stage stages them as partners, so they start (and stay) zero
         for (int q = 0; q < 2; ++q) {
             if ((st = upload<float4>(s, &s->rk_a[q], nullptr, P)) != MS_OK) return st;
             if ((st = upload<float2>(s, &s->rk_b[q], nullptr, P)) != MS_OK) return st;
+            MS_CUDA_TRY(cudaMemsetAsync(s->rk_a[q], 0, sizeof(float4) * P, s->stream));
+            MS_CUDA_TRY(cudaMemsetAsync(s->rk_b[q], 0, sizeof(float2) * P, s->stream));
         }
         if ((st = upload<float4>(s, &s->rk_acc, nullptr, 2 * P)) != MS_OK) return st;
     }
@@ -394,6 +401,11 @@ ms_status build_lattice(ms_sim *s, const ms_params *p, int32_t N, const float *x
     }
     if ((st = upload<int>(s, &s->err, nullptr, 2)) != MS_OK) return st;
     MS_CUDA_TRY(cudaMemsetAsync(s->err, 0, 2 * sizeof(int), s->stream));
+    for (int q = 0; q < 2; ++q) {
+        if ((st = ms::lattice_maps_add(s->lat_maps, s->lat, s->sa[q], s->sb[q])) != MS_OK) return st;
+        if (p->integrator == 3 && (st = ms::lattice_maps_add(s->lat_maps, s->lat, s->rk_a[q], s->rk_b[q])) != MS_OK)
+            return st;
+    }
     MS_CUDA_TRY(cudaStreamSynchronize(s->stream));      // host arrays must outlive the copies
     return MS_OK;
 }
@@ -1106,7 +1118,8 @@ ms_status ms_step(ms_sim *s, int32_t nsteps)
                 a.sb = q == 0 ? s->sb[s->cur] : s->rk_b[(q - 1) & 1];
                 a.oa = q == 3 ? s->sa[s->cur ^ 1] : s->rk_a[q & 1];
                 a.ob = q == 3 ? s->sb[s->cur ^ 1] : s->rk_b[q & 1];
-                MS_CUDA_TRY(lattice ? ms::launch_step_lattice(a, s->lat, s->stream) : ms::launch_step(a, s->stream));
+                MS_CUDA_TRY(lattice ? ms::launch_step_lattice(a, s->lat, s->lat_maps, s->n_sms, s->stream)
+                                    : ms::launch_step(a, s->stream));
             }
         } else {
             if (s->actuated) {
@@ -1115,7 +1128,8 @@ ms_status ms_step(ms_sim *s, int32_t nsteps)
             }
             a.sa = s->sa[s->cur]; a.sb = s->sb[s->cur];
             a.oa = s->sa[s->cur ^ 1]; a.ob = s->sb[s->cur ^ 1];
-            MS_CUDA_TRY(lattice ? ms::launch_step_lattice(a, s->lat, s->stream) : ms::launch_step(a, s->stream));
+            MS_CUDA_TRY(lattice ? ms::launch_step_lattice(a, s->lat, s->lat_maps, s->n_sms, s->stream)
+                                    : ms::launch_step(a, s->stream));
         }
         s->cur ^= 1;
         if (s->tr_n > 0 && s->tr_count < s->tr_cap) {

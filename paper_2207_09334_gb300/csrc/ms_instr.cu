@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kTileMasses) k_energy_tiled(const EnergyArgs a
 }
 
 // lattice layout: one CTA per brick, one thread per cell; each spring once,
-// from the cell it leaves in a forward direction (k < 0: no spring)
+// from the cell it leaves in a forward direction (k = NaN: no spring)
 __global__ void __launch_bounds__(kBrickCells) k_energy_lattice(const EnergyArgs a, const LatticeArgs g)
 {
     const int tid = threadIdx.x;
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kBrickCells) k_energy_lattice(const EnergyArgs
 #pragma unroll
         for (int d = 0; d < kLatDirs; ++d) {
             const float k = __ldg(g.kf[d] + i);
-            if (k < 0.0f) continue;
+            if (!(k == k)) continue;
             const float4 xj = __ldg(&a.sa[i + lat_dx(d) + g.X * (lat_dy(d) + g.Y * lat_dz(d))]);
             const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
             const float e = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - g.L[d];

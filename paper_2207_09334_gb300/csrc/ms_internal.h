@@ -1,6 +1,7 @@
 // ms_internal.h -- structures shared by the host builder and the step kernels
 // of the mass-spring library (library-internal; not part of the C ABI).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -129,15 +130,16 @@ struct StepArgs {
 //     padded lattice index; the caller's mass c sits at cidx[c].
 //   * Each of the 13 forward directions d (lat_dx/dy/dz below) has its own
 //     array over the padded cells: kf[d][i] = k of the spring from cell i to
-//     cell i + off(d), or -1 where there is none (a missing pair, a cell
+//     cell i + off(d), or NaN where there is none (a missing pair, a cell
 //     without mass, the guard band).
 //   * Cells without a mass have w = NaN and a zero state; no kernel integrates
 //     them.
 constexpr int kKernelLattice = 4;
-constexpr int kBrickX = 16, kBrickY = 8, kBrickZ = 4;
-constexpr int kBrickCells = kBrickX * kBrickY * kBrickZ;        // 512: one thread per cell
+constexpr int kBrickX = 16, kBrickY = 8, kBrickZ = 8;
+constexpr int kBrickCells = kBrickX * kBrickY * kBrickZ;        // 1024 cells per brick
+constexpr int kLatThreads = kBrickCells / 2;                    // 512: each thread two cells stacked in z
 constexpr int kHaloX = kBrickX + 2, kHaloY = kBrickY + 2, kHaloZ = kBrickZ + 2;
-constexpr int kHaloCells = kHaloX * kHaloY * kHaloZ;            // 1080 cells staged per brick
+constexpr int kHaloCells = kHaloX * kHaloY * kHaloZ;            // 1800 cells staged per brick
 constexpr int kLatDirs = 13;
 // forward direction d: (1,0,0); then (dx,1,0) for dx = -1..1; then (dx,dy,1) for
 // dy = -1..1, dx = -1..1 -- the 13 offsets that are positive in (z, y, x) order
@@ -153,7 +155,23 @@ struct LatticeArgs {
     int X, Y, Z;                 // padded extents (cells)
     int nbx, nby, nbz;           // bricks per axis
 };
-cudaError_t launch_step_lattice(const StepArgs &a, const LatticeArgs &g, cudaStream_t st);
+// Tensor maps (TMA descriptors) of the lattice layout: one pair per state
+// buffer that a step reads -- its (x, y, z, vx) array as a 4-D float box and
+// its (vy, vz) array as a 3-D box of 8-byte elements -- and one of the 13
+// stiffness arrays as a 4-D float box (for L2 prefetch).
+struct LatticeMaps {
+    static constexpr int kMax = 8;
+    int n = 0;
+    const void *sa[kMax] = {};
+    const void *sb[kMax] = {};
+    CUtensorMap a[kMax];
+    CUtensorMap b[kMax];
+    CUtensorMap k;
+};
+// adds the pair of state buffer (sa, sb); the stiffness map on the first call
+ms_status lattice_maps_add(LatticeMaps &m, const LatticeArgs &g, const float4 *sa, const float2 *sb);
+cudaError_t launch_step_lattice(const StepArgs &a, const LatticeArgs &g, const LatticeMaps &m, int n_sms,
+                                cudaStream_t st);
 
 // Persistent grid step (ms_step.cu): nsteps steps of the tiled layout in one
 // cooperative launch; buffer n & 1 holds the state at step n of the call.

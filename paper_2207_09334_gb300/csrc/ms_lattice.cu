@@ -3,105 +3,348 @@
 // For a box lattice with 26-neighbourhood springs (the benchmark's
 // throughput lattice; the paper's voxel and cubic lattices of "Generating a
 // Lattice"), the topology and the rest lengths follow from the lattice
-// itself, so the step reads per spring only its stiffness.  That halves the
-// bytes of the general (tiled) layout, which stores partner indices and rest
-// lengths and lists every spring at both of its masses.
+// itself, so the step reads per spring only its stiffness.  That is a
+// quarter of the spring bytes of the general (tiled) layout, which stores
+// partner indices and rest lengths and lists every spring at both masses.
 //
-// One CTA per brick of 16 x 8 x 4 cells (one thread per cell):
-//   * the state of the brick and of its one-cell halo (18 x 10 x 6 cells) is
+// Bricks of 16 x 8 x 8 cells; 512 threads per brick, each thread two cells
+// stacked in z (a at z, b at z + 1):
+//   * the state of the brick and of its one-cell halo (18 x 10 x 10 cells) is
 //     staged in shared memory; a partner in direction d is then the shared
 //     entry at a constant offset, with no index stored anywhere;
-//   * each thread evaluates its cell's 26 springs (eq. 2's Hooke term plus
-//     the axial dashpot, reading R2): the 13 forward springs with k from its
-//     own cell's arrays kf[d][i], the 13 backward springs with k from the
-//     partner's arrays (kb[d][i] = kf[d][i - off(d)], a read that hits L1 or
-//     L2 because the partner sits in this brick or in one processed just
-//     before);
+//   * the CTAs are persistent (two per multiprocessor) and walk the bricks
+//     in raster order; while the threads compute brick n, two TMA tensor
+//     copies (one elected thread, completing on an mbarrier) stage brick
+//     n + 1's block into the other shared buffer, and a TMA prefetch brings
+//     its stiffness into L2, so no warp waits for DRAM at a brick's start;
+//   * a thread walks the 3 x 3 columns around its pair and reads the four
+//     cells z - 1 .. z + 2 of each column once: they are partners of a (z - 1
+//     .. z + 1) and of b (z .. z + 2), so each shared-memory read of a partner
+//     state serves both cells (the shared-memory pipe, not DRAM, bounds a
+//     one-cell-per-thread form), and the spring between a and b is evaluated
+//     once;
+//   * each spring term is eq. 2's Hooke term plus the axial dashpot (reading
+//     R2), written as f = [k (1 - L/l) + c (dv . d)/l^2] d with one hardware
+//     reciprocal square root; k comes from the cell's own array for a forward
+//     direction and from the partner's (kb[d][i] = kf[d][i - off(d)]) for a
+//     backward one;
 //   * then gravity, external force, ground contact, damping and the update of
-//     the cell's mass (integrate_mass, shared with the other step kernels), and
-//     the new state goes to the other buffer (Algorithm 1's synchronisation
-//     is the kernel boundary).
-// Every spring is evaluated at both ends; the two evaluations are exact
-// negatives, and each mass sums its springs in a fixed order (forward
-// directions 0..12, then backward 0..12), so runs are bit-reproducible.
+//     both masses (integrate_mass, shared with the other step kernels); the
+//     new state goes to the other buffer (Algorithm 1's synchronisation is
+//     the kernel boundary).
+// Each mass sums its springs in a fixed order, so runs are bit-reproducible.
+#include <cudaTypedefs.h>
+
 #include "ms_internal.h"
 #include "ms_device.cuh"
+
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <string>
 
 namespace ms {
 namespace {
 
-// spring_term_packed for a lattice spring with stiffness k; k < 0 marks a
-// spring that does not exist (its partner cell may hold no mass), which adds
-// nothing.  For an existing spring the result is spring_term_packed's.
-__device__ __forceinline__ void lattice_spring(const float4 xi, const float4 vi, const float4 pa, const float2 pb,
-                                               float k, float L, float c, float &fx, float &fy, float &fz)
+// shared-memory offset of the cell (dx, dy, dz) away inside the staged block
+__host__ __device__ constexpr int halo_off(int dx, int dy, int dz) { return dx + kHaloX * (dy + kHaloY * dz); }
+
+// forward direction index of (dx, dy, dz) (lat_dx/dy/dz), or -1 for a backward one
+__host__ __device__ constexpr int fwd_index(int dx, int dy, int dz)
 {
-    const float dx = pa.x - xi.x, dy = pa.y - xi.y, dz = pa.z - xi.z;
-    const float l2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float il = rsqrt_hw(l2);
-    const float l = l2 * il;
-    const float rv = fmaf(pa.w - vi.x, dx, fmaf(pb.x - vi.y, dy, (pb.y - vi.z) * dz)) * il;
-    float fs = fmaf(k, l - L, c * rv) * il;
-    fs = (l2 > 0.0f && k >= 0.0f) ? fs : 0.0f;
-    fx = fmaf(fs, dx, fx); fy = fmaf(fs, dy, fy); fz = fmaf(fs, dz, fz);
+    return dz == 1 ? 4 + (dx + 1) + 3 * (dy + 1)
+         : (dz == 0 && dy == 1) ? dx + 2
+         : (dz == 0 && dy == 0 && dx == 1) ? 0
+         : -1;
 }
 
-// shared-memory offset of the partner in direction d inside the staged block
-__host__ __device__ constexpr int halo_off(int d) { return lat_dx(d) + kHaloX * (lat_dy(d) + kHaloY * lat_dz(d)); }
+// k of the spring of cell i in direction (dx, dy, dz): from the cell's own
+// array for a forward direction, from the partner's for a backward one
+template <int DX, int DY, int DZ>
+__device__ __forceinline__ float spring_k(const LatticeArgs &g, int i)
+{
+    constexpr int f = fwd_index(DX, DY, DZ);
+    constexpr int b = fwd_index(-DX, -DY, -DZ);
+    if constexpr (f >= 0) return __ldg(g.kf[f] + i);
+    else return __ldg(g.kb[b] + i);
+}
+
+template <int DX, int DY, int DZ>
+__device__ __forceinline__ float spring_L(const LatticeArgs &g)
+{
+    constexpr int f = fwd_index(DX, DY, DZ);
+    return g.L[f >= 0 ? f : fwd_index(-DX, -DY, -DZ)];
+}
+
+// Magnitude s of the spring term f = s d on the mass at (xi, vi) from the
+// partner (pa, pb) = ((x, y, z, vx), (vy, vz)), d = x_partner - x_self:
+//   s = k (l - L)/l + c (v_partner - v_self) . d / l^2
+// k = NaN (no spring) or a spring of zero length give s = NaN, returned as 0.
+__device__ __forceinline__ float lattice_term(const float4 xi, const float3 vi, const float4 pa, const float2 pb,
+                                              float k, float L, float c, float &dx, float &dy, float &dz)
+{
+    dx = pa.x - xi.x; dy = pa.y - xi.y; dz = pa.z - xi.z;
+    const float l2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float il = rsqrt_hw(l2);
+    const float t = fmaf(-(k * L), il, k);
+    const float dot = fmaf(pa.w - vi.x, dx, fmaf(pb.x - vi.y, dy, (pb.y - vi.z) * dz));
+    const float s = fmaf(c * dot, il * il, t);
+    return s == s ? s : 0.0f;
+}
+
+__device__ __forceinline__ void add_term(const float4 xi, const float3 vi, const float4 pa, const float2 pb, float k,
+                                         float L, float c, float &fx, float &fy, float &fz)
+{
+    float dx, dy, dz;
+    const float s = lattice_term(xi, vi, pa, pb, k, L, c, dx, dy, dz);
+    fx = fmaf(s, dx, fx); fy = fmaf(s, dy, fy); fz = fmaf(s, dz, fz);
+}
+
+// Springs of the pair (a at z, b at z + 1) into the column (DX, DY): partner
+// cells z - 1 .. z + 2 read once each.  The centre column (0, 0) holds a and b
+// themselves: a's spring to z - 1, the a-b spring once, b's spring to z + 2.
+template <int DX, int DY>
+__device__ __forceinline__ void column(const LatticeArgs &g, const float4 *spa, const float2 *spb, int sa_, int ia,
+                                       int ib, const float4 xa, const float3 va, const float4 xb, const float3 vb,
+                                       float3 &Fa, float3 &Fb)
+{
+    const int c0 = sa_ + halo_off(DX, DY, 0);
+    const float c = g.c;
+    {   // z - 1: a only
+        const float4 p = spa[c0 - halo_off(0, 0, 1)];
+        const float2 q = spb[c0 - halo_off(0, 0, 1)];
+        add_term(xa, va, p, q, spring_k<DX, DY, -1>(g, ia), spring_L<DX, DY, -1>(g), c, Fa.x, Fa.y, Fa.z);
+    }
+    if constexpr (DX != 0 || DY != 0) {
+        {   // z: a in-plane, b one below
+            const float4 p = spa[c0];
+            const float2 q = spb[c0];
+            add_term(xa, va, p, q, spring_k<DX, DY, 0>(g, ia), spring_L<DX, DY, 0>(g), c, Fa.x, Fa.y, Fa.z);
+            add_term(xb, vb, p, q, spring_k<DX, DY, -1>(g, ib), spring_L<DX, DY, -1>(g), c, Fb.x, Fb.y, Fb.z);
+        }
+        {   // z + 1: a one above, b in-plane
+            const float4 p = spa[c0 + halo_off(0, 0, 1)];
+            const float2 q = spb[c0 + halo_off(0, 0, 1)];
+            add_term(xa, va, p, q, spring_k<DX, DY, 1>(g, ia), spring_L<DX, DY, 1>(g), c, Fa.x, Fa.y, Fa.z);
+            add_term(xb, vb, p, q, spring_k<DX, DY, 0>(g, ib), spring_L<DX, DY, 0>(g), c, Fb.x, Fb.y, Fb.z);
+        }
+    } else {
+        // the a-b spring, once: +s d on a, -s d on b
+        float dx, dy, dz;
+        const float4 pb4 = make_float4(xb.x, xb.y, xb.z, vb.x);
+        const float s = lattice_term(xa, va, pb4, make_float2(vb.y, vb.z), __ldg(g.kf[fwd_index(0, 0, 1)] + ia),
+                                     g.L[fwd_index(0, 0, 1)], c, dx, dy, dz);
+        Fa.x = fmaf(s, dx, Fa.x); Fa.y = fmaf(s, dy, Fa.y); Fa.z = fmaf(s, dz, Fa.z);
+        Fb.x = fmaf(-s, dx, Fb.x); Fb.y = fmaf(-s, dy, Fb.y); Fb.z = fmaf(-s, dz, Fb.z);
+    }
+    {   // z + 2: b only
+        const float4 p = spa[c0 + halo_off(0, 0, 2)];
+        const float2 q = spb[c0 + halo_off(0, 0, 2)];
+        add_term(xb, vb, p, q, spring_k<DX, DY, 1>(g, ib), spring_L<DX, DY, 1>(g), c, Fb.x, Fb.y, Fb.z);
+    }
+}
+
+// all springs of the pair (a, b), column by column
+__device__ __forceinline__ void pair_forces(const LatticeArgs &g, const float4 *spa, const float2 *spb, int s0, int ia,
+                                            int ib, const float4 xa, const float3 va, const float4 xb,
+                                            const float3 vb, float3 &Fa, float3 &Fb)
+{
+    Fa = make_float3(0.f, 0.f, 0.f);
+    Fb = Fa;
+    column<-1, -1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
+    column< 0, -1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
+    column< 1, -1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
+    column<-1,  0>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
+    column< 0,  0>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
+    column< 1,  0>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
+    column<-1,  1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
+    column< 0,  1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
+    column< 1,  1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
+}
+
+// one staged block: (x, y, z, vx) then (vy, vz) of the 18 x 10 x 10 cells
+constexpr uint32_t kStageA = kHaloCells * sizeof(float4);       // 28 800 bytes (a multiple of 128)
+constexpr uint32_t kStageB = kHaloCells * sizeof(float2);       // 14 400 bytes
+constexpr uint32_t kStageCopied = kStageA + kStageB;            // bytes the two copies of a stage bring
+constexpr uint32_t kStageBytes = (kStageCopied + 127) / 128 * 128;   // stage stride: copies land 128-byte aligned
+static_assert(kStageA % 128 == 0 && kStageBytes % 128 == 0, "tensor copies need 128-byte aligned destinations");
+constexpr int kLatCtasPerSm = 2;
 
 template <bool HAS_FEXT, bool RK4>
-__global__ void __launch_bounds__(kBrickCells, 3) k_step_lattice(const StepArgs a, const LatticeArgs g)
+__global__ void __launch_bounds__(kLatThreads, kLatCtasPerSm)
+k_step_lattice(const StepArgs a, const LatticeArgs g, const __grid_constant__ CUtensorMap map_a,
+               const __grid_constant__ CUtensorMap map_b, const __grid_constant__ CUtensorMap map_k)
 {
-    __shared__ float4 spa[kHaloCells];     // (x, y, z, vx) of the brick and its halo
-    __shared__ float2 spb[kHaloCells];     // (vy, vz)
+    extern __shared__ __align__(128) unsigned char dyn[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int give_up;
     const int tid = threadIdx.x;
-    const int b = blockIdx.x;
-    const int bx = b % g.nbx, byz = b / g.nbx, by = byz % g.nby, bz = byz / g.nby;
+    const int nbricks = g.nbx * g.nby * g.nbz;
     const int XY = g.X * g.Y;
-    // padded index of the staged block's first cell (the brick's origin less one cell on each axis)
-    const int base = bx * kBrickX + g.X * (by * kBrickY) + XY * (bz * kBrickZ);
-    for (int e = tid; e < kHaloCells; e += kBrickCells) {
-        const int hx = e % kHaloX, hy = (e / kHaloX) % kHaloY, hz = e / (kHaloX * kHaloY);
-        const int gi = base + hx + g.X * hy + XY * hz;
-        spa[e] = __ldg(&a.sa[gi]);
-        spb[e] = __ldg(&a.sb[gi]);
+    // brick b: its staged block starts at padded cell (bx*16, by*8, bz*8)
+    auto origin = [&](int b, int &ox, int &oy, int &oz) {
+        const int bx = b % g.nbx, byz = b / g.nbx;
+        ox = bx * kBrickX; oy = (byz % g.nby) * kBrickY; oz = (byz / g.nby) * kBrickZ;
+    };
+    auto issue = [&](int b, int stage) {          // one thread: stage brick b, prefetch its stiffness
+        int ox, oy, oz;
+        origin(b, ox, oy, oz);
+        unsigned char *dst = dyn + (size_t)stage * kStageBytes;
+        mbar_expect_tx(&bar[stage], kStageCopied);
+        tma_load_4d(dst, &map_a, 0, ox, oy, oz, &bar[stage]);
+        tma_load_3d(dst + kStageA, &map_b, ox, oy, oz, &bar[stage]);
+        tma_prefetch_4d(&map_k, ox, oy, oz, 0);
+    };
+    if (tid == 0) {
+        give_up = 0;
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
     }
     __syncthreads();
-    const int cx = tid % kBrickX, cy = (tid / kBrickX) % kBrickY, cz = tid / (kBrickX * kBrickY);
-    const int s = (cx + 1) + kHaloX * ((cy + 1) + kHaloY * (cz + 1));
-    const int i = base + (cx + 1) + g.X * (cy + 1) + XY * (cz + 1);
-    const float w = __ldg(&a.w[i]);
-    if (w != w) return;                    // a cell without a mass
-    const float4 p = spa[s];
-    const float2 q = spb[s];
-    const float4 xi = make_float4(p.x, p.y, p.z, w), vi = make_float4(p.w, q.x, q.y, 0.f);
-    float fx = 0.f, fy = 0.f, fz = 0.f;
-#pragma unroll
-    for (int d = 0; d < kLatDirs; ++d)
-        lattice_spring(xi, vi, spa[s + halo_off(d)], spb[s + halo_off(d)], __ldg(g.kf[d] + i), g.L[d], g.c, fx, fy, fz);
-#pragma unroll
-    for (int d = 0; d < kLatDirs; ++d)
-        lattice_spring(xi, vi, spa[s - halo_off(d)], spb[s - halo_off(d)], __ldg(g.kb[d] + i), g.L[d], g.c, fx, fy, fz);
-    float4 xn, vn;
-    integrate_mass<HAS_FEXT, RK4>(a, i, xi, vi, fx, fy, fz, xn, vn);
-    store_mass(a, i, xn, vn);
+    if (tid == 0 && (int)blockIdx.x < nbricks) issue(blockIdx.x, 0);
+    const int cx = tid % kBrickX, cy = (tid / kBrickX) % kBrickY, cz = 2 * (tid / (kBrickX * kBrickY));
+    const int s0 = (cx + 1) + kHaloX * ((cy + 1) + kHaloY * (cz + 1));     // cell a; b is one layer up
+    int n = 0;
+    for (int b = blockIdx.x; b < nbricks; b += gridDim.x, ++n) {
+        const int stage = n & 1;
+        if (tid == 0 && b + (int)gridDim.x < nbricks) {
+            fence_proxy_async();                  // the other buffer's reads (previous brick) are done
+            issue(b + gridDim.x, stage ^ 1);
+        }
+        int ox, oy, oz;
+        origin(b, ox, oy, oz);
+        const int ia = (ox + cx + 1) + g.X * (oy + cy + 1) + XY * (oz + cz + 1), ib = ia + XY;
+        const float wa = __ldg(&a.w[ia]), wb = __ldg(&a.w[ib]);
+        if (!mbar_wait(&bar[stage], (n >> 1) & 1)) give_up = 1;
+        const float4 *spa = reinterpret_cast<const float4 *>(dyn + (size_t)stage * kStageBytes);
+        const float2 *spb = reinterpret_cast<const float2 *>(dyn + (size_t)stage * kStageBytes + kStageA);
+        if ((wa == wa || wb == wb) && !give_up) {
+            const float4 p = spa[s0];
+            const float2 q = spb[s0];
+            const float4 xa = make_float4(p.x, p.y, p.z, wa);
+            const float3 va = make_float3(p.w, q.x, q.y);
+            const float4 r = spa[s0 + halo_off(0, 0, 1)];
+            const float2 t = spb[s0 + halo_off(0, 0, 1)];
+            const float4 xb = make_float4(r.x, r.y, r.z, wb);
+            const float3 vb = make_float3(r.w, t.x, t.y);
+            float3 Fa, Fb;
+            pair_forces(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
+            float4 xn, vn;
+            if (wa == wa) {
+                integrate_mass<HAS_FEXT, RK4>(a, ia, xa, make_float4(va.x, va.y, va.z, 0.f), Fa.x, Fa.y, Fa.z, xn, vn);
+                store_mass(a, ia, xn, vn);
+            }
+            if (wb == wb) {
+                integrate_mass<HAS_FEXT, RK4>(a, ib, xb, make_float4(vb.x, vb.y, vb.z, 0.f), Fb.x, Fb.y, Fb.z, xn, vn);
+                store_mass(a, ib, xn, vn);
+            }
+        }
+        __syncthreads();                          // this buffer is consumed before it is refilled
+        if (give_up) break;
+    }
+    if (give_up && tid == 0) {
+        // a stage never landed: flag it, and give the copy issued for the next
+        // brick a bounded chance to land before the shared memory is released
+        atomicOr(a.err, kErrTimeout);
+        mbar_wait(&bar[(n + 1) & 1], ((n + 1) >> 1) & 1);
+    }
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+ms_status encode(CUtensorMap *map, CUtensorMapDataType type, int rank, const void *ptr, const cuuint64_t *dims,
+                 const cuuint64_t *strides, const cuuint32_t *box)
+{
+    auto fn = tensor_map_encoder();
+    if (!fn) return fail(MS_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    if ((uintptr_t)ptr & 15) return fail(MS_ERR_CUDA, "lattice tensor map: base not 16-byte aligned");
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const CUresult r = fn(map, type, (cuuint32_t)rank, const_cast<void *>(ptr), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(MS_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return MS_OK;
 }
 
 }  // namespace
 
-cudaError_t launch_step_lattice(const StepArgs &a, const LatticeArgs &g, cudaStream_t st)
+ms_status lattice_maps_add(LatticeMaps &m, const LatticeArgs &g, const float4 *sa, const float2 *sb)
 {
-    const long long grid = (long long)g.nbx * g.nby * g.nbz;
-    if (grid <= 0) return cudaSuccess;
-    if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
-    const bool hf = a.fext != nullptr;
-    if (a.integrator == 3) {
-        if (hf) k_step_lattice<true, true><<<(unsigned)grid, kBrickCells, 0, st>>>(a, g);
-        else k_step_lattice<false, true><<<(unsigned)grid, kBrickCells, 0, st>>>(a, g);
-    } else {
-        if (hf) k_step_lattice<true, false><<<(unsigned)grid, kBrickCells, 0, st>>>(a, g);
-        else k_step_lattice<false, false><<<(unsigned)grid, kBrickCells, 0, st>>>(a, g);
+    const cuuint64_t X = (cuuint64_t)g.X, Y = (cuuint64_t)g.Y, Z = (cuuint64_t)g.Z;
+    ms_status st;
+    if (m.n == 0) {
+        // the 13 stiffness arrays, one allocation P floats apart: (x, y, z, d);
+        // prefetch box = the cells whose k a brick reads, every direction
+        const cuuint64_t dims[4] = {X, Y, Z, (cuuint64_t)kLatDirs};
+        const cuuint64_t strides[3] = {X * 4, X * Y * 4, X * Y * Z * 4};
+        // x rounded up to 16 bytes; z from one below the brick to its top layer
+        // (a spring's k is read at its lower-or-equal end, never above the brick)
+        const cuuint32_t box[4] = {kHaloX + 2, kHaloY, kBrickZ + 1, (cuuint32_t)kLatDirs};
+        if ((st = encode(&m.k, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g.kf[0], dims, strides, box)) != MS_OK) return st;
     }
+    if (m.n >= LatticeMaps::kMax) return fail(MS_ERR_ARG, "too many lattice state buffers");
+    {   // (x, y, z, vx): 4 floats per cell
+        const cuuint64_t dims[4] = {4, X, Y, Z};
+        const cuuint64_t strides[3] = {16, X * 16, X * Y * 16};
+        const cuuint32_t box[4] = {4, kHaloX, kHaloY, kHaloZ};
+        if ((st = encode(&m.a[m.n], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, sa, dims, strides, box)) != MS_OK) return st;
+    }
+    {   // (vy, vz): one 8-byte element per cell (copied verbatim)
+        const cuuint64_t dims[3] = {X, Y, Z};
+        const cuuint64_t strides[2] = {X * 8, X * Y * 8};
+        const cuuint32_t box[3] = {kHaloX, kHaloY, kHaloZ};
+        if ((st = encode(&m.b[m.n], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, sb, dims, strides, box)) != MS_OK) return st;
+    }
+    m.sa[m.n] = sa;
+    m.sb[m.n] = sb;
+    ++m.n;
+    return MS_OK;
+}
+
+cudaError_t launch_step_lattice(const StepArgs &a, const LatticeArgs &g, const LatticeMaps &m, int n_sms,
+                                cudaStream_t st)
+{
+    const long long nbricks = (long long)g.nbx * g.nby * g.nbz;
+    if (nbricks <= 0) return cudaSuccess;
+    if (nbricks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    int q = 0;
+    while (q < m.n && !(m.sa[q] == a.sa && m.sb[q] == a.sb)) ++q;
+    if (q == m.n) return cudaErrorInvalidValue;                // a buffer without tensor maps
+    const unsigned grid = (unsigned)std::min<long long>(nbricks, (long long)kLatCtasPerSm * std::max(n_sms, 1));
+    const size_t smem = 2 * (size_t)kStageBytes;
+#define MS_LAUNCH_L(F, R)                                                                                  \
+    do {                                                                                                   \
+        static std::atomic<uint64_t> opted{0};                                                             \
+        int dev = 0;                                                                                       \
+        cudaError_t e_ = cudaGetDevice(&dev);                                                              \
+        if (e_ != cudaSuccess) return e_;                                                                  \
+        const uint64_t bit = dev < 64 ? (uint64_t)1 << dev : 0;                                            \
+        if (!bit || !(opted.load() & bit)) {                                                               \
+            e_ = cudaFuncSetAttribute(k_step_lattice<F, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+            if (e_ != cudaSuccess) return e_;                                                              \
+            if (bit) opted.fetch_or(bit);                                                                  \
+        }                                                                                                  \
+        k_step_lattice<F, R><<<grid, kLatThreads, smem, st>>>(a, g, m.a[q], m.b[q], m.k);                  \
+    } while (0)
+    const bool hf = a.fext != nullptr;
+    if (a.integrator == 3) { if (hf) MS_LAUNCH_L(true, true); else MS_LAUNCH_L(false, true); }
+    else { if (hf) MS_LAUNCH_L(true, false); else MS_LAUNCH_L(false, false); }
+#undef MS_LAUNCH_L
     return cudaGetLastError();
 }
 

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_reference_arm_prints_one_complete_line():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
-                          "--warmup", "1", "--ref-seconds", "0.2", "--ref-side", "10"],
+                          "--warmup", "1", "--ref-side", "10"],
                          capture_output=True, text=True, timeout=300, cwd=ROOT)
     assert out.returncode == 0, out.stderr
     lines = [l for l in out.stdout.splitlines() if l.strip()]
@@ -27,5 +27,8 @@ def test_reference_arm_prints_one_complete_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    # the line describes the benchmark's workload, the 256^3 lattice
+    # the line describes the benchmark's workload, the 256^3 lattice, and the
+    # sample each step timed; the time per step is the sample's, as timed
     assert d["config"]["n_masses"] == 256 ** 3 and d["config"]["n_springs"] == 216338940
+    assert "10^3" in d["config"]["sample"] and "10^3" in cb["sample"]
+    assert d["extrapolated_ms_per_step_at_workload"] > d["ms_per_step"]
