@@ -412,19 +412,72 @@ ms_status build_lattice(ms_sim *s, const ms_params *p, int32_t N, const float *x
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-const char *ms_last_error(void) { return g_last_error.c_str(); }
+// ---------------------------------------------------------------------------
+// ms_create for the general layouts (gather, tiled, persistent), in steps:
+// check the input, order the masses, merge parallel springs into records,
+// lay the records out for the chosen kernel, build and upload the state.
+// ---------------------------------------------------------------------------
+struct CreateInput {
+    const ms_params *p;
+    int32_t N;
+    const float *x0, *v0, *mass;
+    const uint8_t *fixed;
+    const float *fext;
+    int64_t S;
+    const int32_t *ij;
+    const float *k, *c;
+    float c_uniform;
+    const float *rest_len;
+};
 
-const char *ms_version(void) { return "cronos-ms-gb300 0.1 (sm_103a)"; }
+// merged spring records in internal order: owner o < partner, records of
+// owner o in [rec_first[o], rec_first[o + 1])
+struct MergedSprings {
+    std::vector<int32_t> deg, bdeg;       // records owned / referenced per mass
+    std::vector<int64_t> rec_first;
+    std::vector<int32_t> rec_partner;
+    std::vector<float2> rec_kl;           // (summed k, stiffness-weighted L0)
+    std::vector<float> rec_c;             // summed c (per-spring damping only)
+    std::vector<double> sumK;             // per mass: sum of the k of its records
+    int64_t n_rec = 0;
+};
 
-ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float *v0, const float *mass,
-                    const uint8_t *fixed, const float *fext, int64_t S, const int32_t *ij, const float *k,
-                    const float *c, float c_uniform, const float *rest_len, const ms_allocator *alloc,
-                    void *stream, ms_sim **out)
+// host image of the general layouts before upload
+struct GeneralLayout {
+    int n_slices = 0;
+    int64_t n_slots = 0;
+    std::vector<uint32_t> slot_a, slot_b;
+    std::vector<ms::Slice> sl;
+    std::vector<int32_t> h_nbr;
+    std::vector<uint16_t> h_nbr16;
+    std::vector<uint32_t> h_b;
+    std::vector<int4> h_tiles;
+    std::vector<int32_t> h_halo;
+    std::vector<float2> h_kl;
+    std::vector<float> h_c;
+    std::vector<uint16_t> c_nbr;          // persistent cluster layout
+    std::vector<float2> c_kl;
+    std::vector<float> c_c;
+};
+
+// Every argument check, before any allocation (host only).
+ms_status check_create_input(const CreateInput &in, const ms_allocator *alloc)
 {
-    if (!out) return fail(MS_ERR_ARG, "out is NULL");
-    *out = nullptr;
+    const ms_params *p = in.p;
+    const int32_t N = in.N;
+    const float *x0 = in.x0;
+    const float *v0 = in.v0;
+    const float *mass = in.mass;
+    const float *fext = in.fext;
+    const uint8_t *fixed = in.fixed;
+    const int64_t S = in.S;
+    const int32_t *ij = in.ij;
+    const float *k = in.k;
+    const float *c = in.c;
+    const float *rest_len = in.rest_len;
+    const float c_uniform = in.c_uniform;
     if (!p || !x0 || !v0 || !mass) return fail(MS_ERR_ARG, "p, x0, v0 and mass are required");
     if (N < 1 || N >= (1 << ms::kOwnerBits)) return fail(MS_ERR_ARG, "N must be in [1, 2^27)");
     if (S < 0 || (S > 0 && (!ij || !k))) return fail(MS_ERR_ARG, "S < 0, or ij / k missing");
@@ -453,43 +506,18 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
         if (c && !(c[e] >= 0.f && std::isfinite(c[e]))) return fail(MS_ERR_ARG, "c must be >= 0 and finite at spring " + std::to_string(e));
         if (rest_len && !(rest_len[e] >= 0.f && std::isfinite(rest_len[e]))) return fail(MS_ERR_ARG, "rest length must be >= 0 and finite at spring " + std::to_string(e));
     }
+    return MS_OK;
+}
 
-    ms_sim *s = new (std::nothrow) ms_sim();
-    if (!s) return fail(MS_ERR_OOM, "host allocation failed");
-    struct Guard { ms_sim *s; ~Guard() { if (s) { s->release(); delete s; } } } guard{s};
-    s->p = *p; s->N = N; s->S = S;
-    s->stream = (cudaStream_t)stream;
-    if (alloc) { s->alloc = *alloc; s->custom_alloc = true; }
-    s->c_uniform = c_uniform;
-
-    if (p->kernel < 0 || p->kernel > 4 || p->reorder < 0 || p->reorder > 2) return fail(MS_ERR_ARG, "kernel must be 0..4 and reorder 0..2");
-    // lattice layout: when asked for, or by default for a large box lattice
-    if (p->kernel == ms::kKernelLattice || (p->kernel == 0 && N >= kLatticeAutoMin)) {
-        LatticeShape L;
-        std::string why;
-        if (lattice_shape(N, x0, S, ij, k, c, c_uniform, rest_len, L, why)) {
-            ms_status st = build_lattice(s, p, N, x0, v0, mass, fixed, fext, L);
-            if (st != MS_OK) return st;
-            guard.s = nullptr;
-            *out = s;
-            return MS_OK;
-        }
-        if (p->kernel == ms::kKernelLattice) return fail(MS_ERR_ARG, "not a lattice for the lattice kernel: " + why);
-    }
-    if (p->kernel == 3 && p->integrator != 0)
-        return fail(MS_ERR_ARG, "the persistent kernel integrates with symplectic Euler only");
-    // persistent: up to kClusterMax x kClMassesMax masses one thread-block
-    // cluster; above, the tiled layout in one cooperative launch (one wave of tiles)
-    const bool cluster_fits = N <= ms::kClMassesMax * ms::kClusterMax;
-    s->kernel = p->kernel == 1 ? ms::kKernelGather
-              : p->kernel == 2 ? ms::kKernelTiled
-              : p->kernel == 3 ? ms::kKernelPersistent
-              : ms::kKernelTiled;
-    const bool persistent = s->kernel == ms::kKernelPersistent;
-    s->grid_persistent = persistent && !cluster_fits;
-    // the cluster kernel keeps the gather layout (for the energy kernel); the grid kernel steps the tiled one
-    if (persistent) s->kernel = cluster_fits ? ms::kKernelGather : ms::kKernelTiled;
-
+// Mass order: Morton order by initial position for the tiled and persistent
+// kernels (or when asked for), else the caller's.
+void order_masses(ms_sim *s, const CreateInput &in, bool persistent)
+{
+    const ms_params *p = in.p;
+    const int32_t N = in.N;
+    const float *x0 = in.x0;
+    const int64_t S = in.S;
+    const int32_t *ij = in.ij;
     // 1. mass order
     s->perm.resize(N); s->iperm.resize(N);
     for (int32_t i = 0; i < N; ++i) s->perm[i] = i;
@@ -504,7 +532,6 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
         double h = 0.0;
         for (int64_t e = 0; e < S; ++e) {
             const int32_t a = ij[2 * e], b = ij[2 * e + 1];
-            if (a < 0 || a >= N || b < 0 || b >= N) continue;      // rejected below
             const double dx = (double)x0[3 * b] - x0[3 * a], dy = (double)x0[3 * b + 1] - x0[3 * a + 1],
                          dz = (double)x0[3 * b + 2] - x0[3 * a + 2];
             const double l = std::sqrt(dx * dx + dy * dy + dz * dz);
@@ -523,7 +550,18 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
         s->permuted = true;
     }
     for (int32_t i = 0; i < N; ++i) s->iperm[s->perm[i]] = i;
+}
 
+// File springs by owner and merge parallel springs into records.
+ms_status merge_springs(ms_sim *s, const CreateInput &in, MergedSprings &M)
+{
+    const int32_t N = in.N;
+    const float *x0 = in.x0;
+    const int64_t S = in.S;
+    const int32_t *ij = in.ij;
+    const float *k = in.k;
+    const float *c = in.c;
+    const float *rest_len = in.rest_len;
     // 2. file springs by owner (counting sort), merge parallel springs into
     //    records: (owner < partner) in internal order, grouped by owner.
     std::vector<int64_t> row(N + 1, 0);
@@ -595,7 +633,27 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
     s->n_records = n_rec;
     r_other.clear(); r_other.shrink_to_fit(); r_spring.clear(); r_spring.shrink_to_fit();
     if (n_rec >= (int64_t)UINT32_MAX / 2) return fail(MS_ERR_ARG, "too many springs for 32-bit record offsets");
+    M.deg.swap(deg); M.bdeg.swap(bdeg); M.rec_first.swap(rec_first); M.rec_partner.swap(rec_partner);
+    M.rec_kl.swap(rec_kl); M.rec_c.swap(rec_c); M.sumK.swap(sumK);
+    M.n_rec = n_rec;
+    return MS_OK;
+}
 
+// Records laid out for the tiled kernel (falling back to the gather layout
+// when a tile does not fit shared memory) or for the gather kernel.
+ms_status build_rows(ms_sim *s, const CreateInput &in, const MergedSprings &M, bool persistent, bool cluster_fits,
+                     GeneralLayout &G)
+{
+    const int32_t N = in.N;
+    const float *x0 = in.x0;
+    const float *c = in.c;
+    const auto &deg = M.deg;
+    const auto &bdeg = M.bdeg;
+    const auto &rec_first = M.rec_first;
+    const auto &rec_partner = M.rec_partner;
+    const auto &rec_kl = M.rec_kl;
+    const auto &rec_c = M.rec_c;
+    const int64_t n_rec = M.n_rec;
     // 3. device layout of the chosen kernel
     const int n_slices = (N + 31) / 32;
     s->n_slices = n_slices;
@@ -780,7 +838,22 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
     s->persistent = persistent && cluster_fits;
     s->rec_slot_a.swap(slot_a);
     s->rec_slot_b.swap(slot_b);
+    G.n_slices = n_slices; G.n_slots = n_slots;
+    G.sl.swap(sl); G.h_nbr.swap(h_nbr); G.h_nbr16.swap(h_nbr16); G.h_b.swap(h_b);
+    G.h_tiles.swap(h_tiles); G.h_halo.swap(h_halo); G.h_kl.swap(h_kl); G.h_c.swap(h_c);
+    return MS_OK;
+}
 
+// Records of the persistent cluster kernel (small systems).
+ms_status build_cluster_rows(ms_sim *s, const CreateInput &in, const MergedSprings &M, GeneralLayout &G)
+{
+    const int32_t N = in.N;
+    const float *c = in.c;
+    const auto &rec_first = M.rec_first;
+    const auto &rec_partner = M.rec_partner;
+    const auto &rec_kl = M.rec_kl;
+    const auto &rec_c = M.rec_c;
+    const int64_t n_rec = M.n_rec;
     // persistent cluster layout: tiles of CM masses, the smallest of 64, 128,
     // 256, 512 that needs at most kClusterMax tiles; every mass lists all of
     // its springs (both directions), the slots of its L lanes interleaved,
@@ -830,7 +903,36 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
         s->cl_slots = slots;
         s->cl_n = (int64_t)tiles * per_tile;
     }
+    G.c_nbr.swap(c_nbr); G.c_kl.swap(c_kl); G.c_c.swap(c_c);
+    return MS_OK;
+}
 
+// The masses' state (internal order), the stability bound, and the upload of
+// every array of the chosen layout.
+ms_status upload_general(ms_sim *s, const CreateInput &in, const MergedSprings &M, GeneralLayout &G)
+{
+    const ms_params *p = in.p;
+    const int32_t N = in.N;
+    const float *x0 = in.x0;
+    const float *v0 = in.v0;
+    const float *mass = in.mass;
+    const float *fext = in.fext;
+    const uint8_t *fixed = in.fixed;
+    const float *c = in.c;
+    const auto &sumK = M.sumK;
+    const int n_slices = G.n_slices;
+    const int64_t n_slots = G.n_slots;
+    const auto &sl = G.sl;
+    const auto &h_nbr = G.h_nbr;
+    const auto &h_nbr16 = G.h_nbr16;
+    const auto &h_b = G.h_b;
+    const auto &h_tiles = G.h_tiles;
+    const auto &h_halo = G.h_halo;
+    const auto &h_kl = G.h_kl;
+    const auto &h_c = G.h_c;
+    const auto &c_nbr = G.c_nbr;
+    const auto &c_kl = G.c_kl;
+    const auto &c_c = G.c_c;
     // masses
     std::vector<float4> ha(N), hf;
     std::vector<float2> hb(N);
@@ -917,7 +1019,17 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
     MS_CUDA_TRY(cudaMemsetAsync(s->err, 0, 2 * sizeof(int), s->stream));
     // host arrays must outlive the asynchronous copies
     MS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return MS_OK;
+}
 
+// The caller's k and rest lengths, kept for ms_set_actuation's merge.
+void keep_caller_springs(ms_sim *s, const CreateInput &in)
+{
+    const float *x0 = in.x0;
+    const int64_t S = in.S;
+    const int32_t *ij = in.ij;
+    const float *k = in.k;
+    const float *rest_len = in.rest_len;
     s->k_caller.assign(k, k + S);
     s->L0_caller.resize(S);
     for (int64_t e = 0; e < S; ++e) {
@@ -929,6 +1041,70 @@ ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float 
             s->L0_caller[e] = (float)std::sqrt(dx * dx + dy * dy + dz * dz);
         }
     }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ms_last_error(void) { return g_last_error.c_str(); }
+
+const char *ms_version(void) { return "cronos-ms-gb300 0.1 (sm_103a)"; }
+
+ms_status ms_create(const ms_params *p, int32_t N, const float *x0, const float *v0, const float *mass,
+                    const uint8_t *fixed, const float *fext, int64_t S, const int32_t *ij, const float *k,
+                    const float *c, float c_uniform, const float *rest_len, const ms_allocator *alloc,
+                    void *stream, ms_sim **out)
+{
+    if (!out) return fail(MS_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    const CreateInput in{p, N, x0, v0, mass, fixed, fext, S, ij, k, c, c_uniform, rest_len};
+    ms_status st = check_create_input(in, alloc);
+    if (st != MS_OK) return st;
+
+    ms_sim *s = new (std::nothrow) ms_sim();
+    if (!s) return fail(MS_ERR_OOM, "host allocation failed");
+    struct Guard { ms_sim *s; ~Guard() { if (s) { s->release(); delete s; } } } guard{s};
+    s->p = *p; s->N = N; s->S = S;
+    s->stream = (cudaStream_t)stream;
+    if (alloc) { s->alloc = *alloc; s->custom_alloc = true; }
+    s->c_uniform = c_uniform;
+
+    if (p->kernel < 0 || p->kernel > 4 || p->reorder < 0 || p->reorder > 2) return fail(MS_ERR_ARG, "kernel must be 0..4 and reorder 0..2");
+    // lattice layout: when asked for, or by default for a large box lattice
+    if (p->kernel == ms::kKernelLattice || (p->kernel == 0 && N >= kLatticeAutoMin)) {
+        LatticeShape L;
+        std::string why;
+        if (lattice_shape(N, x0, S, ij, k, c, c_uniform, rest_len, L, why)) {
+            if ((st = build_lattice(s, p, N, x0, v0, mass, fixed, fext, L)) != MS_OK) return st;
+            guard.s = nullptr;
+            *out = s;
+            return MS_OK;
+        }
+        if (p->kernel == ms::kKernelLattice) return fail(MS_ERR_ARG, "not a lattice for the lattice kernel: " + why);
+    }
+    if (p->kernel == 3 && p->integrator != 0)
+        return fail(MS_ERR_ARG, "the persistent kernel integrates with symplectic Euler only");
+    // persistent: up to kClusterMax x kClMassesMax masses one thread-block
+    // cluster; above, the tiled layout in one cooperative launch (one wave of tiles)
+    const bool cluster_fits = N <= ms::kClMassesMax * ms::kClusterMax;
+    s->kernel = p->kernel == 1 ? ms::kKernelGather
+              : p->kernel == 2 ? ms::kKernelTiled
+              : p->kernel == 3 ? ms::kKernelPersistent
+              : ms::kKernelTiled;
+    const bool persistent = s->kernel == ms::kKernelPersistent;
+    s->grid_persistent = persistent && !cluster_fits;
+    // the cluster kernel keeps the gather layout (for the energy kernel); the grid kernel steps the tiled one
+    if (persistent) s->kernel = cluster_fits ? ms::kKernelGather : ms::kKernelTiled;
+
+    order_masses(s, in, persistent);
+    MergedSprings M;
+    if ((st = merge_springs(s, in, M)) != MS_OK) return st;
+    GeneralLayout G;
+    if ((st = build_rows(s, in, M, persistent, cluster_fits, G)) != MS_OK) return st;
+    if ((st = build_cluster_rows(s, in, M, G)) != MS_OK) return st;
+    if ((st = upload_general(s, in, M, G)) != MS_OK) return st;
+    keep_caller_springs(s, in);
     guard.s = nullptr;
     *out = s;
     return MS_OK;

@@ -126,13 +126,20 @@ def test_contact_gradient_200_steps(ms, ora):
 @pytest.mark.slow
 def test_contact_gradient_2000_steps_3x3x3(ms, ora):
     """The differentiable-batch check: a 3x3x3 robot, 2000 steps with ground
-    contact and friction, loss = centre-of-mass x-travel, central FD of the
-    FP64 oracle at eps = 1e-6.  Over 2000 steps of stick-slip contact the
-    gradient itself is sensitive to the state: perturbing the FP64 start by
-    1e-9 m moves FD components by about 10 %.  So each component must match
-    within 1e-3 relative, or within three times the spread of the FD over
-    three such perturbed starts (plus 2 % of the largest component), and
-    the signs of the significant components must agree."""
+    contact and friction, loss = centre-of-mass x-travel, against central FD
+    of the FP64 oracle.
+
+    Reading R16 at 2000 steps: the rollout is chaotic (stick-slip contact),
+    so the gradient depends on the trajectory: perturbing the FP64 start by
+    1e-9 m -- the scale of FP32 rounding of the positions -- moves the FD
+    components by 20 % to 80 %.  The FP32 adjoint differentiates its own
+    trajectory, so R16's 1e-3 gate applies to the components whose FD is
+    both consistent across eps in {1e-5, 1e-6, 1e-7} and well conditioned
+    (spread over three perturbed starts below 1e-3 of the value).  Every
+    other component must lie within three times its own spread (no floor
+    from the other components), an exactly zero FD (the phase of a passive
+    voxel) needs an exactly zero adjoint, and the signs of the significant
+    components must agree."""
     rng = np.random.default_rng(3)
     mat, phase = synth.random_voxel_design(rng, (3, 3, 3))
     logk = base_logk(mat)
@@ -142,24 +149,35 @@ def test_contact_gradient_2000_steps_3x3x3(ms, ora):
                     params, checkpoint_every=100, max_steps=nsteps) as adj:
         loss, gp, gk = adj.gradients(nsteps, phase, logk)
     p64, k64 = phase.astype(np.float64), logk.astype(np.float64)
-    base = fd_grad(ora, mat, p64, k64, params, nsteps, 1e-6)
+    fd = {e: fd_grad(ora, mat, p64, k64, params, nsteps, e) for e in (1e-5, 1e-6, 1e-7)}
+    base = fd[1e-6]
     s0 = ora.voxel_system(mat, phase, synth.VOXEL_MATERIALS, synth.VOXEL_FREQ, synth.VOXEL_EDGE, synth.VOXEL_MASS)
     ens = []
     for q in range(3):
         pert = 1e-9 * np.random.default_rng(300 + q).standard_normal(s0["x"].shape)
         ens.append(fd_grad_perturbed(ora, mat, p64, k64, params, nsteps, 1e-6, pert))
     occ = np.flatnonzero(mat.ravel() > 0)
-    print("\ncomponent   adjoint        fd(eps=1e-6)   fd spread")
+    strict = loose = 0
+    print("\ncomponent   adjoint        fd(eps=1e-6)   fd spread   eps-consistent")
     for which, g in ((0, gp), (1, gk)):
         f = base[which]
         spread = np.max([np.abs(e[which] - f) for e in ens], axis=0)
         big = np.abs(f[occ]).max()
         for v in occ:
-            tol = max(1e-3 * abs(f[v]), 3 * spread[v] + 0.02 * big)
-            print("%-5s %2d  % .5e  % .5e  %.2e" % ("phase" if which == 0 else "logk", v, g[v], f[v], spread[v]))
-            assert abs(g[v] - f[v]) <= tol, (which, v, g[v], f[v], spread[v])
+            cons = all(abs(fd[e][which][v] - f[v]) <= 1e-3 * abs(f[v]) for e in (1e-5, 1e-7))
+            print("%-5s %2d  % .5e  % .5e  %.2e  %d" % ("phase" if which == 0 else "logk", v, g[v], f[v], spread[v], cons))
+            if f[v] == 0.0 and spread[v] == 0.0:
+                assert g[v] == 0.0, (which, v, g[v])
+            elif cons and spread[v] <= 1e-3 * abs(f[v]):
+                strict += 1
+                assert abs(g[v] - f[v]) <= 1e-3 * abs(f[v]), (which, v, g[v], f[v])
+            else:
+                loose += 1
+                assert abs(g[v] - f[v]) <= max(1e-3 * abs(f[v]), 3 * spread[v]), (which, v, g[v], f[v], spread[v])
             if abs(f[v]) > 0.1 * big:
                 assert np.sign(g[v]) == np.sign(f[v])
+    print(f"{strict} components under the 1e-3 gate, {loose} under their own spread")
+    assert strict + loose > 0
 
 
 def fd_grad_perturbed(ora, mat, phase, logk, params, nsteps, eps, pert):
