@@ -78,7 +78,7 @@ class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-              "clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_power_cap,clocks.mem")
 
     def __init__(self, index: int):
         self.index = index
@@ -116,16 +116,17 @@ class Clocks:
             if len(parts) < 7:
                 continue
             try:
-                rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+                mem = float(parts[7]) if len(parts) > 7 else float("nan")
+                rows.append((float(parts[0]), float(parts[1]), parts[3:7], mem))
             except ValueError:
                 continue
         os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[q] for _, _, flags in rows for q, f in enumerate(flags) if f.lower() == "active"})
+        reasons = sorted({names[q] for _, _, flags, _ in rows for q, f in enumerate(flags) if f.lower() == "active"})
         return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "mem_mhz": statistics.median(r[3] for r in rows)}
 
 
 def dist_setup():
