@@ -371,10 +371,12 @@ def run_ours(args, world, rank, local):
     cpu = oracle_baseline(max_seconds=args.cpu_seconds) if (rank == 0 and world == 1 and args.cpu_seconds > 0) else None
 
     clocks = clk.summary()
-    batched = None
+    batched = screening = adjoint = None
     if args.batched and args.integrator == "symplectic_euler":
         sim.close()                                  # free the lattice before the population is built
         batched = measure_population(args, reps, local, args.sim_steps_per_bench_step, 1)
+        screening = measure_screening(args, reps, local)
+        adjoint = measure_adjoint(args, reps, local)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
@@ -392,8 +394,10 @@ def run_ours(args, world, rank, local):
             "clocks": clocks}
     if cpu is not None:
         line["cpu_baseline"] = cpu
-    if batched is not None:
-        line["batched"] = batched                 # its own timed region and launch count
+    if batched is not None:                       # each with its own timed region
+        line["batched"] = batched
+        line["surrogate_screening"] = screening
+        line["adjoint"] = adjoint
     if rank == 0:
         print(json.dumps(line), flush=True)
     sim.close()
@@ -477,6 +481,76 @@ def measure_population(args, reps, local, sim_steps, timed_launches, warm_launch
            "gpu_launches": 3 * timed_launches}
     pop.close()
     return rec
+
+
+def measure_screening(args, reps, local, passes=3, warm=2):
+    """The surrogate's screening rate (config 5's learned component): 2^20 raw
+    8^3 material grids scored per bench pass by the tensor-core MLP (one-hot
+    tiles built on chip), 65 536 designs per forward pass."""
+    import torch
+    import paper_2207_09334_gb300 as ms
+    B, n_cand = args.screen_batch, args.candidates
+    rng = np.random.default_rng(4)
+    cand = torch.tensor(rng.integers(0, 4, size=(n_cand, 512)).astype(np.uint8), device="cuda")
+    out = torch.empty(n_cand, device="cuda")
+    stream = torch.cuda.current_stream()
+    with ms.Surrogate(2048, 512, max_batch=max(B, 1024), seed=0) as net:
+        def screen_once():
+            for q in range(0, n_cand, B):
+                net.load_materials(cand[q:q + B])
+                net.forward(B, out[q:q + B])
+        for _ in range(warm):
+            screen_once()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        reps.barrier()
+        e0.record(stream)
+        for _ in range(passes):
+            screen_once()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        reps.barrier()
+        ms_total = reps.max(e0.elapsed_time(e1))
+    flops = 2.0 * (2048 * 512 + 512 * 512 + 512) * n_cand * passes * reps.world
+    return {"value": reps.world * n_cand * passes / (ms_total * 1e-3), "unit": "designs/s",
+            "ms_per_pass": ms_total / passes, "tensor_tflops": flops / (ms_total * 1e-3) / 1e12,
+            "config": {"workload": f"MLP 2048->512->512->1 (bf16, fp32 accumulate) scoring {n_cand} 8^3 designs per "
+                                   f"pass, {B} per forward pass", "passes": passes}}
+
+
+def measure_adjoint(args, reps, local, evals=2, warm=1):
+    """The differentiable batch (config 4): 256 walkers of 8^3 voxels, loss =
+    centre-of-mass x-travel after 2000 steps, gradients w.r.t. every voxel's
+    phase and log-stiffness by the checkpointed adjoint."""
+    import torch
+    import paper_2207_09334_gb300 as ms
+    designs = synth.walker_designs(args.walkers, seed=3)
+    mats = [m for m, _ in designs]
+    phase = torch.tensor(np.concatenate([p.ravel() for _, p in designs]), device="cuda")
+    kmat = synth.VOXEL_MATERIALS[:, 0]
+    logk = torch.tensor(np.concatenate([np.where(m > 0, np.log(np.maximum(kmat[m], 1.0)), 0.0).ravel()
+                                        for m in mats]).astype(np.float32), device="cuda")
+    nsteps = args.rollout_steps
+    stream = torch.cuda.current_stream()
+    with ms.Adjoint(mats, synth.VOXEL_MATERIALS, synth.VOXEL_FREQ, synth.VOXEL_EDGE, synth.VOXEL_MASS,
+                    synth.voxel_params(), checkpoint_every=100, max_steps=nsteps) as adj:
+        for _ in range(warm):
+            adj.gradients(nsteps, phase, logk)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        reps.barrier()
+        e0.record(stream)
+        for _ in range(evals):
+            loss, gp, gk = adj.gradients(nsteps, phase, logk)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        reps.barrier()
+        ms_total = reps.max(e0.elapsed_time(e1))
+    return {"value": reps.world * args.walkers * nsteps * synth.voxel_params()["dt"] * evals / (ms_total * 1e-3),
+            "unit": "robot-sim-s/s (forward + reverse)", "ms_per_evaluation": ms_total / evals,
+            "config": {"workload": f"{args.walkers} walkers of 8^3 voxels (seed 3), {nsteps} steps, checkpoint every "
+                                   "100; one evaluation = loss + gradient for all walkers", "evaluations": evals},
+            "mean_travel_m": float(loss.mean())}
 
 
 def run_population(args, world, rank, local):
@@ -817,7 +891,8 @@ def main():
     ap.add_argument("--sim-steps-per-bench-step", type=int, default=5000,
                     help="population workload: simulated steps per persistent launch (one bench step)")
     ap.add_argument("--batched", type=int, default=1,
-                    help="lattice workload: add the population's batched record (one 5000-step launch)")
+                    help="lattice workload: add the records of the population (one 5000-step launch), the "
+                         "surrogate's screening and the adjoint")
     ap.add_argument("--loop-steps", type=int, default=5)
     ap.add_argument("--candidates", type=int, default=1 << 20)
     ap.add_argument("--screen-batch", type=int, default=65536, help="designs per surrogate forward pass")
