@@ -18,7 +18,9 @@
 //     accumulator back with tcgen05.ld (warp w owns TMEM lanes 32(w mod 4)..+31
 //     = rows, and one of the column parts) and apply the fused epilogue: plain fp32 store, bias + GELU (forward), or
 //     GELU' (backward), writing row-major and transposed bf16 copies as the
-//     next product needs.
+//     next product needs.  The last layer's n_hidden -> 1 head is folded into
+//     the second layer's epilogue as 16-column partial dot products (summed
+//     in a fixed order by a small kernel), so inference never stores H2.
 // Every wait is bounded by %globaltimer; on expiry the kernel records a
 // timeout in the error flag, stops issuing work and returns.
 #include <cuda.h>
@@ -63,6 +65,8 @@ struct GemmArgs {
     __nv_bfloat16 *Ht;        // transposed out [N][M] (or nullptr)
     const uint8_t *mats;      // one-hot A operand: materials [M][n_vox] (ids 0..3), K = 4 n_vox
     int n_vox;
+    const float *w3;          // EPI_BIAS_GELU, fused head (or nullptr): head weights [N]
+    float *hpart;             // fused head: partial dot products [N / 16][M]
     int *err;
 };
 
@@ -108,6 +112,16 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
     asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
                  ::"r"(saddr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(saddr(bar))
                  : "memory");
+}
+
+// bring [p, p + bytes) into L2 in pieces of at most 16 KB (bytes a multiple
+// of 16, p 16-byte aligned)
+__device__ __forceinline__ void bulk_prefetch_l2(const uint8_t *p, uint32_t bytes)
+{
+    for (uint32_t o = 0; o < bytes; o += 16384u) {
+        const uint32_t n = bytes - o < 16384u ? bytes - o : 16384u;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<uint64_t>(p + o)), "r"(n) : "memory");
+    }
 }
 
 // shared-memory matrix descriptor: K-major tile, 128-byte swizzle, 8-row
@@ -175,6 +189,24 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, const uint32_t
                 hv[q] = __float2bfloat16(gelu(__bfloat162float(zv[q])));
             }
         }
+        if (g.w3) {
+            // fused head: this row's dot product with w3 over each 16 columns
+#pragma unroll
+            for (int q0 = 0; q0 < CW; q0 += 16) {
+                const float4 *w4 = reinterpret_cast<const float4 *>(g.w3 + nb + q0);
+                float hs = 0.f;
+#pragma unroll
+                for (int q4 = 0; q4 < 4; ++q4) {
+                    const float4 w = __ldg(&w4[q4]);
+                    const int q = q0 + 4 * q4;
+                    hs = fmaf(__bfloat162float(hv[q]), w.x, hs);
+                    hs = fmaf(__bfloat162float(hv[q + 1]), w.y, hs);
+                    hs = fmaf(__bfloat162float(hv[q + 2]), w.z, hs);
+                    hs = fmaf(__bfloat162float(hv[q + 3]), w.w, hs);
+                }
+                g.hpart[(size_t)((nb + q0) >> 4) * g.M + row] = hs;
+            }
+        }
     } else {
         const uint4 *zr = reinterpret_cast<const uint4 *>(g.Z + (size_t)row * g.N + nb);
 #pragma unroll
@@ -183,9 +215,11 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, const uint32_t
         for (int q = 0; q < CW; ++q)
             hv[q] = __float2bfloat16(__uint_as_float(r[q]) * gelu_grad(__bfloat162float(zv[q])));
     }
-    uint4 *dh = reinterpret_cast<uint4 *>(g.H + (size_t)row * g.N + nb);
+    if (g.H) {
+        uint4 *dh = reinterpret_cast<uint4 *>(g.H + (size_t)row * g.N + nb);
 #pragma unroll
-    for (int q = 0; q < CW / 8; ++q) dh[q] = reinterpret_cast<const uint4 *>(hv)[q];
+        for (int q = 0; q < CW / 8; ++q) dh[q] = reinterpret_cast<const uint4 *>(hv)[q];
+    }
     if (g.epi == EPI_BIAS_GELU && g.Z) {                    // pre-activation kept for the backward pass
         uint4 *dz = reinterpret_cast<uint4 *>(g.Z + (size_t)row * g.N + nb);
 #pragma unroll
@@ -239,7 +273,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *b)
 // X[b][4 v + m] = (materials[b][v] == m) for 16 voxels straight into shared
 // memory, in the layout a 128-byte-swizzled TMA load of X would give (row r
 // at r * 128 bytes, 16-byte chunk j of the row at chunk j ^ (r mod 8)), so the
-// one-hot matrix never exists in global memory.  Builder thread r owns row r.
+// one-hot matrix never exists in global memory.  Builder thread r owns row r;
+// the material rows of a CTA's next tile are prefetched into L2 (one bulk
+// prefetch) while the current tile is built.
 __device__ __forceinline__ uint64_t onehot4(uint32_t m)
 {   // the four bf16 (m == 0, .., m == 3) of one voxel, 1.0 = 0x3f80; all zero for m > 3
     return m < 4u ? (uint64_t)0x3f80u << (16u * m) : 0ull;
@@ -296,13 +332,13 @@ __global__ void __launch_bounds__(gemm_threads<ONEHOT>(), 1) k_gemm_tc(const __g
             unsigned it = 0;
             bool ok = true;
             for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-                const int m0 = (tile / tiles_n) * kBM, n0 = (tile % tiles_n) * BN;
+                const int n0 = (tile % tiles_n) * BN;
                 for (int kt = 0; kt < KT; ++kt, ++it) {
                     const unsigned s = it % kStages;
                     if (it >= (unsigned)kStages && !mbar_wait(&empty[s], ((it / kStages) - 1) & 1)) { ok = false; break; }
                     unsigned char *a = ring + (size_t)s * kStageBytes;
                     mbar_expect_tx(&full[s], kTxBytes);
-                    if (!ONEHOT) tma_load_2d(a, &mapA, kt * kBK, m0, &full[s]);
+                    if (!ONEHOT) tma_load_2d(a, &mapA, kt * kBK, (tile / tiles_n) * kBM, &full[s]);
 #pragma unroll
                     for (int q = 0; q < BN / kBM; ++q)
                         tma_load_2d(a + kTileBytes * (1 + q), &mapB, kt * kBK, n0 + q * kBM, &full[s]);
@@ -316,8 +352,12 @@ __global__ void __launch_bounds__(gemm_threads<ONEHOT>(), 1) k_gemm_tc(const __g
         const int r = tid - 32 * (2 + kEW);
         unsigned it = 0;
         bool ok = true;
+        if (r == 0 && (int)blockIdx.x < n_tiles)             // the first tile's material rows into L2
+            bulk_prefetch_l2(g.mats + (size_t)((blockIdx.x / tiles_n) * kBM) * g.n_vox, kBM * g.n_vox);
         for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
             const int m0 = (tile / tiles_n) * kBM;
+            if (r == 0 && tile + (int)gridDim.x < n_tiles)    // and the next tile's, while this one is built
+                bulk_prefetch_l2(g.mats + (size_t)(((tile + gridDim.x) / tiles_n) * kBM) * g.n_vox, kBM * g.n_vox);
             const uint4 *src = reinterpret_cast<const uint4 *>(g.mats + (size_t)(m0 + r) * g.n_vox);
             uint4 mv = __ldg(&src[0]);
             for (int kt = 0; kt < KT; ++kt, ++it) {
@@ -419,15 +459,15 @@ __global__ void k_transpose_bf16(const __nv_bfloat16 *in, int R, int Cc, __nv_bf
     }
 }
 
-// y[b] = H2[b] . w3 + b3 (one warp per row)
-__global__ void k_head(const __nv_bfloat16 *H2, const float *w3, const float *b3, int B, int Hd, float *y)
+// y[b] = H2[b] . w3 + b3 from the second layer's 16-column partial sums
+// hpart [nparts][B], added in a fixed order
+__global__ void k_head_sum(const float *hpart, int nparts, int B, const float *b3, float *y)
 {
-    const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (row >= B) return;
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
     float s = 0.f;
-    for (int k = lane; k < Hd; k += 32) s += __bfloat162float(H2[(size_t)row * Hd + k]) * w3[k];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) y[row] = s + b3[0];
+    for (int j = 0; j < nparts; ++j) s += hpart[(size_t)j * B + b];
+    y[b] = s + b3[0];
 }
 
 // dy = (y - t)/B; per-row loss terms
@@ -608,6 +648,7 @@ struct mlp_model {
     __nv_bfloat16 *X = nullptr, *Xt = nullptr, *Z1 = nullptr, *H1 = nullptr, *H1t = nullptr, *Z2 = nullptr, *H2 = nullptr;
     __nv_bfloat16 *dZ2 = nullptr, *dZ2t = nullptr, *dZ1 = nullptr, *dZ1t = nullptr;
     float *y = nullptr, *dy = nullptr, *lterm = nullptr, *loss = nullptr;
+    float *hpart = nullptr;            // the head's 16-column partial sums [n_h / 16][max_b]
     int *err = nullptr;
     // materials of the loaded batch (mlp_encode); X holds their one-hot
     // encoding only once a pass needs it (x_pending = not yet written)
@@ -686,10 +727,12 @@ ms_status forward(mlp_model *m, int B, bool keep)
         s = gemm(m->X, m->W1b, B, m->n_h, m->n_in, g, m->stream);
     }
     if (s != MS_OK) return s;
-    // Z2 = H1 W2^T + b2, H2 = GELU(Z2)
-    g.bias = m->P + m->off_b2; g.Z = keep ? m->Z2 : nullptr; g.H = m->H2; g.Ht = nullptr;
+    // Z2 = H1 W2^T + b2, H2 = GELU(Z2) (stored for training only), and the
+    // head y = H2 w3 + b3 from the epilogue's partial sums
+    g.bias = m->P + m->off_b2; g.Z = keep ? m->Z2 : nullptr; g.H = keep ? m->H2 : nullptr; g.Ht = nullptr;
+    g.w3 = m->P + m->off_w3; g.hpart = m->hpart;
     if ((s = gemm(m->H1, m->W2b, B, m->n_h, m->n_h, g, m->stream)) != MS_OK) return s;
-    k_head<<<nblk((size_t)B * 32), 256, 0, m->stream>>>(m->H2, m->P + m->off_w3, m->P + m->off_b3, B, m->n_h, m->y);
+    k_head_sum<<<nblk(B), 256, 0, m->stream>>>(m->hpart, m->n_h / 16, B, m->P + m->off_b3, m->y);
     MLP_CUDA_TRY(cudaGetLastError());
     return MS_OK;
 }
@@ -766,7 +809,8 @@ ms_status mlp_create(int32_t n_in, int32_t n_hidden, int32_t max_batch, uint64_t
     m->y = mal<float>(m, B); m->dy = mal<float>(m, B); m->lterm = mal<float>(m, B); m->loss = mal<float>(m, 1);
     m->err = mal<int>(m, 1);
     m->mats = mal<uint8_t>(m, B * (I / 4));
-    if (!m->mats) return fail(MS_ERR_OOM, "device allocation failed");
+    m->hpart = mal<float>(m, (H / 16) * B);
+    if (!m->mats || !m->hpart) return fail(MS_ERR_OOM, "device allocation failed");
     if (!m->P || !m->G || !m->Mo || !m->Vo || !m->W1b || !m->W2b || !m->W2tb || !m->X || !m->Xt || !m->Z1 ||
         !m->H1 || !m->H1t || !m->Z2 || !m->H2 || !m->dZ2 || !m->dZ2t || !m->dZ1 || !m->dZ1t || !m->y || !m->dy ||
         !m->lterm || !m->loss || !m->err)

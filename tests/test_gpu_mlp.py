@@ -180,3 +180,49 @@ def test_training_fits_a_learnable_target(ms):
             first = first if first is not None else loss
         net.sync()
     assert loss < 0.1 * first, (first, loss)
+
+
+def _bf16_nearest(x):
+    """bf16 nearest to each FP64 value (ties to even), computed exactly."""
+    x = np.asarray(x, np.float64)
+    m, e = np.frexp(np.abs(x))
+    r = np.ldexp(np.rint(np.ldexp(m, 8)), e - 8)       # np.rint: ties to even
+    return np.where(x < 0, -r, r)
+
+
+def test_gelu_of_every_input_range_matches_the_definition(ms):
+    """The forward epilogues apply GELU(z) = z Phi(z) to bf16 pre-activations.
+    A model whose unit k reads only voxel k (Z1_k = W1[k][4k + m], exact), with
+    W2 = I (Z2 = H1, exact) and w3 = e_j, predicts y = GELU(GELU(z)) rounded to
+    bf16 after each GELU.  512 values of z over +-[2^-12, 128] (both signs,
+    zero, and the powers of two where the bf16 step changes) are checked
+    against the FP64 definition: within one bf16 step of the value, plus the
+    FP32 cancellation of 1 + erf(z / sqrt 2) in the negative tail (1e-7 |z|),
+    and bit-equal for at least 98 % of the values with z >= -2."""
+    import torch
+    from oracle import mlp
+    n_in, h, B = 512, 128, 128
+    rng = np.random.default_rng(11)
+    edges = [2.0 ** -7, 2.0 ** -7 * (1 - 2 ** -8), 7.96875, 8.0, 8.0625, 0.0, 2.0 ** -12, 100.0, 1.0, 0.5]
+    z = np.concatenate([edges, [-e for e in edges]])
+    mag = 2.0 ** rng.uniform(-12, 7, 4 * h - z.size)
+    z = _bf16_nearest(np.concatenate([z, mag * rng.choice([-1.0, 1.0], mag.size)]))
+    W1 = np.zeros((h, n_in)); W2 = np.eye(h)
+    for k in range(h):
+        W1[k, 4 * k:4 * k + 4] = z[4 * k:4 * k + 4]
+    mats = torch.tensor(np.tile((np.arange(B) % 4)[:, None], (1, n_in // 4)).astype(np.uint8), device="cuda")
+    got = np.empty(4 * h)
+    with ms.Surrogate(n_in, h, max_batch=B, seed=0) as net:
+        for j in range(h):
+            w3 = np.zeros(h); w3[j] = 1.0
+            net.set_params(np.concatenate([W1.ravel(), np.zeros(h), W2.ravel(), np.zeros(h), w3, [0.0]]))
+            net.load_materials(mats)
+            y = net.forward(B).cpu().numpy().astype(np.float64)
+            got[4 * j:4 * j + 4] = y[:4]
+        net.sync()
+    e1 = _bf16_nearest(mlp.gelu(z))
+    want = _bf16_nearest(mlp.gelu(e1))
+    err = np.abs(got - want)
+    assert (err <= 2.0 ** -7 * np.abs(want) + 1e-7 * np.abs(z) + 1e-30).all(), err.max()
+    mild = z >= -2.0
+    assert np.mean(got[mild] == want[mild]) >= 0.98, np.mean(got[mild] == want[mild])
