@@ -30,7 +30,7 @@ class MsInfo(C.Structure):
                 ("n_slots", C.c_int64), ("n_back_slots", C.c_int64), ("device_bytes", C.c_int64),
                 ("step_count", C.c_int64), ("stability_bound", C.c_double),
                 ("max_fwd_degree", C.c_int32), ("max_back_degree", C.c_int32), ("kernel", C.c_int32),
-                ("n_tiles", C.c_int32), ("max_tile_local", C.c_int32)]
+                ("n_tiles", C.c_int32), ("max_tile_local", C.c_int32), ("lattice_guard", C.c_int32)]
 
 
 class MsbVoxelSpec(C.Structure):

@@ -214,7 +214,9 @@ struct LatticeShape {
     int nx = 0, ny = 0, nz = 0, nbx = 0, nby = 0, nbz = 0, X = 0, Y = 0, Z = 0;
     int64_t P = 0;                    // padded cells
     std::vector<int32_t> cidx;        // caller mass -> padded index
-    std::vector<float> kf;            // [13][P] stiffness, NaN = no spring
+    std::vector<float> kf;            // [13][P] stiffness; 0 on a slot that touches a cell without a
+                                      // mass, NaN between two masses that have no spring
+    bool guard = false;               // some slot between two masses is NaN
     float L[ms::kLatDirs] = {};
     float c = 0.f;
     std::vector<double> sumK;         // per caller mass: sum of the k of its springs
@@ -273,15 +275,13 @@ bool lattice_shape(int32_t N, const float *x0, int64_t S, const int32_t *ij, con
     if (L.P >= (int64_t)INT32_MAX / 2) { why = "the padded lattice is too large for 32-bit cell indices"; return false; }
     const int64_t XY = (int64_t)L.X * L.Y;
     L.cidx.resize(N);
-    {
-        std::vector<uint8_t> used((size_t)L.P, 0);
-        for (int32_t i = 0; i < N; ++i) {
-            const int64_t ci = (cell[3 * (size_t)i] + 1) + L.X * (int64_t)(cell[3 * (size_t)i + 1] + 1) +
-                               XY * (cell[3 * (size_t)i + 2] + 1);
-            if (used[ci]) { why = "two masses on one grid point"; return false; }
-            used[ci] = 1;
-            L.cidx[i] = (int32_t)ci;
-        }
+    std::vector<uint8_t> used((size_t)L.P, 0);
+    for (int32_t i = 0; i < N; ++i) {
+        const int64_t ci = (cell[3 * (size_t)i] + 1) + L.X * (int64_t)(cell[3 * (size_t)i + 1] + 1) +
+                           XY * (cell[3 * (size_t)i + 2] + 1);
+        if (used[ci]) { why = "two masses on one grid point"; return false; }
+        used[ci] = 1;
+        L.cidx[i] = (int32_t)ci;
     }
     // springs: neighbouring cells, one per pair, one rest length per direction, one dashpot value
     L.c = c ? c[0] : c_uniform;
@@ -314,6 +314,19 @@ bool lattice_shape(int32_t N, const float *x0, int64_t S, const int32_t *ij, con
         slot = k[e];
         L.sumK[a] += k[e]; L.sumK[b] += k[e];
     }
+    // a slot without a spring: k = 0 where it touches a cell without a mass
+    // (that cell sits at the sentinel position, and the term vanishes), NaN
+    // between two masses (the kernel then tests every term)
+    L.guard = false;
+    for (int d = 0; d < ms::kLatDirs; ++d) {
+        const int64_t off = ms::lat_dx(d) + (int64_t)L.X * ms::lat_dy(d) + XY * ms::lat_dz(d);   // > 0
+        float *kd = &L.kf[(size_t)d * (size_t)L.P];
+        for (int64_t i = 0; i < L.P; ++i) {
+            if (kd[i] == kd[i]) continue;
+            if (used[(size_t)i] && i + off < L.P && used[(size_t)(i + off)]) L.guard = true;
+            else kd[i] = 0.f;
+        }
+    }
     return true;
 }
 
@@ -335,8 +348,9 @@ ms_status build_lattice(ms_sim *s, const ms_params *p, int32_t N, const float *x
     s->iperm = L.cidx;
     s->perm.clear();
     s->permuted = true;
-    // state of the padded cells: zero, w = NaN where there is no mass
-    std::vector<float4> ha(P, make_float4(0.f, 0.f, 0.f, 0.f));
+    // state of the padded cells: w = NaN and the sentinel position (zero
+    // velocity) where there is no mass
+    std::vector<float4> ha(P, make_float4(ms::kLatEmptyPos, ms::kLatEmptyPos, ms::kLatEmptyPos, 0.f));
     std::vector<float2> hb(P, make_float2(0.f, 0.f));
     std::vector<float> hw(P, std::numeric_limits<float>::quiet_NaN());
     std::vector<float4> hf;
@@ -379,18 +393,18 @@ ms_status build_lattice(ms_sim *s, const ms_params *p, int32_t N, const float *x
         s->lat.L[d] = L.L[d];
     }
     s->lat.c = L.c;
+    s->lat.guard = L.guard ? 1 : 0;
     s->lat.X = L.X; s->lat.Y = L.Y; s->lat.Z = L.Z;
     s->lat.nbx = L.nbx; s->lat.nby = L.nby; s->lat.nbz = L.nbz;
     if ((st = upload(s, &s->d_cidx, L.cidx.data(), (size_t)N)) != MS_OK) return st;
     if ((st = upload<float>(s, &s->stage, nullptr, (size_t)N * 6)) != MS_OK) return st;
     if (p->integrator == 3) {
         // stage states: cells without a mass are never written, and the next
-        // stage stages them as partners, so they start (and stay) zero
+        // stage stages them as partners, so they start (and stay) at the
+        // sentinel state
         for (int q = 0; q < 2; ++q) {
-            if ((st = upload<float4>(s, &s->rk_a[q], nullptr, P)) != MS_OK) return st;
-            if ((st = upload<float2>(s, &s->rk_b[q], nullptr, P)) != MS_OK) return st;
-            MS_CUDA_TRY(cudaMemsetAsync(s->rk_a[q], 0, sizeof(float4) * P, s->stream));
-            MS_CUDA_TRY(cudaMemsetAsync(s->rk_b[q], 0, sizeof(float2) * P, s->stream));
+            if ((st = upload(s, &s->rk_a[q], ha.data(), P)) != MS_OK) return st;
+            if ((st = upload(s, &s->rk_b[q], hb.data(), P)) != MS_OK) return st;
         }
         if ((st = upload<float4>(s, &s->rk_acc, nullptr, 2 * P)) != MS_OK) return st;
     }
@@ -1460,6 +1474,7 @@ ms_status ms_get_info(const ms_sim *s, ms_info_t *out)
     out->max_fwd_degree = s->max_fwd; out->max_back_degree = s->max_back;
     out->kernel = (s->persistent || s->grid_persistent) ? ms::kKernelPersistent : s->kernel;
     out->n_tiles = s->n_tiles; out->max_tile_local = s->max_tile_local;
+    out->lattice_guard = s->kernel == ms::kKernelLattice ? s->lat.guard : 0;
     return MS_OK;
 }
 

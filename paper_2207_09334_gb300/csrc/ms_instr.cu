@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kBrickCells) k_energy_lattice(const EnergyArgs
 #pragma unroll
         for (int d = 0; d < kLatDirs; ++d) {
             const float k = __ldg(g.kf[d] + i);
-            if (!(k == k)) continue;
+            if (!(k == k) || k == 0.f) continue;            // no spring, or one that adds no energy
             const float4 xj = __ldg(&a.sa[i + lat_dx(d) + g.X * (lat_dy(d) + g.Y * lat_dz(d))]);
             const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
             const float e = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - g.L[d];

@@ -154,7 +154,13 @@ struct LatticeArgs {
     float c;                     // dashpot coefficient of every spring
     int X, Y, Z;                 // padded extents (cells)
     int nbx, nby, nbz;           // bricks per axis
+    int guard;                   // 1: some neighbouring masses have no spring between them (k = NaN there)
 };
+// Cells without a mass (padding, holes) hold this position and zero velocity,
+// and every spring slot that touches one holds k = 0: the squared distance to
+// such a cell overflows to +inf, 1/l becomes 0, and the spring term is exactly
+// zero without a test.
+constexpr float kLatEmptyPos = 1e30f;
 // Tensor maps (TMA descriptors) of the lattice layout: one pair per state
 // buffer that a step reads -- its (x, y, z, vx) array as a 4-D float box and
 // its (vy, vz) array as a 3-D box of 8-byte elements -- and one of the 13

@@ -24,10 +24,13 @@
 //     one-cell-per-thread form), and the spring between a and b is evaluated
 //     once;
 //   * each spring term is eq. 2's Hooke term plus the axial dashpot (reading
-//     R2), written as f = [k (1 - L/l) + c (dv . d)/l^2] d with one hardware
-//     reciprocal square root; k comes from the cell's own array for a forward
-//     direction and from the partner's (kb[d][i] = kf[d][i - off(d)]) for a
-//     backward one;
+//     R2), written as f = s d, s = k + (c (dv . d)/l - k L)/l, with one
+//     hardware reciprocal square root; k comes from the cell's own array for a
+//     forward direction and from the partner's (kb[d][i] = kf[d][i - off(d)])
+//     for a backward one.  A cell without a mass sits at a far sentinel
+//     position with k = 0 on its springs, so its terms vanish exactly; only a
+//     lattice where some neighbouring masses lack a spring (k = NaN there)
+//     runs the variant that tests each term (GUARD);
 //   * then gravity, external force, ground contact, damping and the update of
 //     both masses (integrate_mass, shared with the other step kernels); the
 //     new state goes to the other buffer (Algorithm 1's synchronisation is
@@ -78,32 +81,39 @@ __device__ __forceinline__ float spring_L(const LatticeArgs &g)
 
 // Magnitude s of the spring term f = s d on the mass at (xi, vi) from the
 // partner (pa, pb) = ((x, y, z, vx), (vy, vz)), d = x_partner - x_self:
-//   s = k (l - L)/l + c (v_partner - v_self) . d / l^2
-// k = NaN (no spring) or a spring of zero length give s = NaN, returned as 0.
+//   s = k (l - L)/l + c (v_partner - v_self) . d / l^2 = k + (c dv.d / l - k L) / l.
+// A partner without a mass (at kLatEmptyPos, k = 0) gives l^2 = +inf, 1/l = 0
+// and s = 0.  A spring of zero length adds nothing: GUARD turns its NaN into
+// 0 (as it does for k = NaN, a missing spring between two masses); without
+// GUARD, l^2 is raised to 1e-30, s stays finite and d = 0.
+constexpr float kLatMinL2 = 1e-30f;
+
+template <bool GUARD>
 __device__ __forceinline__ float lattice_term(const float4 xi, const float3 vi, const float4 pa, const float2 pb,
                                               float k, float L, float c, float &dx, float &dy, float &dz)
 {
     dx = pa.x - xi.x; dy = pa.y - xi.y; dz = pa.z - xi.z;
     const float l2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float il = rsqrt_hw(l2);
-    const float t = fmaf(-(k * L), il, k);
+    const float il = rsqrt_hw(GUARD ? l2 : fmaxf(l2, kLatMinL2));
     const float dot = fmaf(pa.w - vi.x, dx, fmaf(pb.x - vi.y, dy, (pb.y - vi.z) * dz));
-    const float s = fmaf(c * dot, il * il, t);
-    return s == s ? s : 0.0f;
+    const float s = fmaf(fmaf(c * dot, il, -(k * L)), il, k);
+    if (GUARD) return s == s ? s : 0.0f;
+    return s;
 }
 
+template <bool GUARD>
 __device__ __forceinline__ void add_term(const float4 xi, const float3 vi, const float4 pa, const float2 pb, float k,
                                          float L, float c, float &fx, float &fy, float &fz)
 {
     float dx, dy, dz;
-    const float s = lattice_term(xi, vi, pa, pb, k, L, c, dx, dy, dz);
+    const float s = lattice_term<GUARD>(xi, vi, pa, pb, k, L, c, dx, dy, dz);
     fx = fmaf(s, dx, fx); fy = fmaf(s, dy, fy); fz = fmaf(s, dz, fz);
 }
 
 // Springs of the pair (a at z, b at z + 1) into the column (DX, DY): partner
 // cells z - 1 .. z + 2 read once each.  The centre column (0, 0) holds a and b
 // themselves: a's spring to z - 1, the a-b spring once, b's spring to z + 2.
-template <int DX, int DY>
+template <bool GUARD, int DX, int DY>
 __device__ __forceinline__ void column(const LatticeArgs &g, const float4 *spa, const float2 *spb, int sa_, int ia,
                                        int ib, const float4 xa, const float3 va, const float4 xb, const float3 vb,
                                        float3 &Fa, float3 &Fb)
@@ -113,53 +123,55 @@ __device__ __forceinline__ void column(const LatticeArgs &g, const float4 *spa, 
     {   // z - 1: a only
         const float4 p = spa[c0 - halo_off(0, 0, 1)];
         const float2 q = spb[c0 - halo_off(0, 0, 1)];
-        add_term(xa, va, p, q, spring_k<DX, DY, -1>(g, ia), spring_L<DX, DY, -1>(g), c, Fa.x, Fa.y, Fa.z);
+        add_term<GUARD>(xa, va, p, q, spring_k<DX, DY, -1>(g, ia), spring_L<DX, DY, -1>(g), c, Fa.x, Fa.y, Fa.z);
     }
     if constexpr (DX != 0 || DY != 0) {
         {   // z: a in-plane, b one below
             const float4 p = spa[c0];
             const float2 q = spb[c0];
-            add_term(xa, va, p, q, spring_k<DX, DY, 0>(g, ia), spring_L<DX, DY, 0>(g), c, Fa.x, Fa.y, Fa.z);
-            add_term(xb, vb, p, q, spring_k<DX, DY, -1>(g, ib), spring_L<DX, DY, -1>(g), c, Fb.x, Fb.y, Fb.z);
+            add_term<GUARD>(xa, va, p, q, spring_k<DX, DY, 0>(g, ia), spring_L<DX, DY, 0>(g), c, Fa.x, Fa.y, Fa.z);
+            add_term<GUARD>(xb, vb, p, q, spring_k<DX, DY, -1>(g, ib), spring_L<DX, DY, -1>(g), c, Fb.x, Fb.y, Fb.z);
         }
         {   // z + 1: a one above, b in-plane
             const float4 p = spa[c0 + halo_off(0, 0, 1)];
             const float2 q = spb[c0 + halo_off(0, 0, 1)];
-            add_term(xa, va, p, q, spring_k<DX, DY, 1>(g, ia), spring_L<DX, DY, 1>(g), c, Fa.x, Fa.y, Fa.z);
-            add_term(xb, vb, p, q, spring_k<DX, DY, 0>(g, ib), spring_L<DX, DY, 0>(g), c, Fb.x, Fb.y, Fb.z);
+            add_term<GUARD>(xa, va, p, q, spring_k<DX, DY, 1>(g, ia), spring_L<DX, DY, 1>(g), c, Fa.x, Fa.y, Fa.z);
+            add_term<GUARD>(xb, vb, p, q, spring_k<DX, DY, 0>(g, ib), spring_L<DX, DY, 0>(g), c, Fb.x, Fb.y, Fb.z);
         }
     } else {
         // the a-b spring, once: +s d on a, -s d on b
         float dx, dy, dz;
         const float4 pb4 = make_float4(xb.x, xb.y, xb.z, vb.x);
-        const float s = lattice_term(xa, va, pb4, make_float2(vb.y, vb.z), __ldg(g.kf[fwd_index(0, 0, 1)] + ia),
-                                     g.L[fwd_index(0, 0, 1)], c, dx, dy, dz);
+        const float s = lattice_term<GUARD>(xa, va, pb4, make_float2(vb.y, vb.z),
+                                            __ldg(g.kf[fwd_index(0, 0, 1)] + ia), g.L[fwd_index(0, 0, 1)], c, dx,
+                                            dy, dz);
         Fa.x = fmaf(s, dx, Fa.x); Fa.y = fmaf(s, dy, Fa.y); Fa.z = fmaf(s, dz, Fa.z);
         Fb.x = fmaf(-s, dx, Fb.x); Fb.y = fmaf(-s, dy, Fb.y); Fb.z = fmaf(-s, dz, Fb.z);
     }
     {   // z + 2: b only
         const float4 p = spa[c0 + halo_off(0, 0, 2)];
         const float2 q = spb[c0 + halo_off(0, 0, 2)];
-        add_term(xb, vb, p, q, spring_k<DX, DY, 1>(g, ib), spring_L<DX, DY, 1>(g), c, Fb.x, Fb.y, Fb.z);
+        add_term<GUARD>(xb, vb, p, q, spring_k<DX, DY, 1>(g, ib), spring_L<DX, DY, 1>(g), c, Fb.x, Fb.y, Fb.z);
     }
 }
 
 // all springs of the pair (a, b), column by column
+template <bool GUARD>
 __device__ __forceinline__ void pair_forces(const LatticeArgs &g, const float4 *spa, const float2 *spb, int s0, int ia,
                                             int ib, const float4 xa, const float3 va, const float4 xb,
                                             const float3 vb, float3 &Fa, float3 &Fb)
 {
     Fa = make_float3(0.f, 0.f, 0.f);
     Fb = Fa;
-    column<-1, -1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
-    column< 0, -1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
-    column< 1, -1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
-    column<-1,  0>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
-    column< 0,  0>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
-    column< 1,  0>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
-    column<-1,  1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
-    column< 0,  1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
-    column< 1,  1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
+    column<GUARD, -1, -1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
+    column<GUARD,  0, -1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
+    column<GUARD,  1, -1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
+    column<GUARD, -1,  0>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
+    column<GUARD,  0,  0>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
+    column<GUARD,  1,  0>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
+    column<GUARD, -1,  1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
+    column<GUARD,  0,  1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
+    column<GUARD,  1,  1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
 }
 
 // one staged block: (x, y, z, vx) then (vy, vz) of the 18 x 10 x 10 cells
@@ -170,7 +182,7 @@ constexpr uint32_t kStageBytes = (kStageCopied + 127) / 128 * 128;   // stage st
 static_assert(kStageA % 128 == 0 && kStageBytes % 128 == 0, "tensor copies need 128-byte aligned destinations");
 constexpr int kLatCtasPerSm = 2;
 
-template <bool HAS_FEXT, bool RK4>
+template <bool HAS_FEXT, bool RK4, bool GUARD>
 __global__ void __launch_bounds__(kLatThreads, kLatCtasPerSm)
 k_step_lattice(const StepArgs a, const LatticeArgs g, const __grid_constant__ CUtensorMap map_a,
                const __grid_constant__ CUtensorMap map_b, const __grid_constant__ CUtensorMap map_k)
@@ -229,7 +241,7 @@ k_step_lattice(const StepArgs a, const LatticeArgs g, const __grid_constant__ CU
             const float4 xb = make_float4(r.x, r.y, r.z, wb);
             const float3 vb = make_float3(r.w, t.x, t.y);
             float3 Fa, Fb;
-            pair_forces(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
+            pair_forces<GUARD>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
             float4 xn, vn;
             if (wa == wa) {
                 integrate_mass<HAS_FEXT, RK4>(a, ia, xa, make_float4(va.x, va.y, va.z, 0.f), Fa.x, Fa.y, Fa.z, xn, vn);
@@ -327,7 +339,7 @@ cudaError_t launch_step_lattice(const StepArgs &a, const LatticeArgs &g, const L
     if (q == m.n) return cudaErrorInvalidValue;                // a buffer without tensor maps
     const unsigned grid = (unsigned)std::min<long long>(nbricks, (long long)kLatCtasPerSm * std::max(n_sms, 1));
     const size_t smem = 2 * (size_t)kStageBytes;
-#define MS_LAUNCH_L(F, R)                                                                                  \
+#define MS_LAUNCH_L(F, R, G)                                                                               \
     do {                                                                                                   \
         static std::atomic<uint64_t> opted{0};                                                             \
         int dev = 0;                                                                                       \
@@ -335,15 +347,20 @@ cudaError_t launch_step_lattice(const StepArgs &a, const LatticeArgs &g, const L
         if (e_ != cudaSuccess) return e_;                                                                  \
         const uint64_t bit = dev < 64 ? (uint64_t)1 << dev : 0;                                            \
         if (!bit || !(opted.load() & bit)) {                                                               \
-            e_ = cudaFuncSetAttribute(k_step_lattice<F, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+            e_ = cudaFuncSetAttribute(k_step_lattice<F, R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
             if (e_ != cudaSuccess) return e_;                                                              \
             if (bit) opted.fetch_or(bit);                                                                  \
         }                                                                                                  \
-        k_step_lattice<F, R><<<grid, kLatThreads, smem, st>>>(a, g, m.a[q], m.b[q], m.k);                  \
+        k_step_lattice<F, R, G><<<grid, kLatThreads, smem, st>>>(a, g, m.a[q], m.b[q], m.k);               \
     } while (0)
     const bool hf = a.fext != nullptr;
-    if (a.integrator == 3) { if (hf) MS_LAUNCH_L(true, true); else MS_LAUNCH_L(false, true); }
-    else { if (hf) MS_LAUNCH_L(true, false); else MS_LAUNCH_L(false, false); }
+    if (g.guard) {
+        if (a.integrator == 3) { if (hf) MS_LAUNCH_L(true, true, true); else MS_LAUNCH_L(false, true, true); }
+        else { if (hf) MS_LAUNCH_L(true, false, true); else MS_LAUNCH_L(false, false, true); }
+    } else {
+        if (a.integrator == 3) { if (hf) MS_LAUNCH_L(true, true, false); else MS_LAUNCH_L(false, true, false); }
+        else { if (hf) MS_LAUNCH_L(true, false, false); else MS_LAUNCH_L(false, false, false); }
+    }
 #undef MS_LAUNCH_L
     return cudaGetLastError();
 }

@@ -4,9 +4,13 @@ k stored per spring) against the FP64 oracle on identical seeded inputs.
 Gates are those of the other step tests: max |x_gpu - x_oracle| <= 1e-5 of the
 body size after a contact-free run, <= 1e-4 after 200 steps with ground
 contact (and the centre-of-mass displacement within 1 %).  The lattices are
-sized so that bricks of 16 x 8 x 4 cells are cut by a ragged tail on every
-axis, and some have holes (cells without a mass, inside a brick) and missing
-springs between present masses.
+sized so that bricks of 16 x 8 x 8 cells are cut by a ragged tail on every
+axis, and some have holes (cells without a mass, inside a brick) with or
+without missing springs between present masses.  A lattice where every pair
+of neighbouring masses has its spring runs the kernel without a per-term
+test (cells without a mass sit at a far sentinel position with k = 0); one
+with a missing spring between two masses runs the variant that tests every
+term.
 """
 import numpy as np
 import pytest
@@ -68,9 +72,12 @@ def drop(s, keep_mass, keep_spring=None):
     return out
 
 
-def run_gpu(ms, s, p, n, chunks=1, integrator="symplectic_euler", kernel="lattice"):
+def run_gpu(ms, s, p, n, chunks=1, integrator="symplectic_euler", kernel="lattice", guard=None):
     with ms.Sim(s, p, kernel=kernel, integrator=integrator) as sim:
-        assert sim.info()["kernel"] == (4 if kernel == "lattice" else sim.info()["kernel"])
+        info = sim.info()
+        assert info["kernel"] == (4 if kernel == "lattice" else info["kernel"])
+        if guard is not None:
+            assert info["lattice_guard"] == guard
         done = 0
         for q in range(chunks):
             todo = n * (q + 1) // chunks - done
@@ -85,7 +92,7 @@ def test_ragged_throughput_lattice_200_steps(ms, ora):
     brick; gravity, anchored bottom layer, 200 steps in two calls."""
     s = ragged_lattice()
     p = synth.throughput_params()
-    xg, vg = run_gpu(ms, s, p, 200, chunks=2)
+    xg, vg = run_gpu(ms, s, p, 200, chunks=2, guard=0)
     xo, vo = ora.run(s, f32p(p), 200)
     assert np.abs(xg - xo).max() <= 1e-5 * body_size(s), np.abs(xg - xo).max()
     assert np.abs(vg - vo).max() <= 1e-3
@@ -94,8 +101,9 @@ def test_ragged_throughput_lattice_200_steps(ms, ora):
 def test_lattice_with_holes_and_missing_springs(ms, ora):
     """Cells without a mass inside the bricks (a random 10 % of the masses
     removed with their springs), and 15 % of the remaining springs removed
-    between masses that stay: those pairs read k = -1 and must exert nothing,
-    the dashpot included.  External force on some masses."""
+    between masses that stay: those pairs read k = NaN, the kernel tests every
+    term, and they must exert nothing, the dashpot included.  External force
+    on some masses."""
     s = ragged_lattice(nx=29, ny=13, nz=9, seed=4)
     rng = np.random.default_rng(5)
     keep_m = rng.random(s["x"].shape[0]) > 0.10
@@ -104,8 +112,30 @@ def test_lattice_with_holes_and_missing_springs(ms, ora):
     t = drop(s, keep_m, keep_s)
     t["fext"] = (2e-4 * rng.standard_normal(t["x"].shape)).astype(np.float32)
     p = synth.throughput_params()
-    xg, _ = run_gpu(ms, t, p, 150)
+    xg, _ = run_gpu(ms, t, p, 150, guard=1)
     xo, _ = ora.run(t, f32p(p), 150)
+    assert np.abs(xg - xo).max() <= 1e-5 * body_size(t), np.abs(xg - xo).max()
+
+
+@pytest.mark.parametrize("integ", ["symplectic_euler", "rk4"])
+def test_lattice_with_holes_and_every_spring(ms, ora, integ):
+    """Holes (a random 12 % of the masses removed with their springs) with
+    every spring between the remaining neighbours kept: the kernel runs
+    without the per-term test, and the cells without a mass (the sentinel
+    position, k = 0 on their slots) must exert nothing, also when staged from
+    the RK4 stage buffers.  RK4 on the soft lattice of the integrator test."""
+    s = ragged_lattice(nx=29, ny=13, nz=9, seed=6)
+    p = synth.throughput_params()
+    if integ == "rk4":
+        s["k"] = np.random.default_rng(12).uniform(50.0, 150.0, s["ij"].shape[0]).astype(np.float32)
+        s["v"] = (0.02 * np.random.default_rng(13).standard_normal(s["v"].shape)).astype(np.float32)
+        p = synth.params(dt=2e-5, g=(0, 0, -9.81))
+    rng = np.random.default_rng(7)
+    keep_m = rng.random(s["x"].shape[0]) > 0.12
+    keep_m[: 29 * 13] = True
+    t = drop(s, keep_m)
+    xg, _ = run_gpu(ms, t, p, 150, chunks=2, integrator=integ, guard=0)
+    xo, _ = ora.run(t, f32p(p), 150, integrator=integ)
     assert np.abs(xg - xo).max() <= 1e-5 * body_size(t), np.abs(xg - xo).max()
 
 
