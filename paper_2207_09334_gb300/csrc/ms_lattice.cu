@@ -88,26 +88,45 @@ __device__ __forceinline__ float spring_L(const LatticeArgs &g)
 // GUARD, l^2 is raised to 1e-30, s stays finite and d = 0.
 constexpr float kLatMinL2 = 1e-30f;
 
-template <bool GUARD>
-__device__ __forceinline__ float lattice_term(const float4 xi, const float3 vi, const float4 pa, const float2 pb,
-                                              float k, float L, float c, float &dx, float &dy, float &dz)
+// A mass as the spring terms use it: the negated pairs (-x, -y), (-z, -vx) and
+// (-vy, -vz).  A partner's state arrives from shared memory as the register
+// pairs (x, y), (z, vx) of one 16-byte load and (vy, vz) of one 8-byte load,
+// so each pair of differences is one packed FP32x2 add (sm_100 and later),
+// rounded as the two scalar subtractions would be.  The force accumulates as
+// (fx, fy) in one packed FMA and fz.
+struct Own { float2 nxy, nzv, nvyz; };
+struct Force { float2 xy; float z; };
+
+__device__ __forceinline__ Own own_of(const float4 x, const float3 v)
 {
-    dx = pa.x - xi.x; dy = pa.y - xi.y; dz = pa.z - xi.z;
-    const float l2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    return {make_float2(-x.x, -x.y), make_float2(-x.z, -v.x), make_float2(-v.y, -v.z)};
+}
+
+template <bool GUARD>
+__device__ __forceinline__ float lattice_term(const Own &o, const float4 pa, const float2 pb, float k, float L,
+                                              float c, float2 &dxy, float &dz)
+{
+    dxy = __fadd2_rn(make_float2(pa.x, pa.y), o.nxy);
+    const float2 zv = __fadd2_rn(make_float2(pa.z, pa.w), o.nzv);       // (dz, dvx)
+    const float2 vyz = __fadd2_rn(pb, o.nvyz);                          // (dvy, dvz)
+    dz = zv.x;
+    const float l2 = fmaf(dxy.x, dxy.x, fmaf(dxy.y, dxy.y, dz * dz));
     const float il = rsqrt_hw(GUARD ? l2 : fmaxf(l2, kLatMinL2));
-    const float dot = fmaf(pa.w - vi.x, dx, fmaf(pb.x - vi.y, dy, (pb.y - vi.z) * dz));
+    const float dot = fmaf(zv.y, dxy.x, fmaf(vyz.x, dxy.y, vyz.y * dz));
     const float s = fmaf(fmaf(c * dot, il, -(k * L)), il, k);
     if (GUARD) return s == s ? s : 0.0f;
     return s;
 }
 
 template <bool GUARD>
-__device__ __forceinline__ void add_term(const float4 xi, const float3 vi, const float4 pa, const float2 pb, float k,
-                                         float L, float c, float &fx, float &fy, float &fz)
+__device__ __forceinline__ void add_term(const Own &o, const float4 pa, const float2 pb, float k, float L, float c,
+                                         Force &F)
 {
-    float dx, dy, dz;
-    const float s = lattice_term<GUARD>(xi, vi, pa, pb, k, L, c, dx, dy, dz);
-    fx = fmaf(s, dx, fx); fy = fmaf(s, dy, fy); fz = fmaf(s, dz, fz);
+    float2 dxy;
+    float dz;
+    const float s = lattice_term<GUARD>(o, pa, pb, k, L, c, dxy, dz);
+    F.xy = __ffma2_rn(make_float2(s, s), dxy, F.xy);
+    F.z = fmaf(s, dz, F.z);
 }
 
 // Springs of the pair (a at z, b at z + 1) into the column (DX, DY): partner
@@ -115,43 +134,45 @@ __device__ __forceinline__ void add_term(const float4 xi, const float3 vi, const
 // themselves: a's spring to z - 1, the a-b spring once, b's spring to z + 2.
 template <bool GUARD, int DX, int DY>
 __device__ __forceinline__ void column(const LatticeArgs &g, const float4 *spa, const float2 *spb, int sa_, int ia,
-                                       int ib, const float4 xa, const float3 va, const float4 xb, const float3 vb,
-                                       float3 &Fa, float3 &Fb)
+                                       int ib, const Own &oa, const Own &ob, const float4 xb, const float3 vb,
+                                       Force &Fa, Force &Fb)
 {
     const int c0 = sa_ + halo_off(DX, DY, 0);
     const float c = g.c;
     {   // z - 1: a only
         const float4 p = spa[c0 - halo_off(0, 0, 1)];
         const float2 q = spb[c0 - halo_off(0, 0, 1)];
-        add_term<GUARD>(xa, va, p, q, spring_k<DX, DY, -1>(g, ia), spring_L<DX, DY, -1>(g), c, Fa.x, Fa.y, Fa.z);
+        add_term<GUARD>(oa, p, q, spring_k<DX, DY, -1>(g, ia), spring_L<DX, DY, -1>(g), c, Fa);
     }
     if constexpr (DX != 0 || DY != 0) {
         {   // z: a in-plane, b one below
             const float4 p = spa[c0];
             const float2 q = spb[c0];
-            add_term<GUARD>(xa, va, p, q, spring_k<DX, DY, 0>(g, ia), spring_L<DX, DY, 0>(g), c, Fa.x, Fa.y, Fa.z);
-            add_term<GUARD>(xb, vb, p, q, spring_k<DX, DY, -1>(g, ib), spring_L<DX, DY, -1>(g), c, Fb.x, Fb.y, Fb.z);
+            add_term<GUARD>(oa, p, q, spring_k<DX, DY, 0>(g, ia), spring_L<DX, DY, 0>(g), c, Fa);
+            add_term<GUARD>(ob, p, q, spring_k<DX, DY, -1>(g, ib), spring_L<DX, DY, -1>(g), c, Fb);
         }
         {   // z + 1: a one above, b in-plane
             const float4 p = spa[c0 + halo_off(0, 0, 1)];
             const float2 q = spb[c0 + halo_off(0, 0, 1)];
-            add_term<GUARD>(xa, va, p, q, spring_k<DX, DY, 1>(g, ia), spring_L<DX, DY, 1>(g), c, Fa.x, Fa.y, Fa.z);
-            add_term<GUARD>(xb, vb, p, q, spring_k<DX, DY, 0>(g, ib), spring_L<DX, DY, 0>(g), c, Fb.x, Fb.y, Fb.z);
+            add_term<GUARD>(oa, p, q, spring_k<DX, DY, 1>(g, ia), spring_L<DX, DY, 1>(g), c, Fa);
+            add_term<GUARD>(ob, p, q, spring_k<DX, DY, 0>(g, ib), spring_L<DX, DY, 0>(g), c, Fb);
         }
     } else {
         // the a-b spring, once: +s d on a, -s d on b
-        float dx, dy, dz;
-        const float4 pb4 = make_float4(xb.x, xb.y, xb.z, vb.x);
-        const float s = lattice_term<GUARD>(xa, va, pb4, make_float2(vb.y, vb.z),
-                                            __ldg(g.kf[fwd_index(0, 0, 1)] + ia), g.L[fwd_index(0, 0, 1)], c, dx,
-                                            dy, dz);
-        Fa.x = fmaf(s, dx, Fa.x); Fa.y = fmaf(s, dy, Fa.y); Fa.z = fmaf(s, dz, Fa.z);
-        Fb.x = fmaf(-s, dx, Fb.x); Fb.y = fmaf(-s, dy, Fb.y); Fb.z = fmaf(-s, dz, Fb.z);
+        float2 dxy;
+        float dz;
+        const float s = lattice_term<GUARD>(oa, make_float4(xb.x, xb.y, xb.z, vb.x), make_float2(vb.y, vb.z),
+                                            __ldg(g.kf[fwd_index(0, 0, 1)] + ia), g.L[fwd_index(0, 0, 1)], c, dxy,
+                                            dz);
+        Fa.xy = __ffma2_rn(make_float2(s, s), dxy, Fa.xy);
+        Fa.z = fmaf(s, dz, Fa.z);
+        Fb.xy = __ffma2_rn(make_float2(-s, -s), dxy, Fb.xy);
+        Fb.z = fmaf(-s, dz, Fb.z);
     }
     {   // z + 2: b only
         const float4 p = spa[c0 + halo_off(0, 0, 2)];
         const float2 q = spb[c0 + halo_off(0, 0, 2)];
-        add_term<GUARD>(xb, vb, p, q, spring_k<DX, DY, 1>(g, ib), spring_L<DX, DY, 1>(g), c, Fb.x, Fb.y, Fb.z);
+        add_term<GUARD>(ob, p, q, spring_k<DX, DY, 1>(g, ib), spring_L<DX, DY, 1>(g), c, Fb);
     }
 }
 
@@ -159,19 +180,21 @@ __device__ __forceinline__ void column(const LatticeArgs &g, const float4 *spa, 
 template <bool GUARD>
 __device__ __forceinline__ void pair_forces(const LatticeArgs &g, const float4 *spa, const float2 *spb, int s0, int ia,
                                             int ib, const float4 xa, const float3 va, const float4 xb,
-                                            const float3 vb, float3 &Fa, float3 &Fb)
+                                            const float3 vb, float3 &Fa3, float3 &Fb3)
 {
-    Fa = make_float3(0.f, 0.f, 0.f);
-    Fb = Fa;
-    column<GUARD, -1, -1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
-    column<GUARD,  0, -1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
-    column<GUARD,  1, -1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
-    column<GUARD, -1,  0>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
-    column<GUARD,  0,  0>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
-    column<GUARD,  1,  0>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
-    column<GUARD, -1,  1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
-    column<GUARD,  0,  1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
-    column<GUARD,  1,  1>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
+    const Own oa = own_of(xa, va), ob = own_of(xb, vb);
+    Force Fa{make_float2(0.f, 0.f), 0.f}, Fb = Fa;
+    column<GUARD, -1, -1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, Fa, Fb);
+    column<GUARD,  0, -1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, Fa, Fb);
+    column<GUARD,  1, -1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, Fa, Fb);
+    column<GUARD, -1,  0>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, Fa, Fb);
+    column<GUARD,  0,  0>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, Fa, Fb);
+    column<GUARD,  1,  0>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, Fa, Fb);
+    column<GUARD, -1,  1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, Fa, Fb);
+    column<GUARD,  0,  1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, Fa, Fb);
+    column<GUARD,  1,  1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, Fa, Fb);
+    Fa3 = make_float3(Fa.xy.x, Fa.xy.y, Fa.z);
+    Fb3 = make_float3(Fb.xy.x, Fb.xy.y, Fb.z);
 }
 
 // one staged block: (x, y, z, vx) then (vy, vz) of the 18 x 10 x 10 cells
