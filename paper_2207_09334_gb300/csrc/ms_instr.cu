@@ -122,7 +122,9 @@ __global__ void __launch_bounds__(kTileMasses) k_energy_tiled(const EnergyArgs a
 }
 
 // lattice layout: one CTA per brick, one thread per cell; each spring once,
-// from the cell it leaves in a forward direction (k = NaN: no spring)
+// from the cell it leaves in a forward direction (k = NaN: no spring between
+// two masses; k = 0: a slot that touches a cell without a mass, or a spring
+// of zero stiffness, either way no energy)
 __global__ void __launch_bounds__(kBrickCells) k_energy_lattice(const EnergyArgs a, const LatticeArgs g)
 {
     const int tid = threadIdx.x;

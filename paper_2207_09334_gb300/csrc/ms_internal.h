@@ -130,10 +130,10 @@ struct StepArgs {
 //     padded lattice index; the caller's mass c sits at cidx[c].
 //   * Each of the 13 forward directions d (lat_dx/dy/dz below) has its own
 //     array over the padded cells: kf[d][i] = k of the spring from cell i to
-//     cell i + off(d), or NaN where there is none (a missing pair, a cell
-//     without mass, the guard band).
-//   * Cells without a mass have w = NaN and a zero state; no kernel integrates
-//     them.
+//     cell i + off(d); 0 on a slot that touches a cell without a mass (a
+//     hole, the guard band), NaN between two masses that have no spring.
+//   * Cells without a mass have w = NaN, the position kLatEmptyPos on every
+//     axis and zero velocity; no kernel integrates them.
 constexpr int kKernelLattice = 4;
 constexpr int kBrickX = 16, kBrickY = 8, kBrickZ = 8;
 constexpr int kBrickCells = kBrickX * kBrickY * kBrickZ;        // 1024 cells per brick
