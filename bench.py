@@ -765,9 +765,10 @@ def run_cube(args, world, rank, local):
 
 def run_sweep(args, world, rank, local):
     """Element update rate against system size (the paper's rate-vs-size
-    experiment): throughput lattices of n^3 masses, the default kernel, and the
+    experiment): throughput lattices of n^3 masses, the default kernel, the
     persistent kernel where the system fits it (a thread-block cluster up to
-    8192 masses, then one cooperative launch while every tile is resident)."""
+    8192 masses, then one cooperative launch while every tile is resident),
+    and the lattice kernel where it is not already the default."""
     import torch
     import paper_2207_09334_gb300 as ms
     torch.cuda.set_device(local)
@@ -778,11 +779,17 @@ def run_sweep(args, world, rank, local):
     for n in args.sweep_sizes:
         s, p = lattice_workload(n)
         N, S = s["x"].shape[0], s["ij"].shape[0]
-        for kernel in ("auto", "persistent"):
+        auto_kernel = None
+        for kernel in ("auto", "persistent", "lattice"):
             try:
                 sim = ms.Sim(s, p, kernel=None if kernel == "auto" else kernel, stream=stream)
             except ms.MsError:
                 continue                            # the persistent kernel does not take this size
+            if kernel == "auto":
+                auto_kernel = sim.info()["kernel"]
+            elif sim.info()["kernel"] == auto_kernel:
+                sim.close()                         # already measured as the default
+                continue
             with sim:
                 steps = max(20, min(2000, int(2e9 // (N + S))))     # about 2e9 element updates per point
                 sim.step(max(3, steps // 10))
