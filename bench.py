@@ -537,6 +537,7 @@ def measure_adjoint(args, reps, local, evals=2, warm=1):
         for _ in range(warm):
             adj.gradients(nsteps, phase, logk)
         torch.cuda.synchronize()
+        threads = adj.threads
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         reps.barrier()
         e0.record(stream)
@@ -549,7 +550,8 @@ def measure_adjoint(args, reps, local, evals=2, warm=1):
     return {"value": reps.world * args.walkers * nsteps * synth.voxel_params()["dt"] * evals / (ms_total * 1e-3),
             "unit": "robot-sim-s/s (forward + reverse)", "ms_per_evaluation": ms_total / evals,
             "config": {"workload": f"{args.walkers} walkers of 8^3 voxels (seed 3), {nsteps} steps, checkpoint every "
-                                   "100; one evaluation = loss + gradient for all walkers", "evaluations": evals},
+                                   "100; one evaluation = loss + gradient for all walkers", "evaluations": evals,
+                       "threads_per_robot": threads},
             "mean_travel_m": float(loss.mean())}
 
 
@@ -859,7 +861,7 @@ def run_adjoint(args, world, rank, local):
             "data": "synthetic (seeded)",
             "config": {"workload": f"{args.walkers} walkers of 8^3 voxels (seed 3), {nsteps} steps, checkpoint every 100; "
                                    "one bench step = one loss + gradient evaluation for all walkers",
-                       "voxels": int(adj.n_voxels), "masses": int(adj.n_masses)},
+                       "voxels": int(adj.n_voxels), "masses": int(adj.n_masses), "threads_per_robot": adj.threads},
             "mean_travel_m": float(loss.mean()), "grad_phase_rms": float(gp.pow(2).mean().sqrt()),
             "grad_logk_rms": float(gk.pow(2).mean().sqrt()),
             "gpu_launches": 5 * args.steps, "clocks": clk.summary()}

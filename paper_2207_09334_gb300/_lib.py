@@ -92,6 +92,8 @@ SIGNATURES = {
                              C.POINTER(MsAllocator), VP, C.POINTER(VP)]),
     "msa_gradients": (C.c_int, [VP, I32, VP, VP, VP, VP, VP, VP, I32]),
     "msa_sizes": (C.c_int, [VP, C.POINTER(I64), C.POINTER(I64)]),
+    "msa_set_threads": (C.c_int, [VP, I32]),
+    "msa_threads": (I32, [VP]),
     "msa_destroy": (C.c_int, [VP]),
     "mlp_create": (C.c_int, [I32, I32, I32, C.c_uint64, C.POINTER(MsAllocator), VP, C.POINTER(VP)]),
     "mlp_num_params": (I64, [VP]),

@@ -24,7 +24,7 @@ class Adjoint:
 
     def __init__(self, materials, material_table, freq, voxel_edge, voxel_mass, params,
                  checkpoint_every: int = 100, max_steps: int = 2000, stream=None,
-                 use_torch_allocator: bool = True):
+                 use_torch_allocator: bool = True, threads: int = 0):
         lib = _lib.load()
         self._lib = lib
         self.dims = np.array([[m.shape[2], m.shape[1], m.shape[0]] for m in materials], np.int32)
@@ -49,6 +49,14 @@ class Adjoint:
         self.n_voxels, self.n_masses = nv.value, nm.value
         counts = self.dims.prod(axis=1)
         self.voxel_robot = np.repeat(np.arange(self.n_robots), counts)
+        if threads:
+            check(lib.msa_set_threads(h, int(threads)))
+
+    @property
+    def threads(self) -> int:
+        """Threads per robot of the adjoint kernel (256, 512 or 1024; chosen
+        from the population unless given to the constructor)."""
+        return int(self._lib.msa_threads(self.h))
 
     def gradients(self, nsteps: int, phase, logk, seed_x=None):
         """Returns (loss[n_robots], d loss_r / d phase, d loss_r / d logk).

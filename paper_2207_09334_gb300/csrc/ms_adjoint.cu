@@ -38,7 +38,11 @@
 namespace ms {
 namespace {
 
-constexpr int kAdjThreads = 256;
+// Threads per robot (one CTA each): 256, 512 or 1024, every one at 64
+// registers.  More threads per robot hide more of the latency of each step's
+// record loads; fewer let more robots run at once.  msa_create picks the size
+// from the population (choose_threads), msa_set_threads overrides it.
+constexpr int kAdjThreadChoices[3] = {1024, 512, 256};
 constexpr int kAdjMaxMasses = 1024;
 constexpr int kAdjMaxVoxels = 4096;
 
@@ -90,6 +94,7 @@ __global__ void k_adj_merge(const int2 *slot_range, const RobotDev *robots, cons
     }
 }
 
+template <int T>
 __device__ __forceinline__ float block_sum(float v, float *red)
 {
     v = warp_sum(v);
@@ -98,7 +103,7 @@ __device__ __forceinline__ float block_sum(float v, float *red)
     if (lane == 0) red[warp] = v;
     __syncthreads();
     float t = 0.f;
-    for (int w = 0; w < kAdjThreads / 32; ++w) t += red[w];
+    for (int w = 0; w < T / 32; ++w) t += red[w];
     return t;
 }
 
@@ -129,10 +134,11 @@ __device__ __forceinline__ float spring_adjoint(const float4 xi, const float4 vi
     return wu;
 }
 
-__global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a)
+template <int T>
+__global__ void __launch_bounds__(T, 65536 / (64 * T)) k_adjoint(const AdjArgs a)
 {
     extern __shared__ float4 sm4[];
-    __shared__ float red[kAdjThreads / 32];
+    __shared__ float red[T / 32];
     const int r = blockIdx.x, tid = threadIdx.x;
     const RobotDev R = a.robots[r];
     const int n = R.n, nv = R.n_vox;
@@ -144,23 +150,23 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a)
     float4 *ck = a.ckpt + (size_t)r * a.n_ckpt * a.n_cap * 2;
     float4 *sg = a.seg + (size_t)r * a.K * a.n_cap * 3;
 
-    for (int i = tid; i < n; i += kAdjThreads) {
+    for (int i = tid; i < n; i += T) {
         xs[i] = a.st0[2 * (R.mass_base + i)];
         vs[i] = a.st0[2 * (R.mass_base + i) + 1];
     }
-    for (int v = tid; v < nv; v += kAdjThreads) { gph[v] = 0.f; glk[v] = 0.f; }
+    for (int v = tid; v < nv; v += T) { gph[v] = 0.f; glk[v] = 0.f; }
     __syncthreads();
 
     // ---- forward pass with checkpoints ----
     for (int step = 0; step < a.nsteps; ++step) {
         if (step % a.K == 0) {
             float4 *c = ck + (size_t)(step / a.K) * a.n_cap * 2;
-            for (int i = tid; i < n; i += kAdjThreads) { c[2 * i] = xs[i]; c[2 * i + 1] = vs[i]; }
+            for (int i = tid; i < n; i += T) { c[2 * i] = xs[i]; c[2 * i + 1] = vs[i]; }
         }
         const float2 sc = a.sc[step];
-        for (int i = tid; i < n; i += kAdjThreads) aa[i] = robot_force(rc, R.slice_base, rec_base, i, xs, vs, sc.x, sc.y);
+        for (int i = tid; i < n; i += T) aa[i] = robot_force(rc, R.slice_base, rec_base, i, xs, vs, sc.x, sc.y);
         __syncthreads();
-        for (int i = tid; i < n; i += kAdjThreads) {
+        for (int i = tid; i < n; i += T) {
             float4 x = xs[i], v = vs[i];
             robot_integrate(e, x, v, aa[i]);
             xs[i] = x; vs[i] = v;
@@ -170,7 +176,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a)
 
     // ---- loss and terminal adjoint ----
     float part = 0.f;
-    for (int i = tid; i < n; i += kAdjThreads) {
+    for (int i = tid; i < n; i += T) {
         const float4 x = xs[i];
         float4 s4;
         if (a.seed) s4 = a.seed[R.mass_base + i];
@@ -180,7 +186,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a)
         lv[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (!isfinite(x.x + x.y + x.z)) atomicOr(a.err, kErrNonFinite);
     }
-    const float L = block_sum(part, red);
+    const float L = block_sum<T>(part, red);
     if (tid == 0) a.loss[r] = a.seed ? L : L - R.com0_x;
 
     // ---- reverse pass, segment by segment ----
@@ -189,14 +195,14 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a)
         const int n0 = cseg * a.K, n1 = min(n0 + a.K, a.nsteps);
         const float4 *c = ck + (size_t)cseg * a.n_cap * 2;
         __syncthreads();
-        for (int i = tid; i < n; i += kAdjThreads) { xs[i] = c[2 * i]; vs[i] = c[2 * i + 1]; }
+        for (int i = tid; i < n; i += T) { xs[i] = c[2 * i]; vs[i] = c[2 * i + 1]; }
         __syncthreads();
         for (int step = n0; step < n1; ++step) {            // recompute the segment
             float4 *sgn = sg + (size_t)(step - n0) * a.n_cap * 3;
             const float2 sc = a.sc[step];
-            for (int i = tid; i < n; i += kAdjThreads) aa[i] = robot_force(rc, R.slice_base, rec_base, i, xs, vs, sc.x, sc.y);
+            for (int i = tid; i < n; i += T) aa[i] = robot_force(rc, R.slice_base, rec_base, i, xs, vs, sc.x, sc.y);
             __syncthreads();
-            for (int i = tid; i < n; i += kAdjThreads) {
+            for (int i = tid; i < n; i += T) {
                 float4 x = xs[i], v = vs[i], vt;
                 sgn[3 * i] = x; sgn[3 * i + 1] = v;
                 robot_integrate(e, x, v, aa[i], &vt);
@@ -208,10 +214,10 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a)
         for (int step = n1 - 1; step >= n0; --step) {       // and walk it backwards
             const float4 *sgn = sg + (size_t)(step - n0) * a.n_cap * 3;
             const float2 sc = a.sc[step];
-            for (int i = tid; i < n; i += kAdjThreads) { xs[i] = sgn[3 * i]; vs[i] = sgn[3 * i + 1]; vts[i] = sgn[3 * i + 2]; }
+            for (int i = tid; i < n; i += T) { xs[i] = sgn[3 * i]; vs[i] = sgn[3 * i + 1]; vts[i] = sgn[3 * i + 2]; }
             __syncthreads();
             // phase A: through the update, the clamp and the contact force
-            for (int i = tid; i < n; i += kAdjThreads) {
+            for (int i = tid; i < n; i += T) {
                 const float4 x = xs[i], vt = vts[i], lxi = lx[i], lvi = lv[i];
                 const float w = x.w;
                 if (w < 0.f) { aa[i] = make_float4(0.f, 0.f, 0.f, 0.f); lv[i] = aa[i]; continue; }
@@ -239,7 +245,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a)
             }
             __syncthreads();
             // phase B: through the spring forces (each mass gathers its springs)
-            for (int i = tid; i < n; i += kAdjThreads) {
+            for (int i = tid; i < n; i += T) {
                 const float4 xi = xs[i], vi = vs[i], ai = aa[i];
                 float3 gx = make_float3(0.f, 0.f, 0.f), gv = make_float3(0.f, 0.f, 0.f);
                 const unsigned lane = (unsigned)i & 31u;
@@ -274,7 +280,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a)
             }
             __syncthreads();
             // phase C: parameter gradients, voxel by voxel over its 28 springs
-            for (int v = tid; v < nv; v += kAdjThreads) {
+            for (int v = tid; v < nv; v += T) {
                 const int gvx = R.vox_base + v;
                 const uint32_t *vsl = a.vox_slots + (size_t)gvx * 28;
                 if (vsl[0] == 0xffffffffu) continue;               // empty voxel
@@ -298,10 +304,30 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(const AdjArgs a)
             __syncthreads();
         }
     }
-    for (int v = tid; v < nv; v += kAdjThreads) {
+    for (int v = tid; v < nv; v += T) {
         a.g_phase[R.vox_base + v] = gph[v];
         a.g_logk[R.vox_base + v] = glk[v];
     }
+}
+
+// Threads per robot for a population: the choice T whose estimated time,
+// waves(T) * ceil(n_cap / T), is smallest (the larger T on a tie), where a
+// wave is one CTA per robot on every multiprocessor, as many at once as the
+// registers (64 per thread), the 2048 threads and the shared memory of a
+// multiprocessor allow.
+int choose_threads(int n_robots, int n_cap, size_t smem, int n_sms, int smem_per_sm)
+{
+    int best = kAdjThreadChoices[0];
+    long long best_cost = -1;
+    for (int T : kAdjThreadChoices) {
+        int per_sm = std::min(65536 / (64 * T), 2048 / T);
+        if (smem_per_sm > 0) per_sm = std::min<int>(per_sm, (int)((size_t)smem_per_sm / (smem + 1024)));
+        per_sm = std::max(per_sm, 1);
+        const long long slots = (long long)per_sm * std::max(n_sms, 1);
+        const long long cost = ((n_robots + slots - 1) / slots) * (long long)((n_cap + T - 1) / T);
+        if (best_cost < 0 || cost < best_cost) { best = T; best_cost = cost; }
+    }
+    return best;
 }
 
 }  // namespace
@@ -317,6 +343,7 @@ struct msa_adjoint {
     bool custom_alloc = false;
     std::vector<std::pair<void *, size_t>> allocs;
     int n_robots = 0, K = 100, max_steps = 0, n_ckpt = 0, n_cap = 0, max_vox = 0;
+    int threads = 0;                   // threads per robot (one of kAdjThreadChoices)
     int64_t n_masses = 0, n_voxels = 0, n_slots = 0;
     RobotDev *robots = nullptr;
     int2 *slot_range = nullptr;
@@ -443,7 +470,16 @@ ms_status msa_create(const ms_params *p, const msb_voxel_spec *spec, int32_t n_r
     MSA_CUDA_TRY(cudaMemsetAsync(b->scratch, 0, sizeof(float2) * vb.nbr.size(), b->stream));
     b->smem = (size_t)b->n_cap * 6 * sizeof(float4) + (size_t)b->max_vox * 2 * sizeof(float);
     if (b->smem > 200 * 1024) return fail(MS_ERR_ARG, "a robot's adjoint state does not fit in shared memory");
-    MSA_CUDA_TRY(cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    MSA_CUDA_TRY(cudaFuncSetAttribute(k_adjoint<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    MSA_CUDA_TRY(cudaFuncSetAttribute(k_adjoint<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    MSA_CUDA_TRY(cudaFuncSetAttribute(k_adjoint<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    {
+        int dev = 0, n_sms = 1, smem_sm = 0;
+        MSA_CUDA_TRY(cudaGetDevice(&dev));
+        MSA_CUDA_TRY(cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev));
+        MSA_CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        b->threads = choose_threads(b->n_robots, b->n_cap, b->smem, n_sms, smem_sm);
+    }
     MSA_CUDA_TRY(cudaStreamSynchronize(b->stream));
     guard.b = nullptr;
     *out = b;
@@ -488,7 +524,11 @@ ms_status msa_gradients(msa_adjoint *b, int32_t nsteps, const float *phase, cons
     a.env = make_env(b->p);
     a.nsteps = nsteps; a.K = b->K; a.n_ckpt = b->n_ckpt; a.n_cap = b->n_cap;
     a.loss = b->loss; a.g_phase = b->g_phase; a.g_logk = b->g_logk; a.err = b->err;
-    k_adjoint<<<b->n_robots, kAdjThreads, b->smem, b->stream>>>(a);
+    switch (b->threads) {
+    case 1024: k_adjoint<1024><<<b->n_robots, 1024, b->smem, b->stream>>>(a); break;
+    case 512: k_adjoint<512><<<b->n_robots, 512, b->smem, b->stream>>>(a); break;
+    default: k_adjoint<256><<<b->n_robots, 256, b->smem, b->stream>>>(a); break;
+    }
     MSA_CUDA_TRY(cudaGetLastError());
     MSA_CUDA_TRY(cudaMemcpyAsync(loss, b->loss, sizeof(float) * b->n_robots, outk, b->stream));
     MSA_CUDA_TRY(cudaMemcpyAsync(g_phase, b->g_phase, sizeof(float) * b->n_voxels, outk, b->stream));
@@ -501,6 +541,17 @@ ms_status msa_gradients(msa_adjoint *b, int32_t nsteps, const float *phase, cons
     }
     return MS_OK;
 }
+
+ms_status msa_set_threads(msa_adjoint *b, int32_t threads)
+{
+    if (!b) return fail(MS_ERR_ARG, "adjoint is NULL");
+    if (threads != 1024 && threads != 512 && threads != 256)
+        return fail(MS_ERR_ARG, "threads per robot must be 256, 512 or 1024");
+    b->threads = threads;
+    return MS_OK;
+}
+
+int32_t msa_threads(const msa_adjoint *b) { return b ? b->threads : 0; }
 
 ms_status msa_sizes(const msa_adjoint *b, int64_t *n_voxels, int64_t *n_masses)
 {

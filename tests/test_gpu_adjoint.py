@@ -65,9 +65,12 @@ def base_logk(mat):
     return np.where(mat > 0, np.log(np.maximum(k[mat], 1.0)), 0.0).astype(np.float32)
 
 
-def test_smooth_loss_gradient_matches_fd(ms, ora):
+@pytest.mark.parametrize("threads", [0, 256, 512])
+def test_smooth_loss_gradient_matches_fd(ms, ora, threads):
     """No contact, no gravity, loss = sum_i w_i . x_i(T): a smooth function of
-    every parameter; every component must match the FD within 1e-3."""
+    every parameter; every component must match the FD within 1e-3.  With
+    each size of the adjoint kernel's CTA (one robot: 1024 threads by the
+    library's choice, 256 and 512 set explicitly)."""
     rng = np.random.default_rng(31)
     mat = rng.integers(1, 4, size=(2, 2, 2)).astype(np.uint8)
     phase = rng.uniform(0, 2 * np.pi, size=mat.shape).astype(np.float32)
@@ -77,8 +80,9 @@ def test_smooth_loss_gradient_matches_fd(ms, ora):
     seed = rng.standard_normal((n, 3)).astype(np.float32)
     nsteps = 400
     with ms.Adjoint([mat], synth.VOXEL_MATERIALS, synth.VOXEL_FREQ, synth.VOXEL_EDGE, synth.VOXEL_MASS,
-                    params, checkpoint_every=100, max_steps=nsteps) as adj:
+                    params, checkpoint_every=100, max_steps=nsteps, threads=threads) as adj:
         assert adj.n_masses == n
+        assert adj.threads == (threads or 1024)
         loss, gp, gk = adj.gradients(nsteps, phase, logk, seed_x=seed)
     lo = oracle_loss(ora, mat, phase.astype(np.float64), logk.astype(np.float64), params, nsteps, seed)
     assert abs(loss[0] - lo) <= 1e-5 * max(1.0, abs(lo))
@@ -242,9 +246,9 @@ def _fd_components(ora, mat, phase, logk, params, nsteps, comps, eps=1e-6, seed=
 
 
 def test_adjoint_on_a_robot_larger_than_the_block(ms, ora):
-    """A 6x6x6 robot (343 masses, more than the 256 threads of the CTA, so
-    each thread carries several masses and voxels): smooth loss (no contact,
-    no gravity) over 300 steps, FD on a sample of components within 1e-3."""
+    """A 6x6x6 robot (343 masses) on a CTA of 256 threads, so each thread
+    carries several masses and voxels: smooth loss (no contact, no gravity)
+    over 300 steps, FD on a sample of components within 1e-3."""
     rng = np.random.default_rng(41)
     mat = rng.integers(1, 4, size=(6, 6, 6)).astype(np.uint8)
     phase = rng.uniform(0, 2 * np.pi, size=mat.shape).astype(np.float32)
@@ -253,8 +257,8 @@ def test_adjoint_on_a_robot_larger_than_the_block(ms, ora):
     nsteps = 300
     seed = rng.standard_normal((343, 3)).astype(np.float32)
     with ms.Adjoint([mat], synth.VOXEL_MATERIALS, synth.VOXEL_FREQ, synth.VOXEL_EDGE, synth.VOXEL_MASS,
-                    params, checkpoint_every=64, max_steps=nsteps) as adj:
-        assert adj.n_masses == 343
+                    params, checkpoint_every=64, max_steps=nsteps, threads=256) as adj:
+        assert adj.n_masses == 343 and adj.threads == 256
         loss, gp, gk = adj.gradients(nsteps, phase, logk, seed_x=seed)
     occ = np.flatnonzero(mat.ravel() > 0)
     pick = rng.choice(occ, size=8, replace=False)
@@ -288,3 +292,22 @@ def test_adjoint_with_contact_on_a_larger_robot_200_steps(ms, ora):
     assert consistent.sum() >= len(comps) // 2
     bad = consistent & (np.abs(g - f6) > 1e-3 * den)
     assert not bad.any(), list(zip(comps, g, f6, consistent))
+
+
+def test_threads_per_robot_follow_the_population(ms):
+    """The kernel's CTA size is chosen from the population: one thread per mass
+    for a few walkers (1024 for 8^3 voxels, 729 masses), and small CTAs when
+    many small robots must share the multiprocessors.  Other sizes are
+    refused."""
+    params = synth.voxel_params()
+    args = (synth.VOXEL_MATERIALS, synth.VOXEL_FREQ, synth.VOXEL_EDGE, synth.VOXEL_MASS, params)
+    walkers = [m for m, _ in synth.walker_designs(16, seed=3)]
+    with ms.Adjoint(walkers, *args, max_steps=10) as adj:
+        assert adj.threads == 1024
+    rng = np.random.default_rng(9)
+    small = [rng.integers(1, 4, size=(2, 2, 2)).astype(np.uint8) for _ in range(3000)]
+    with ms.Adjoint(small, *args, max_steps=10) as adj:
+        assert adj.threads == 256
+    with pytest.raises(ms.MsError):
+        ms.Adjoint(walkers[:1], *args, max_steps=10, threads=384)
+
