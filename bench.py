@@ -468,7 +468,7 @@ def measure_population(args, reps, local, sim_steps, timed_launches, warm_launch
                                   f"{sim_steps} simulated steps (dt = 1e-4) per persistent launch",
                       "n_masses": inf["n_masses"], "n_springs_merged": inf["n_records"],
                       "block_robots": inf["n_block_items"], "warp_robots": inf["n_warp_items"],
-                      "setup_s": round(t_create, 1)},
+                      "threads_per_cta": inf["threads"], "setup_s": round(t_create, 1)},
            "elements_per_s": (inf["n_masses"] + inf["n_records"]) * steps_per_s * reps.world,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                         "traffic": None, "kernel": "k_batch", "peak_kind": f"{hbm_kind} (hbm_gbs)",

@@ -337,6 +337,7 @@ typedef struct {
     int32_t n_warp_items;    /* robots run warp-per-robot */
     int64_t device_bytes;
     int64_t step_count;
+    int32_t threads;         /* CTA size of the persistent kernel: 512 or 1024 */
 } msb_info_t;
 
 /*
@@ -358,14 +359,23 @@ ms_status msb_create(const ms_params *p, const msb_voxel_spec *spec, int32_t n_r
                      const float *logk, const ms_allocator *alloc, void *stream, msb_batch **out);
 
 /*
- * msb_autotune -- time block-per-robot against warp-per-robot on a sample of
+ * msb_autotune -- for each CTA size of the persistent kernel (512 and 1024
+ * threads), time block-per-robot against warp-per-robot on a sample of
  * robots of every size bucket (sample_steps steps each) and keep the faster
- * schedule per bucket.  Without it, robots of up to 64 masses run
- * warp-per-robot and the rest block-per-robot.  Synchronises the stream.
- * policy: 0 = autotune, 1 = force block-per-robot, 2 = force warp-per-robot
- * wherever a robot fits a warp's share of shared memory.
+ * schedule per bucket; then time the whole population for sample_steps with
+ * those schedules and keep the faster CTA size.  The robots' state is
+ * restored afterwards.  Without it, the CTA has 512 threads, robots of up to
+ * 64 masses run warp-per-robot and the rest block-per-robot.  Synchronises
+ * the stream.  policy: 0 = autotune, 1 = force block-per-robot, 2 = force
+ * warp-per-robot wherever a robot fits a warp's share of shared memory
+ * (policies 1 and 2 keep the current CTA size).
  */
 ms_status msb_autotune(msb_batch *b, int32_t sample_steps, int32_t policy);
+
+/* msb_set_threads -- CTA size of the persistent kernel, 512 or 1024 (else
+ * MS_ERR_ARG); a warp item then holds threads / 32 robots, and a robot whose
+ * warp share no longer fits shared memory runs block-per-robot. */
+ms_status msb_set_threads(msb_batch *b, int32_t threads);
 
 /*
  * msb_run -- advance every robot nsteps steps in one persistent launch

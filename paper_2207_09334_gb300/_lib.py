@@ -42,7 +42,8 @@ class MsbVoxelSpec(C.Structure):
 class MsbInfo(C.Structure):
     _fields_ = [("n_robots", C.c_int32), ("n_masses", C.c_int64), ("n_records", C.c_int64),
                 ("max_robot_masses", C.c_int32), ("n_block_items", C.c_int32),
-                ("n_warp_items", C.c_int32), ("device_bytes", C.c_int64), ("step_count", C.c_int64)]
+                ("n_warp_items", C.c_int32), ("device_bytes", C.c_int64), ("step_count", C.c_int64),
+                ("threads", C.c_int32)]
 
 
 STATUS = {0: "MS_OK", 1: "MS_ERR_ARG", 2: "MS_ERR_OOM", 3: "MS_ERR_CUDA", 4: "MS_ERR_UNSTABLE",
@@ -80,6 +81,7 @@ SIGNATURES = {
     "msb_create": (C.c_int, [C.POINTER(MsParams), C.POINTER(MsbVoxelSpec), I32, VP, VP, VP, VP,
                              C.POINTER(MsAllocator), VP, C.POINTER(VP)]),
     "msb_autotune": (C.c_int, [VP, I32, I32]),
+    "msb_set_threads": (C.c_int, [VP, I32]),
     "msb_run": (C.c_int, [VP, I32]),
     "msb_run_loop": (C.c_int, [VP, I32]),
     "msb_com_travel": (C.c_int, [VP, VP, I32]),

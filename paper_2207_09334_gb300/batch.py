@@ -50,6 +50,10 @@ class Population:
     def autotune(self, sample_steps: int = 100, policy: int = 0):
         check(self._lib.msb_autotune(self.h, int(sample_steps), int(policy)))
 
+    def set_threads(self, threads: int):
+        """CTA size of the persistent kernel: 512 or 1024 threads."""
+        check(self._lib.msb_set_threads(self.h, int(threads)))
+
     def run(self, nsteps: int):
         check(self._lib.msb_run(self.h, int(nsteps)))
 

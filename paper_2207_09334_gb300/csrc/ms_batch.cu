@@ -32,8 +32,11 @@
 namespace ms {
 namespace {
 
-constexpr int kBatchThreads = 512;
-constexpr int kWarpsPerCta = kBatchThreads / 32;
+// CTA size of the persistent kernel: 512 or 1024 threads (msb_autotune times
+// both on the population and keeps the faster; msb_set_threads sets one).  A
+// block item has the whole CTA; a warp item holds one robot per warp.
+constexpr int kBatchThreadsDefault = 512;
+constexpr int kComThreads = 256;    // k_com_travel
 constexpr int kWarpModeMax = 256;   // robots up to this many masses may run warp-per-robot
 
 struct BatchArgs {
@@ -53,11 +56,12 @@ struct BatchArgs {
     int *err;
 };
 
-__global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchArgs a)
+template <int T>
+__global__ void __launch_bounds__(T) k_batch(const BatchArgs a)
 {
     extern __shared__ float4 smem[];
     __shared__ int item_sh;
-    __shared__ float red_sh[2][kWarpsPerCta];
+    __shared__ float red_sh[2][T / 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     for (;;) {
@@ -74,14 +78,14 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchArgs a)
             const int n = R.n;
             float4 *xs = smem, *vs = smem + n, *fs = smem + 2 * n;
             const float4 *g = a.st + 2 * R.mass_base;
-            for (int i = tid; i < n; i += kBatchThreads) { xs[i] = g[2 * i]; vs[i] = g[2 * i + 1]; }
+            for (int i = tid; i < n; i += T) { xs[i] = g[2 * i]; vs[i] = g[2 * i + 1]; }
             __syncthreads();
             for (int step = 0; step < a.nsteps; ++step) {
                 const float2 sc = __ldg(&a.sc[step]);
-                for (int i = tid; i < n; i += kBatchThreads)
+                for (int i = tid; i < n; i += T)
                     fs[i] = robot_force_all<4>(a.rows, R.slice_base, i, xs, vs, sc.x, sc.y);
                 __syncthreads();
-                for (int i = tid; i < n; i += kBatchThreads) {
+                for (int i = tid; i < n; i += T) {
                     float4 x = xs[i], v = vs[i];
                     robot_integrate(a.env, x, v, fs[i]);
                     xs[i] = x; vs[i] = v;
@@ -90,7 +94,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchArgs a)
             }
             float mx = 0.f, m = 0.f;
             bool bad = false;
-            for (int i = tid; i < n; i += kBatchThreads) {
+            for (int i = tid; i < n; i += T) {
                 const float4 x = xs[i], v = vs[i];
                 float4 *gw = a.st + 2 * R.mass_base;
                 gw[2 * i] = x; gw[2 * i + 1] = v;
@@ -103,7 +107,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchArgs a)
             __syncthreads();
             if (tid == 0) {
                 float smx = 0.f, sm = 0.f;
-                for (int w = 0; w < kWarpsPerCta; ++w) { smx += red_sh[0][w]; sm += red_sh[1][w]; }
+                for (int w = 0; w < T / 32; ++w) { smx += red_sh[0][w]; sm += red_sh[1][w]; }
                 a.travel[item.x] = smx / sm - R.com0_x;
             }
             __syncthreads();
@@ -173,7 +177,7 @@ __global__ void k_sc_table_from(long long n0, int nsteps, double dt, double two_
 // Centre-of-mass x travel of every robot from the global state (one CTA per robot).
 __global__ void k_com_travel(const RobotDev *robots, const float4 *st, float *travel)
 {
-    __shared__ float red[2][kWarpsPerCta];
+    __shared__ float red[2][kComThreads / 32];
     const RobotDev R = robots[blockIdx.x];
     float mx = 0.f, m = 0.f;
     for (int i = threadIdx.x; i < R.n; i += blockDim.x) {
@@ -244,6 +248,7 @@ struct msb_batch {
     int wlist_cap = 0;
     std::vector<int> h_wlist;
     std::vector<uint8_t> warp_mode;           // per robot: 1 = warp-per-robot
+    int threads = kBatchThreadsDefault;       // CTA size of the persistent kernel (512 or 1024)
     int warp_cap = 32;
     size_t smem_bytes = 0;
     int grid = 0;
@@ -321,7 +326,7 @@ int dir_index(int dx, int dy, int dz)
 }
 
 // Build the schedule items from per-robot modes: block items one per robot,
-// warp items groups of up to kWarpsPerCta (16) robots of similar size; ordered by
+// warp items groups of up to threads / 32 robots of similar size; ordered by
 // decreasing cost so the persistent CTAs balance (longest item first).
 void set_items(msb_batch *b, const std::vector<int> &block_robots, std::vector<int> warp_robots)
 {
@@ -331,8 +336,9 @@ void set_items(msb_batch *b, const std::vector<int> &block_robots, std::vector<i
     for (int r : block_robots) b->h_items.push_back(make_int4(r, 1, 0, b->h_robots[r].n));
     std::stable_sort(warp_robots.begin(), warp_robots.end(),
                      [&](int x, int y) { return b->h_robots[x].n > b->h_robots[y].n; });
-    for (size_t q = 0; q < warp_robots.size(); q += kWarpsPerCta) {
-        const int cnt = (int)std::min<size_t>(kWarpsPerCta, warp_robots.size() - q);
+    const size_t wpc = (size_t)b->threads / 32;
+    for (size_t q = 0; q < warp_robots.size(); q += wpc) {
+        const int cnt = (int)std::min<size_t>(wpc, warp_robots.size() - q);
         int cost = 0;
         for (int u = 0; u < cnt; ++u) {
             const int r = warp_robots[q + u];
@@ -350,7 +356,7 @@ void set_items(msb_batch *b, const std::vector<int> &block_robots, std::vector<i
     });
     size_t blk = 0;
     for (auto &it : b->h_items) if (it.z == 0) blk = std::max(blk, (size_t)b->h_robots[it.x].n);
-    const size_t warp_bytes = b->h_wlist.empty() ? 0 : (size_t)kWarpsPerCta * 3 * b->warp_cap * sizeof(float4);
+    const size_t warp_bytes = b->h_wlist.empty() ? 0 : wpc * 3 * b->warp_cap * sizeof(float4);
     b->smem_bytes = std::max<size_t>(std::max(blk * 3 * sizeof(float4), warp_bytes), 16);
 }
 
@@ -377,11 +383,16 @@ ms_status upload_items(msb_batch *b)
         b->wlist_cap = std::max(nw, 1);
     }
     if (nw) MSB_CUDA_TRY(cudaMemcpyAsync(b->wlist, b->h_wlist.data(), sizeof(int) * nw, cudaMemcpyHostToDevice, b->stream));
-    MSB_CUDA_TRY(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_bytes));
     int dev = 0, sms = 0, per_sm = 0;
     MSB_CUDA_TRY(cudaGetDevice(&dev));
     MSB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    MSB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kBatchThreads, b->smem_bytes));
+    if (b->threads == 1024) {
+        MSB_CUDA_TRY(cudaFuncSetAttribute(k_batch<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_bytes));
+        MSB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<1024>, 1024, b->smem_bytes));
+    } else {
+        MSB_CUDA_TRY(cudaFuncSetAttribute(k_batch<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_bytes));
+        MSB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<512>, 512, b->smem_bytes));
+    }
     if (per_sm < 1) return fail(MS_ERR_ARG, "a robot does not fit in one CTA's shared memory");
     b->grid = std::max(1, std::min(n, sms * per_sm));
     MSB_CUDA_TRY(cudaStreamSynchronize(b->stream));
@@ -418,7 +429,8 @@ ms_status enqueue_run(msb_batch *b, int nsteps, cudaStream_t s)
     const double two_pi_f = 2.0 * M_PI * b->freq;
     k_sc_table<<<(nsteps + 255) / 256, 256, 0, s>>>(b->counter, nsteps, (double)b->p.dt, two_pi_f, b->sc);
     MSB_CUDA_TRY(cudaGetLastError());
-    k_batch<<<b->grid, kBatchThreads, b->smem_bytes, s>>>(batch_args(b, nsteps));
+    if (b->threads == 1024) k_batch<1024><<<b->grid, 1024, b->smem_bytes, s>>>(batch_args(b, nsteps));
+    else k_batch<512><<<b->grid, 512, b->smem_bytes, s>>>(batch_args(b, nsteps));
     MSB_CUDA_TRY(cudaGetLastError());
     k_advance<<<1, 1, 0, s>>>(b->counter, nsteps);
     MSB_CUDA_TRY(cudaGetLastError());
@@ -803,7 +815,7 @@ ms_status msb_run_loop(msb_batch *b, int32_t nsteps)
         k_advance<<<1, 1, 0, b->stream>>>(b->counter, nsteps);
         MSB_CUDA_TRY(cudaGetLastError());
     }
-    k_com_travel<<<b->n_robots, 256, 0, b->stream>>>(b->robots, b->st, b->travel);
+    k_com_travel<<<b->n_robots, kComThreads, 0, b->stream>>>(b->robots, b->st, b->travel);
     MSB_CUDA_TRY(cudaGetLastError());
     b->step_count += nsteps;
     return MS_OK;
@@ -815,12 +827,14 @@ ms_status msb_autotune(msb_batch *b, int32_t sample_steps, int32_t policy)
     if (!b) return fail(MS_ERR_ARG, "batch is NULL");
     if (policy < 0 || policy > 2) return fail(MS_ERR_ARG, "policy must be 0, 1 or 2");
     const size_t smem_limit = 200 * 1024;
-    auto warp_ok = [&](int n) { return n <= kWarpModeMax && (size_t)kWarpsPerCta * 3 * ((n + 31) / 32 * 32) * sizeof(float4) <= smem_limit; };
+    auto warp_ok = [&](int n) {
+        return n <= kWarpModeMax && (size_t)(b->threads / 32) * 3 * ((n + 31) / 32 * 32) * sizeof(float4) <= smem_limit;
+    };
     if (policy == 1) { std::fill(b->warp_mode.begin(), b->warp_mode.end(), 0); }
     else if (policy == 2) { for (int r = 0; r < b->n_robots; ++r) b->warp_mode[r] = warp_ok(b->h_robots[r].n) ? 1 : 0; }
     else {
         if (sample_steps < 1) return fail(MS_ERR_ARG, "sample_steps must be >= 1");
-        // save the state: the timing runs advance the sampled robots
+        // save the state: the timing runs advance the robots
         MSB_CUDA_TRY(cudaMemcpyAsync(b->st2, b->st, sizeof(float4) * 2 * b->n_masses, cudaMemcpyDeviceToDevice, b->stream));
         ms_status st = ensure_sc(b, sample_steps);
         if (st != MS_OK) return st;
@@ -829,44 +843,80 @@ ms_status msb_autotune(msb_batch *b, int32_t sample_steps, int32_t policy)
         cudaEvent_t e0, e1;
         MSB_CUDA_TRY(cudaEventCreate(&e0));
         MSB_CUDA_TRY(cudaEventCreate(&e1));
-        std::vector<uint8_t> choice(5, 0);
-        for (int bk = 1; bk < 5; ++bk) {
-            std::vector<int> members;
-            for (int r = 0; r < b->n_robots; ++r)
-                if (b->h_robots[r].n > edges[bk - 1] && b->h_robots[r].n <= edges[bk] && warp_ok(b->h_robots[r].n)) members.push_back(r);
-            if (members.empty()) continue;
-            if (members.size() > 256) members.resize(256);
-            float t_mode[2] = {0.f, 0.f};
-            for (int mode = 0; mode < 2; ++mode) {
-                // items for the sample only
-                if (mode == 0) set_items(b, members, {});
-                else set_items(b, {}, members);
-                if ((st = upload_items(b)) != MS_OK) return st;
-                for (int rep = 0; rep < 2; ++rep) {           // first run warms up
-                    MSB_CUDA_TRY(cudaEventRecord(e0, b->stream));
-                    if ((st = enqueue_run(b, sample_steps, b->stream)) != MS_OK) return st;
-                    MSB_CUDA_TRY(cudaEventRecord(e1, b->stream));
-                    MSB_CUDA_TRY(cudaEventSynchronize(e1));
-                }
-                MSB_CUDA_TRY(cudaEventElapsedTime(&t_mode[mode], e0, e1));
+        // two runs of sample_steps steps with the current items; the second is timed
+        auto time_items = [&](float &ms_out) -> ms_status {
+            ms_status s2 = upload_items(b);
+            if (s2 != MS_OK) return s2;
+            for (int rep = 0; rep < 2; ++rep) {
+                MSB_CUDA_TRY(cudaEventRecord(e0, b->stream));
+                if ((s2 = enqueue_run(b, sample_steps, b->stream)) != MS_OK) return s2;
+                MSB_CUDA_TRY(cudaEventRecord(e1, b->stream));
+                MSB_CUDA_TRY(cudaEventSynchronize(e1));
             }
-            choice[bk] = t_mode[1] < t_mode[0] ? 1 : 0;
+            MSB_CUDA_TRY(cudaEventElapsedTime(&ms_out, e0, e1));
+            return MS_OK;
+        };
+        // for each CTA size: the faster schedule per size bucket on a sample of
+        // robots, then the whole population with those schedules
+        float best_t = -1.f;
+        int best_threads = b->threads;
+        std::vector<uint8_t> best_mode = b->warp_mode;
+        for (const int T : {512, 1024}) {
+            b->threads = T;
+            std::vector<uint8_t> choice(5, 0);
+            for (int bk = 1; bk < 5; ++bk) {
+                std::vector<int> members;
+                for (int r = 0; r < b->n_robots; ++r)
+                    if (b->h_robots[r].n > edges[bk - 1] && b->h_robots[r].n <= edges[bk] && warp_ok(b->h_robots[r].n))
+                        members.push_back(r);
+                if (members.empty()) continue;
+                if (members.size() > 256) members.resize(256);
+                float t_mode[2] = {0.f, 0.f};
+                for (int mode = 0; mode < 2; ++mode) {
+                    if (mode == 0) set_items(b, members, {});
+                    else set_items(b, {}, members);
+                    if ((st = time_items(t_mode[mode])) != MS_OK) return st;
+                }
+                choice[bk] = t_mode[1] < t_mode[0] ? 1 : 0;
+            }
+            for (int r = 0; r < b->n_robots; ++r) {
+                const int n = b->h_robots[r].n;
+                int bk = 0;
+                for (int q = 1; q < 5; ++q) if (n > edges[q - 1] && n <= edges[q]) bk = q;
+                b->warp_mode[r] = (bk > 0 && warp_ok(n)) ? choice[bk] : 0;
+            }
+            build_items(b);
+            MSB_CUDA_TRY(cudaMemcpyAsync(b->st, b->st2, sizeof(float4) * 2 * b->n_masses, cudaMemcpyDeviceToDevice, b->stream));
+            float t_all = 0.f;
+            if ((st = time_items(t_all)) != MS_OK) return st;
+            if (best_t < 0.f || t_all < best_t) { best_t = t_all; best_threads = T; best_mode = b->warp_mode; }
         }
+        b->threads = best_threads;
+        b->warp_mode = best_mode;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        for (int r = 0; r < b->n_robots; ++r) {
-            const int n = b->h_robots[r].n;
-            int bk = 0;
-            for (int q = 1; q < 5; ++q) if (n > edges[q - 1] && n <= edges[q]) bk = q;
-            b->warp_mode[r] = (bk > 0 && warp_ok(n)) ? choice[bk] : 0;
-        }
         // restore the state, the clock and the travel record
         MSB_CUDA_TRY(cudaMemcpyAsync(b->st, b->st2, sizeof(float4) * 2 * b->n_masses, cudaMemcpyDeviceToDevice, b->stream));
-        k_com_travel<<<b->n_robots, 256, 0, b->stream>>>(b->robots, b->st, b->travel);
+        k_com_travel<<<b->n_robots, kComThreads, 0, b->stream>>>(b->robots, b->st, b->travel);
         MSB_CUDA_TRY(cudaGetLastError());
         const long long sc_now = b->step_count;
         MSB_CUDA_TRY(cudaMemcpyAsync(b->counter, &sc_now, sizeof(long long), cudaMemcpyHostToDevice, b->stream));
         MSB_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    }
+    build_items(b);
+    return upload_items(b);
+}
+
+ms_status msb_set_threads(msb_batch *b, int32_t threads)
+{
+    if (!b) return fail(MS_ERR_ARG, "batch is NULL");
+    if (threads != 512 && threads != 1024) return fail(MS_ERR_ARG, "threads per CTA must be 512 or 1024");
+    b->threads = threads;
+    // robots whose warp share no longer fits shared memory run block-per-robot
+    const size_t smem_limit = 200 * 1024;
+    for (int r = 0; r < b->n_robots; ++r) {
+        const int n = b->h_robots[r].n;
+        if ((size_t)(threads / 32) * 3 * ((n + 31) / 32 * 32) * sizeof(float4) > smem_limit) b->warp_mode[r] = 0;
     }
     build_items(b);
     return upload_items(b);
@@ -927,6 +977,7 @@ ms_status msb_get_info(const msb_batch *b, msb_info_t *out)
     int nb = 0, nw = 0;
     for (int r = 0; r < b->n_robots; ++r) (b->warp_mode[r] ? nw : nb)++;
     out->n_block_items = nb; out->n_warp_items = nw;
+    out->threads = b->threads;
     out->device_bytes = b->device_bytes; out->step_count = b->step_count;
     return MS_OK;
 }

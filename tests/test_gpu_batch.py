@@ -55,14 +55,19 @@ def oracle_robot(ora, design, nsteps):
     return s, x, v, travel
 
 
-@pytest.mark.parametrize("policy", [1, 2])
-def test_population_matches_oracle_200_steps(ms, ora, policy):
+@pytest.mark.parametrize("policy,threads", [(1, 512), (2, 512), (1, 1024), (2, 1024)])
+def test_population_matches_oracle_200_steps(ms, ora, policy, threads):
+    """Both schedules (block- and warp-per-robot) with both CTA sizes.  With
+    1024 threads a warp item holds 32 robots, so the larger robots no longer
+    fit a warp's share of shared memory and run block-per-robot."""
     designs = population(10, seed=21)
     with make_pop(ms, designs) as pop:
+        pop.set_threads(threads)
         pop.autotune(policy=policy)
         inf = pop.info()
+        assert inf["threads"] == threads
         if policy == 2:
-            assert inf["n_warp_items"] == 10
+            assert inf["n_warp_items"] == (10 if threads == 512 else 9)
         pop.run(200)
         xg, _ = pop.get_state()
         in_contact = 0
@@ -81,14 +86,17 @@ def test_population_matches_oracle_200_steps(ms, ora, policy):
         assert in_contact >= 1                     # contact is exercised
 
 
-def test_population_with_config3_sized_robots_matches_oracle(ms, ora):
+@pytest.mark.parametrize("threads", [512, 1024, 0])
+def test_population_with_config3_sized_robots_matches_oracle(ms, ora, threads):
     """Robots of the benchmark population's largest sizes (sides 10 to 12
     voxels): more than 512 masses each, so the block schedule's per-robot loop
     over masses takes several passes, and a solid 12 x 12 x 12 robot reaches
     the 2197-mass maximum.  Mixed with small robots so that both schedules
     run in the same launch.  200 steps with contact and friction against the
     per-voxel oracle: positions within 1e-4 of the body size, centre-of-mass
-    travel within 1 %."""
+    travel within 1 %.  CTAs of 512 or 1024 threads, or (0) the size and
+    schedules msb_autotune chooses, after which the robots must start from
+    their initial state again."""
     rng = np.random.default_rng(31)
     solid = (rng.integers(1, 4, size=(12, 12, 12)).astype(np.uint8), rng.uniform(0, 2 * np.pi, (12, 12, 12)))
     designs = [solid,
@@ -97,9 +105,14 @@ def test_population_with_config3_sized_robots_matches_oracle(ms, ora):
                synth.random_voxel_design(rng, (12, 10, 11))]
     designs += population(6, seed=32, side_range=(2, 4))
     with make_pop(ms, designs) as pop:
+        if threads:
+            pop.set_threads(threads)
+        else:
+            pop.autotune(sample_steps=20)
         inf = pop.info()
         assert inf["max_robot_masses"] == 13 ** 3
         assert inf["n_block_items"] >= 4
+        assert inf["threads"] == (threads or inf["threads"]) and inf["threads"] in (512, 1024)
         pop.run(200)
         xg, _ = pop.get_state()
         big = 0
