@@ -124,6 +124,28 @@ def test_forward_and_gradients_match_oracle(ms):
     assert abs(got[5] - want[5]) <= 1e-2 * abs(want[5]) + 1e-7
 
 
+def test_screening_pass_matches_oracle_on_sampled_rows(ms):
+    """The screening configuration itself: 65 536 designs per forward pass,
+    so both GEMMs take 128 x 256 tiles in the persistent grid (layer 1 with
+    the one-hot tiles built on chip, layer 2 with the head folded into its
+    epilogue).  512 sampled predictions against the FP64 oracle given the
+    kernel's BF16 weights, element by element as in the forward test."""
+    import torch
+    from oracle import mlp
+    B, n_in, h = 65536, 2048, 512
+    rng = np.random.default_rng(17)
+    mats = rng.integers(0, 4, size=(B, n_in // 4)).astype(np.uint8)
+    with ms.Surrogate(n_in, h, max_batch=B, seed=5) as net:
+        p = net.params().astype(np.float64)
+        y = net.predict(torch.tensor(mats, device="cuda"), chunk=B).cpu().numpy()
+        net.sync()
+    W1, b1, W2, b2, w3, b3 = mlp.unpack(p, n_in, h)
+    pq = np.concatenate([bf16_round(W1).ravel(), b1, bf16_round(W2).ravel(), b2, w3, [b3]])
+    rows = rng.choice(B, size=512, replace=False)
+    y_o, _ = mlp.forward(pq, mlp.one_hot(mats[rows]), n_in, h)
+    close_elementwise("y", y[rows], y_o)
+
+
 def test_fp32_accumulators_on_the_mlp_layers(ms):
     """Given bit-identical BF16 operands, the tensor-core accumulators are
     FP32 sums: the layer-1 pre-activation X W1^T (one-hot X, the model's own
