@@ -497,8 +497,7 @@ def measure_screening(args, reps, local, passes=3, warm=2):
     with ms.Surrogate(2048, 512, max_batch=max(B, 1024), seed=0) as net:
         def screen_once():
             for q in range(0, n_cand, B):
-                net.load_materials(cand[q:q + B])
-                net.forward(B, out[q:q + B])
+                net.forward_materials(cand[q:q + B], out[q:q + B])
         for _ in range(warm):
             screen_once()
         torch.cuda.synchronize()
@@ -596,8 +595,7 @@ def run_surrogate(args, world, rank, local):
 
     def screen_once():
         for s in range(0, n_cand, B):
-            net.load_materials(cand[s:s + B])
-            net.forward(B, out[s:s + B])
+            net.forward_materials(cand[s:s + B], out[s:s + B])
     reps = Replicas(world)
     for _ in range(args.warmup):
         screen_once()

@@ -502,6 +502,11 @@ ms_status mlp_set_input(mlp_model *m, const uint16_t *x_bf16, int32_t B);
  * pre-activations and transposed activations that training needs are not stored
  * (mlp_backward runs its own forward pass) */
 ms_status mlp_forward(mlp_model *m, int32_t B, float *y);
+/* inference on device materials [B][n_in/4] (ids 0..3, 16-byte aligned) read in place by
+ * the first GEMM, without the copy mlp_encode makes (the caller keeps them unchanged until
+ * the pass has run on the model's stream); predictions into device y [B] (may be NULL).
+ * The loaded batch (mlp_encode / mlp_set_input) is left as it was. */
+ms_status mlp_forward_materials(mlp_model *m, const uint8_t *materials, int32_t B, float *y);
 /* forward + backward of the loaded batch against device target [B]; gradients kept in the model;
  * device loss [1] (may be NULL) */
 ms_status mlp_backward(mlp_model *m, const float *target, int32_t B, float *loss);

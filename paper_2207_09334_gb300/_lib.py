@@ -104,6 +104,7 @@ SIGNATURES = {
     "mlp_encode": (C.c_int, [VP, VP, I32]),
     "mlp_set_input": (C.c_int, [VP, VP, I32]),
     "mlp_forward": (C.c_int, [VP, I32, VP]),
+    "mlp_forward_materials": (C.c_int, [VP, VP, I32, VP]),
     "mlp_backward": (C.c_int, [VP, VP, I32, VP]),
     "mlp_adam": (C.c_int, [VP, F32, F32, F32, F32]),
     "mlp_sync": (C.c_int, [VP]),

@@ -710,8 +710,10 @@ ms_status ensure_x(mlp_model *m, int B)
     return MS_OK;
 }
 
-// keep: also store what the backward pass needs (Z1, Z2, H1^T, and X)
-ms_status forward(mlp_model *m, int B, bool keep)
+// keep: also store what the backward pass needs (Z1, Z2, H1^T, and X).
+// ext_mats (inference only): the caller's device materials [B][n_in/4], read
+// in place by the first GEMM instead of the model's copy.
+ms_status forward(mlp_model *m, int B, bool keep, const uint8_t *ext_mats = nullptr)
 {
     GemmArgs g{};
     g.err = m->err;
@@ -720,8 +722,8 @@ ms_status forward(mlp_model *m, int B, bool keep)
     g.epi = EPI_BIAS_GELU; g.bias = m->P + m->off_b1; g.Z = keep ? m->Z1 : nullptr; g.H = m->H1;
     g.Ht = keep ? m->H1t : nullptr;
     ms_status s;
-    if (!keep && m->x_pending) {
-        s = gemm_any(nullptr, m->mats, m->W1b, B, m->n_h, m->n_in, g, m->stream);
+    if (!keep && (ext_mats || m->x_pending)) {
+        s = gemm_any(nullptr, ext_mats ? ext_mats : m->mats, m->W1b, B, m->n_h, m->n_in, g, m->stream);
     } else {
         if ((s = ensure_x(m, B)) != MS_OK) return s;
         s = gemm(m->X, m->W1b, B, m->n_h, m->n_in, g, m->stream);
@@ -884,6 +886,18 @@ ms_status mlp_forward(mlp_model *m, int32_t B, float *y)
     ms_status s = check_batch(m, B);
     if (s != MS_OK) return s;
     if ((s = forward(m, B, false)) != MS_OK) return s;
+    if (y) MLP_CUDA_TRY(cudaMemcpyAsync(y, m->y, sizeof(float) * B, cudaMemcpyDeviceToDevice, m->stream));
+    return MS_OK;
+}
+
+ms_status mlp_forward_materials(mlp_model *m, const uint8_t *materials, int32_t B, float *y)
+{
+    ms::Range range_("mlp_forward_materials");
+    if (!m || !materials) return fail(MS_ERR_ARG, "model and materials are required");
+    ms_status s = check_batch(m, B);
+    if (s != MS_OK) return s;
+    if ((uintptr_t)materials & 15) return fail(MS_ERR_ARG, "materials must be 16-byte aligned");
+    if ((s = forward(m, B, false, materials)) != MS_OK) return s;
     if (y) MLP_CUDA_TRY(cudaMemcpyAsync(y, m->y, sizeof(float) * B, cudaMemcpyDeviceToDevice, m->stream));
     return MS_OK;
 }

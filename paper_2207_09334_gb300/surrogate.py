@@ -88,16 +88,26 @@ class Surrogate:
         self.adam(lr)
         return loss
 
+    def forward_materials(self, mats, out=None):
+        """Predictions for one batch of device materials [B, n_in/4] (uint8,
+        contiguous), read in place by the first GEMM (no copy into the model)."""
+        import torch
+        if out is None:
+            out = torch.empty(mats.shape[0], device="cuda")
+        check(self._lib.mlp_forward_materials(self.h, C.c_void_p(mats.data_ptr()), int(mats.shape[0]),
+                                              C.c_void_p(out.data_ptr())))
+        return out
+
     def predict(self, mats, chunk=None):
         """Predictions for materials [N, n_in/4] (N a multiple of 128), in chunks of max_batch."""
         import torch
         N = mats.shape[0]
         chunk = chunk or self.max_batch
         out = torch.empty(N, device="cuda")
+        mats = mats.contiguous()
         for s in range(0, N, chunk):
             e = min(N, s + chunk)
-            self.load_materials(mats[s:e])
-            self.forward(e - s, out[s:e])
+            self.forward_materials(mats[s:e], out[s:e])
         return out
 
     def sync(self):

@@ -54,7 +54,8 @@ def test_gemm_wide_tiles_match_fp64(ms, M, N, K):
 def test_onehot_tiles_equal_the_materialised_input(ms, B):
     """Inference on a batch of materials builds the one-hot A tiles in shared
     memory (128-byte swizzled) instead of reading X: the predictions equal,
-    bit for bit, those from the same one-hot matrix given as bf16 input.
+    bit for bit, those from the same one-hot matrix given as bf16 input, and
+    those of the entry point that reads the caller's materials in place.
     B = 16384 takes the 128 x 256 tiles, B = 1024 the 128 x 128 ones."""
     import torch
     rng = np.random.default_rng(B)
@@ -66,8 +67,9 @@ def test_onehot_tiles_equal_the_materialised_input(ms, B):
     net.forward(B, y1)
     net.load_input(x)
     net.forward(B, y2)
+    y3 = net.forward_materials(mats)
     net.sync()
-    assert torch.equal(y1, y2)
+    assert torch.equal(y1, y2) and torch.equal(y1, y3)
     net.close()
 
 
