@@ -42,7 +42,8 @@ constexpr int kWarpModeMax = 256;   // robots up to this many masses may run war
 struct BatchArgs {
     const RobotDev *robots;
     const int4 *items;     // (x, count, mode, cost): mode 0 = block (x = robot),
-                           // mode 1 = warp (robots wlist[x .. x+count))
+                           // mode 1 = warp (robots wlist[x .. x+count)),
+                           // mode 2 = pair (robots wlist[x], wlist[x + 1]: one per half CTA)
     const int *wlist;
     int n_items;
     int *queue;            // next item (zeroed before each launch)
@@ -52,9 +53,64 @@ struct BatchArgs {
     const float2 *sc;      // (sin, cos)(2 pi f t_n) per step of this run
     int nsteps;
     int warp_cap;          // masses per warp region in warp mode
+    int pair_cap;          // masses per half in a pair item (1024-thread CTAs)
     float *travel;         // per robot
     int *err;
 };
+
+// Barrier of the NT threads that work on one robot: the whole CTA
+// (BAR = 0), or one half of it (named barrier BAR, for a pair item).
+template <int NT, int BAR>
+__device__ __forceinline__ void group_sync()
+{
+    if (BAR == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NT) : "memory");
+}
+
+// All steps of one robot by a group of NT threads (t = 0 .. NT-1 within the
+// group), its state and forces in xs, vs, fs (shared memory); red holds
+// NT / 32 pairs of warp partial sums for the centre-of-mass travel.
+template <int NT, int BAR>
+__device__ __forceinline__ void run_robot(const BatchArgs &a, int r, int t, float4 *xs, float4 *vs, float4 *fs,
+                                          float *red0, float *red1)
+{
+    const RobotDev R = a.robots[r];
+    const int n = R.n;
+    const float4 *g = a.st + 2 * R.mass_base;
+    for (int i = t; i < n; i += NT) { xs[i] = g[2 * i]; vs[i] = g[2 * i + 1]; }
+    group_sync<NT, BAR>();
+    for (int step = 0; step < a.nsteps; ++step) {
+        const float2 sc = __ldg(&a.sc[step]);
+        for (int i = t; i < n; i += NT)
+            fs[i] = robot_force_all<4>(a.rows, R.slice_base, i, xs, vs, sc.x, sc.y);
+        group_sync<NT, BAR>();
+        for (int i = t; i < n; i += NT) {
+            float4 x = xs[i], v = vs[i];
+            robot_integrate(a.env, x, v, fs[i]);
+            xs[i] = x; vs[i] = v;
+        }
+        group_sync<NT, BAR>();
+    }
+    float mx = 0.f, m = 0.f;
+    bool bad = false;
+    for (int i = t; i < n; i += NT) {
+        const float4 x = xs[i], v = vs[i];
+        float4 *gw = a.st + 2 * R.mass_base;
+        gw[2 * i] = x; gw[2 * i + 1] = v;
+        if (x.w > 0.f) { const float mi = 1.0f / x.w; mx += mi * x.x; m += mi; }
+        bad |= !isfinite(x.x + x.y + x.z + v.x + v.y + v.z);
+    }
+    const int w = t >> 5, lane = t & 31;
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, kErrNonFinite);
+    mx = warp_sum(mx); m = warp_sum(m);
+    if (lane == 0) { red0[w] = mx; red1[w] = m; }
+    group_sync<NT, BAR>();
+    if (t == 0) {
+        float smx = 0.f, sm = 0.f;
+        for (int q = 0; q < NT / 32; ++q) { smx += red0[q]; sm += red1[q]; }
+        a.travel[r] = smx / sm - R.com0_x;
+    }
+}
 
 template <int T>
 __global__ void __launch_bounds__(T) k_batch(const BatchArgs a)
@@ -74,41 +130,23 @@ __global__ void __launch_bounds__(T) k_batch(const BatchArgs a)
 
         if (item.z == 0) {
             // ---------------- block-per-robot ----------------
-            const RobotDev R = a.robots[item.x];
-            const int n = R.n;
-            float4 *xs = smem, *vs = smem + n, *fs = smem + 2 * n;
-            const float4 *g = a.st + 2 * R.mass_base;
-            for (int i = tid; i < n; i += T) { xs[i] = g[2 * i]; vs[i] = g[2 * i + 1]; }
+            const int n = a.robots[item.x].n;
+            run_robot<T, 0>(a, item.x, tid, smem, smem + n, smem + 2 * n, red_sh[0], red_sh[1]);
             __syncthreads();
-            for (int step = 0; step < a.nsteps; ++step) {
-                const float2 sc = __ldg(&a.sc[step]);
-                for (int i = tid; i < n; i += T)
-                    fs[i] = robot_force_all<4>(a.rows, R.slice_base, i, xs, vs, sc.x, sc.y);
-                __syncthreads();
-                for (int i = tid; i < n; i += T) {
-                    float4 x = xs[i], v = vs[i];
-                    robot_integrate(a.env, x, v, fs[i]);
-                    xs[i] = x; vs[i] = v;
+        } else if (item.z == 2) {
+            // ---------------- a pair of robots, one per half of the CTA ----------------
+            if constexpr (T == 1024) {
+                const int half = tid >> 9;
+                if (half < item.y) {
+                    const int r = a.wlist[item.x + half];
+                    float4 *xs = smem + (size_t)half * 3 * a.pair_cap;
+                    if (half == 0)
+                        run_robot<512, 1>(a, r, tid & 511, xs, xs + a.pair_cap, xs + 2 * a.pair_cap, red_sh[0],
+                                          red_sh[1]);
+                    else
+                        run_robot<512, 2>(a, r, tid & 511, xs, xs + a.pair_cap, xs + 2 * a.pair_cap,
+                                          red_sh[0] + 16, red_sh[1] + 16);
                 }
-                __syncthreads();
-            }
-            float mx = 0.f, m = 0.f;
-            bool bad = false;
-            for (int i = tid; i < n; i += T) {
-                const float4 x = xs[i], v = vs[i];
-                float4 *gw = a.st + 2 * R.mass_base;
-                gw[2 * i] = x; gw[2 * i + 1] = v;
-                if (x.w > 0.f) { const float mi = 1.0f / x.w; mx += mi * x.x; m += mi; }
-                bad |= !isfinite(x.x + x.y + x.z + v.x + v.y + v.z);
-            }
-            if (__syncthreads_or(bad) && tid == 0) atomicOr(a.err, kErrNonFinite);
-            mx = warp_sum(mx); m = warp_sum(m);
-            if (lane == 0) { red_sh[0][warp] = mx; red_sh[1][warp] = m; }
-            __syncthreads();
-            if (tid == 0) {
-                float smx = 0.f, sm = 0.f;
-                for (int w = 0; w < T / 32; ++w) { smx += red_sh[0][w]; sm += red_sh[1][w]; }
-                a.travel[item.x] = smx / sm - R.com0_x;
             }
             __syncthreads();
         } else {
@@ -250,6 +288,7 @@ struct msb_batch {
     std::vector<uint8_t> warp_mode;           // per robot: 1 = warp-per-robot
     int threads = kBatchThreadsDefault;       // CTA size of the persistent kernel (512 or 1024)
     int warp_cap = 32;
+    int pair_cap = 32;
     size_t smem_bytes = 0;
     int grid = 0;
     int64_t step_count = 0;
@@ -326,14 +365,20 @@ int dir_index(int dx, int dy, int dz)
 }
 
 // Build the schedule items from per-robot modes: block items one per robot,
-// warp items groups of up to threads / 32 robots of similar size; ordered by
-// decreasing cost so the persistent CTAs balance (longest item first).
+// warp items groups of up to threads / 32 robots of similar size, and (with
+// 1024-thread CTAs) pair items: two block robots of at most 512 masses, one
+// per half of the CTA; ordered by decreasing cost so the persistent CTAs
+// balance (longest item first).
 void set_items(msb_batch *b, const std::vector<int> &block_robots, std::vector<int> warp_robots)
 {
     b->h_items.clear();
     b->h_wlist.clear();
     int cap = 32;
-    for (int r : block_robots) b->h_items.push_back(make_int4(r, 1, 0, b->h_robots[r].n));
+    std::vector<int> paired;
+    for (int r : block_robots) {
+        if (b->threads == 1024 && b->h_robots[r].n <= 512) paired.push_back(r);
+        else b->h_items.push_back(make_int4(r, 1, 0, b->h_robots[r].n));
+    }
     std::stable_sort(warp_robots.begin(), warp_robots.end(),
                      [&](int x, int y) { return b->h_robots[x].n > b->h_robots[y].n; });
     const size_t wpc = (size_t)b->threads / 32;
@@ -349,6 +394,21 @@ void set_items(msb_batch *b, const std::vector<int> &block_robots, std::vector<i
         b->h_items.push_back(make_int4((int)q, cnt, 1, cost));
     }
     b->warp_cap = (cap + 31) / 32 * 32;
+    std::stable_sort(paired.begin(), paired.end(), [&](int x, int y) { return b->h_robots[x].n > b->h_robots[y].n; });
+    int pcap = 32;
+    for (size_t q = 0; q < paired.size(); q += 2) {
+        const int cnt = (int)std::min<size_t>(2, paired.size() - q);
+        const int first = (int)b->h_wlist.size();
+        int cost = 0;
+        for (int u = 0; u < cnt; ++u) {
+            const int r = paired[q + u];
+            b->h_wlist.push_back(r);
+            cost = std::max(cost, b->h_robots[r].n);
+            pcap = std::max(pcap, b->h_robots[r].n);
+        }
+        b->h_items.push_back(make_int4(first, cnt, 2, cost));
+    }
+    b->pair_cap = (pcap + 31) / 32 * 32;
     std::stable_sort(b->h_items.begin(), b->h_items.end(), [](const int4 &x, const int4 &y) {
         // a warp robot advances with 1/8 of the CTA's threads
         const long long cx = (long long)x.w * (x.z == 0 ? 1 : 8), cy = (long long)y.w * (y.z == 0 ? 1 : 8);
@@ -356,8 +416,9 @@ void set_items(msb_batch *b, const std::vector<int> &block_robots, std::vector<i
     });
     size_t blk = 0;
     for (auto &it : b->h_items) if (it.z == 0) blk = std::max(blk, (size_t)b->h_robots[it.x].n);
-    const size_t warp_bytes = b->h_wlist.empty() ? 0 : wpc * 3 * b->warp_cap * sizeof(float4);
-    b->smem_bytes = std::max<size_t>(std::max(blk * 3 * sizeof(float4), warp_bytes), 16);
+    const size_t warp_bytes = warp_robots.empty() ? 0 : wpc * 3 * b->warp_cap * sizeof(float4);
+    const size_t pair_bytes = paired.empty() ? 0 : 2 * 3 * (size_t)b->pair_cap * sizeof(float4);
+    b->smem_bytes = std::max<size_t>(std::max(std::max(blk * 3 * sizeof(float4), warp_bytes), pair_bytes), 16);
 }
 
 void build_items(msb_batch *b)
@@ -418,7 +479,7 @@ BatchArgs batch_args(msb_batch *b, int nsteps)
     a.rows = AllRows{b->a_slice, b->a_nbr, b->a_kl, b->a_ab, b->a_c};
     a.env = make_env(b->p);
     a.sc = b->sc; a.nsteps = nsteps;
-    a.warp_cap = b->warp_cap; a.travel = b->travel; a.err = b->err;
+    a.warp_cap = b->warp_cap; a.pair_cap = b->pair_cap; a.travel = b->travel; a.err = b->err;
     return a;
 }
 

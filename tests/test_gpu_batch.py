@@ -59,7 +59,9 @@ def oracle_robot(ora, design, nsteps):
 def test_population_matches_oracle_200_steps(ms, ora, policy, threads):
     """Both schedules (block- and warp-per-robot) with both CTA sizes.  With
     1024 threads a warp item holds 32 robots, so the larger robots no longer
-    fit a warp's share of shared memory and run block-per-robot."""
+    fit a warp's share of shared memory and run block-per-robot, and block
+    robots of at most 512 masses run two to a CTA, one per half (pair items,
+    each half on its own named barrier)."""
     designs = population(10, seed=21)
     with make_pop(ms, designs) as pop:
         pop.set_threads(threads)
