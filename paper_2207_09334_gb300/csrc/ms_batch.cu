@@ -38,6 +38,7 @@ namespace {
 constexpr int kBatchThreadsDefault = 512;
 constexpr int kComThreads = 256;    // k_com_travel
 constexpr int kWarpModeMax = 256;   // robots up to this many masses may run warp-per-robot
+constexpr int kPairMax = 512;       // block robots up to this many masses run two per 1024-thread CTA
 
 struct BatchArgs {
     const RobotDev *robots;
@@ -366,8 +367,8 @@ int dir_index(int dx, int dy, int dz)
 
 // Build the schedule items from per-robot modes: block items one per robot,
 // warp items groups of up to threads / 32 robots of similar size, and (with
-// 1024-thread CTAs) pair items: two block robots of at most 512 masses, one
-// per half of the CTA; ordered by decreasing cost so the persistent CTAs
+// 1024-thread CTAs) pair items: two block robots of at most kPairMax masses,
+// one per half of the CTA; ordered by decreasing cost so the persistent CTAs
 // balance (longest item first).
 void set_items(msb_batch *b, const std::vector<int> &block_robots, std::vector<int> warp_robots)
 {
@@ -376,7 +377,7 @@ void set_items(msb_batch *b, const std::vector<int> &block_robots, std::vector<i
     int cap = 32;
     std::vector<int> paired;
     for (int r : block_robots) {
-        if (b->threads == 1024 && b->h_robots[r].n <= 512) paired.push_back(r);
+        if (b->threads == 1024 && b->h_robots[r].n <= kPairMax) paired.push_back(r);
         else b->h_items.push_back(make_int4(r, 1, 0, b->h_robots[r].n));
     }
     std::stable_sort(warp_robots.begin(), warp_robots.end(),
