@@ -39,12 +39,14 @@ constexpr int kBatchThreadsDefault = 512;
 constexpr int kComThreads = 256;    // k_com_travel
 constexpr int kWarpModeMax = 256;   // robots up to this many masses may run warp-per-robot
 constexpr int kPairMax = 512;       // block robots up to this many masses run two per 1024-thread CTA
+constexpr int kQuadMax = 256;       // ... and up to this many, four per 1024-thread CTA
 
 struct BatchArgs {
     const RobotDev *robots;
     const int4 *items;     // (x, count, mode, cost): mode 0 = block (x = robot),
                            // mode 1 = warp (robots wlist[x .. x+count)),
-                           // mode 2 = pair (robots wlist[x], wlist[x + 1]: one per half CTA)
+                           // mode 2 = pair, 3 = quad (robots wlist[x .. x+count): one per
+                           // half / quarter of a 1024-thread CTA)
     const int *wlist;
     int n_items;
     int *queue;            // next item (zeroed before each launch)
@@ -55,6 +57,7 @@ struct BatchArgs {
     int nsteps;
     int warp_cap;          // masses per warp region in warp mode
     int pair_cap;          // masses per half in a pair item (1024-thread CTAs)
+    int quad_cap;          // masses per quarter in a quad item
     float *travel;         // per robot
     int *err;
 };
@@ -147,6 +150,23 @@ __global__ void __launch_bounds__(T) k_batch(const BatchArgs a)
                     else
                         run_robot<512, 2>(a, r, tid & 511, xs, xs + a.pair_cap, xs + 2 * a.pair_cap,
                                           red_sh[0] + 16, red_sh[1] + 16);
+                }
+            }
+            __syncthreads();
+        } else if (item.z == 3) {
+            // ---------------- four robots, one per quarter of the CTA ----------------
+            if constexpr (T == 1024) {
+                const int qr = tid >> 8;
+                if (qr < item.y) {
+                    const int r = a.wlist[item.x + qr];
+                    float4 *xs = smem + (size_t)qr * 3 * a.quad_cap, *vs = xs + a.quad_cap, *fs = vs + a.quad_cap;
+                    float *r0 = red_sh[0] + 8 * qr, *r1 = red_sh[1] + 8 * qr;
+                    switch (qr) {
+                    case 0: run_robot<256, 1>(a, r, tid & 255, xs, vs, fs, r0, r1); break;
+                    case 1: run_robot<256, 2>(a, r, tid & 255, xs, vs, fs, r0, r1); break;
+                    case 2: run_robot<256, 3>(a, r, tid & 255, xs, vs, fs, r0, r1); break;
+                    default: run_robot<256, 4>(a, r, tid & 255, xs, vs, fs, r0, r1); break;
+                    }
                 }
             }
             __syncthreads();
@@ -290,6 +310,7 @@ struct msb_batch {
     int threads = kBatchThreadsDefault;       // CTA size of the persistent kernel (512 or 1024)
     int warp_cap = 32;
     int pair_cap = 32;
+    int quad_cap = 32;
     size_t smem_bytes = 0;
     int grid = 0;
     int64_t step_count = 0;
@@ -367,18 +388,21 @@ int dir_index(int dx, int dy, int dz)
 
 // Build the schedule items from per-robot modes: block items one per robot,
 // warp items groups of up to threads / 32 robots of similar size, and (with
-// 1024-thread CTAs) pair items: two block robots of at most kPairMax masses,
-// one per half of the CTA; ordered by decreasing cost so the persistent CTAs
+// 1024-thread CTAs) pair and quad items: two block robots of at most kPairMax
+// masses, or four of at most kQuadMax, one per half / quarter of the CTA
+// (one thread per mass); ordered by decreasing cost so the persistent CTAs
 // balance (longest item first).
 void set_items(msb_batch *b, const std::vector<int> &block_robots, std::vector<int> warp_robots)
 {
     b->h_items.clear();
     b->h_wlist.clear();
     int cap = 32;
-    std::vector<int> paired;
+    std::vector<int> paired, quads;
     for (int r : block_robots) {
-        if (b->threads == 1024 && b->h_robots[r].n <= kPairMax) paired.push_back(r);
-        else b->h_items.push_back(make_int4(r, 1, 0, b->h_robots[r].n));
+        const int n = b->h_robots[r].n;
+        if (b->threads == 1024 && n <= kQuadMax) quads.push_back(r);
+        else if (b->threads == 1024 && n <= kPairMax) paired.push_back(r);
+        else b->h_items.push_back(make_int4(r, 1, 0, n));
     }
     std::stable_sort(warp_robots.begin(), warp_robots.end(),
                      [&](int x, int y) { return b->h_robots[x].n > b->h_robots[y].n; });
@@ -395,21 +419,26 @@ void set_items(msb_batch *b, const std::vector<int> &block_robots, std::vector<i
         b->h_items.push_back(make_int4((int)q, cnt, 1, cost));
     }
     b->warp_cap = (cap + 31) / 32 * 32;
-    std::stable_sort(paired.begin(), paired.end(), [&](int x, int y) { return b->h_robots[x].n > b->h_robots[y].n; });
-    int pcap = 32;
-    for (size_t q = 0; q < paired.size(); q += 2) {
-        const int cnt = (int)std::min<size_t>(2, paired.size() - q);
-        const int first = (int)b->h_wlist.size();
-        int cost = 0;
-        for (int u = 0; u < cnt; ++u) {
-            const int r = paired[q + u];
-            b->h_wlist.push_back(r);
-            cost = std::max(cost, b->h_robots[r].n);
-            pcap = std::max(pcap, b->h_robots[r].n);
+    // groups of G robots of similar size, one per 1024 / G threads (mode 2: G = 2, mode 3: G = 4)
+    auto group = [&](std::vector<int> &rs, int G, int mode) {
+        std::stable_sort(rs.begin(), rs.end(), [&](int x, int y) { return b->h_robots[x].n > b->h_robots[y].n; });
+        int gcap = 32;
+        for (size_t q = 0; q < rs.size(); q += G) {
+            const int cnt = (int)std::min<size_t>((size_t)G, rs.size() - q);
+            const int first = (int)b->h_wlist.size();
+            int cost = 0;
+            for (int u = 0; u < cnt; ++u) {
+                const int r = rs[q + u];
+                b->h_wlist.push_back(r);
+                cost = std::max(cost, b->h_robots[r].n);
+                gcap = std::max(gcap, b->h_robots[r].n);
+            }
+            b->h_items.push_back(make_int4(first, cnt, mode, cost));
         }
-        b->h_items.push_back(make_int4(first, cnt, 2, cost));
-    }
-    b->pair_cap = (pcap + 31) / 32 * 32;
+        return (gcap + 31) / 32 * 32;
+    };
+    b->pair_cap = group(paired, 2, 2);
+    b->quad_cap = group(quads, 4, 3);
     std::stable_sort(b->h_items.begin(), b->h_items.end(), [](const int4 &x, const int4 &y) {
         // a warp robot advances with 1/8 of the CTA's threads
         const long long cx = (long long)x.w * (x.z == 0 ? 1 : 8), cy = (long long)y.w * (y.z == 0 ? 1 : 8);
@@ -419,7 +448,9 @@ void set_items(msb_batch *b, const std::vector<int> &block_robots, std::vector<i
     for (auto &it : b->h_items) if (it.z == 0) blk = std::max(blk, (size_t)b->h_robots[it.x].n);
     const size_t warp_bytes = warp_robots.empty() ? 0 : wpc * 3 * b->warp_cap * sizeof(float4);
     const size_t pair_bytes = paired.empty() ? 0 : 2 * 3 * (size_t)b->pair_cap * sizeof(float4);
-    b->smem_bytes = std::max<size_t>(std::max(std::max(blk * 3 * sizeof(float4), warp_bytes), pair_bytes), 16);
+    const size_t quad_bytes = quads.empty() ? 0 : 4 * 3 * (size_t)b->quad_cap * sizeof(float4);
+    b->smem_bytes = std::max<size_t>(
+        std::max(std::max(blk * 3 * sizeof(float4), warp_bytes), std::max(pair_bytes, quad_bytes)), 16);
 }
 
 void build_items(msb_batch *b)
@@ -480,7 +511,8 @@ BatchArgs batch_args(msb_batch *b, int nsteps)
     a.rows = AllRows{b->a_slice, b->a_nbr, b->a_kl, b->a_ab, b->a_c};
     a.env = make_env(b->p);
     a.sc = b->sc; a.nsteps = nsteps;
-    a.warp_cap = b->warp_cap; a.pair_cap = b->pair_cap; a.travel = b->travel; a.err = b->err;
+    a.warp_cap = b->warp_cap; a.pair_cap = b->pair_cap; a.quad_cap = b->quad_cap;
+    a.travel = b->travel; a.err = b->err;
     return a;
 }
 

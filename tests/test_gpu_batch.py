@@ -94,7 +94,9 @@ def test_population_with_config3_sized_robots_matches_oracle(ms, ora, threads):
     voxels): more than 512 masses each, so the block schedule's per-robot loop
     over masses takes several passes, and a solid 12 x 12 x 12 robot reaches
     the 2197-mass maximum.  Mixed with small robots so that both schedules
-    run in the same launch.  200 steps with contact and friction against the
+    run in the same launch, with robots of 343 to 448 masses that 1024-thread
+    CTAs run two at a time (pair items) and small ones four at a time (quad
+    items).  200 steps with contact and friction against the
     per-voxel oracle: positions within 1e-4 of the body size, centre-of-mass
     travel within 1 %.  CTAs of 512 or 1024 threads, or (0) the size and
     schedules msb_autotune chooses, after which the robots must start from
@@ -104,7 +106,11 @@ def test_population_with_config3_sized_robots_matches_oracle(ms, ora, threads):
     designs = [solid,
                synth.random_voxel_design(rng, (10, 11, 12)),
                synth.random_voxel_design(rng, (11, 11, 11)),
-               synth.random_voxel_design(rng, (12, 10, 11))]
+               synth.random_voxel_design(rng, (12, 10, 11)),
+               # 257 to 512 masses: a pair item with 1024-thread CTAs
+               (rng.integers(1, 4, size=(6, 6, 6)).astype(np.uint8), rng.uniform(0, 2 * np.pi, (6, 6, 6))),
+               (rng.integers(1, 4, size=(6, 7, 6)).astype(np.uint8), rng.uniform(0, 2 * np.pi, (6, 7, 6))),
+               (rng.integers(1, 4, size=(7, 6, 6)).astype(np.uint8), rng.uniform(0, 2 * np.pi, (7, 6, 6)))]
     designs += population(6, seed=32, side_range=(2, 4))
     with make_pop(ms, designs) as pop:
         if threads:
@@ -113,7 +119,7 @@ def test_population_with_config3_sized_robots_matches_oracle(ms, ora, threads):
             pop.autotune(sample_steps=20)
         inf = pop.info()
         assert inf["max_robot_masses"] == 13 ** 3
-        assert inf["n_block_items"] >= 4
+        assert inf["n_block_items"] >= 7
         assert inf["threads"] == (threads or inf["threads"]) and inf["threads"] in (512, 1024)
         pop.run(200)
         xg, _ = pop.get_state()
