@@ -13,8 +13,11 @@
 // from the shared-memory state at t_n (Jacobi, like the paper's grid-wide
 // synchronisation in Algorithm 1), then every mass integrates in place.
 //
-// Two schedules share one kernel:
-//   block-per-robot  all 512 threads of a CTA work on one robot (__syncthreads);
+// Schedules share one kernel (CTAs of 512 or 1024 threads):
+//   block-per-robot  all threads of a CTA work on one robot (__syncthreads);
+//   pair / quad      (1024-thread CTAs) two robots of at most 512 masses, or
+//                    four of at most 256, one per half or quarter of the CTA,
+//                    so that each mass has its own thread (named barriers);
 //   warp-per-robot   each warp of a CTA owns a small robot (__syncwarp only).
 // The CTAs are persistent: they pull work items (a robot, or a group of up to
 // sixteen small robots (one per warp)) from a queue ordered by decreasing cost, and the
@@ -63,7 +66,8 @@ struct BatchArgs {
 };
 
 // Barrier of the NT threads that work on one robot: the whole CTA
-// (BAR = 0), or one half of it (named barrier BAR, for a pair item).
+// (BAR = 0), or a half or a quarter of it (named barrier BAR, for a pair or
+// quad item).
 template <int NT, int BAR>
 __device__ __forceinline__ void group_sync()
 {
