@@ -455,8 +455,8 @@ ms_status msa_gradients(msa_adjoint *a, int32_t nsteps, const float *phase, cons
                         const float *seed_x, float *loss, float *g_phase, float *g_logk, int32_t on_device);
 
 /* msa_set_threads / msa_threads -- threads per robot of the adjoint kernel
- * (one CTA per robot): 256, 512 or 1024.  msa_create picks the size whose
- * estimated time, waves x ceil(largest robot's masses / threads), is
+ * (one CTA per robot): 256, 512, 768 or 1024.  msa_create picks the size
+ * whose estimated time, waves x ceil(largest robot's masses / threads), is
  * smallest for the population on this GPU; msa_set_threads overrides it
  * (MS_ERR_ARG for another value).  Results agree up to FP32 rounding of the
  * loss's block sum; msa_threads returns the current size (0 for NULL). */

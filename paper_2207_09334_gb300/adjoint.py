@@ -54,8 +54,8 @@ class Adjoint:
 
     @property
     def threads(self) -> int:
-        """Threads per robot of the adjoint kernel (256, 512 or 1024; chosen
-        from the population unless given to the constructor)."""
+        """Threads per robot of the adjoint kernel (256, 512, 768 or 1024;
+        chosen from the population unless given to the constructor)."""
         return int(self._lib.msa_threads(self.h))
 
     def gradients(self, nsteps: int, phase, logk, seed_x=None):

@@ -38,11 +38,15 @@
 namespace ms {
 namespace {
 
-// Threads per robot (one CTA each): 256, 512 or 1024, every one at 64
-// registers.  More threads per robot hide more of the latency of each step's
-// record loads; fewer let more robots run at once.  msa_create picks the size
-// from the population (choose_threads), msa_set_threads overrides it.
-constexpr int kAdjThreadChoices[3] = {1024, 512, 256};
+// Threads per robot (one CTA each): 1024, 768, 512 or 256.  More threads per
+// robot hide more of the latency of each step's record loads; fewer let more
+// robots run at once.  Each size has its CTAs per multiprocessor fixed by its
+// register budget: 1024 x 64 registers (one), 768 x 40 (two: one thread per
+// mass of an 8^3-voxel walker, and 256 walkers in one wave), 512 x 64 (two),
+// 256 x 64 (four).  msa_create picks the size from the population
+// (choose_threads), msa_set_threads overrides it.
+constexpr int kAdjThreadChoices[4] = {1024, 768, 512, 256};
+__host__ __device__ constexpr int adj_ctas_per_sm(int T) { return T == 1024 ? 1 : T == 768 ? 2 : T == 512 ? 2 : 4; }
 constexpr int kAdjMaxMasses = 1024;
 constexpr int kAdjMaxVoxels = 4096;
 
@@ -135,7 +139,7 @@ __device__ __forceinline__ float spring_adjoint(const float4 xi, const float4 vi
 }
 
 template <int T>
-__global__ void __launch_bounds__(T, 65536 / (64 * T)) k_adjoint(const AdjArgs a)
+__global__ void __launch_bounds__(T, adj_ctas_per_sm(T)) k_adjoint(const AdjArgs a)
 {
     extern __shared__ float4 sm4[];
     __shared__ float red[T / 32];
@@ -313,14 +317,14 @@ __global__ void __launch_bounds__(T, 65536 / (64 * T)) k_adjoint(const AdjArgs a
 // Threads per robot for a population: the choice T whose estimated time,
 // waves(T) * ceil(n_cap / T), is smallest (the larger T on a tie), where a
 // wave is one CTA per robot on every multiprocessor, as many at once as the
-// registers (64 per thread), the 2048 threads and the shared memory of a
+// register budget (adj_ctas_per_sm) and the shared memory of a
 // multiprocessor allow.
 int choose_threads(int n_robots, int n_cap, size_t smem, int n_sms, int smem_per_sm)
 {
     int best = kAdjThreadChoices[0];
     long long best_cost = -1;
     for (int T : kAdjThreadChoices) {
-        int per_sm = std::min(65536 / (64 * T), 2048 / T);
+        int per_sm = adj_ctas_per_sm(T);
         if (smem_per_sm > 0) per_sm = std::min<int>(per_sm, (int)((size_t)smem_per_sm / (smem + 1024)));
         per_sm = std::max(per_sm, 1);
         const long long slots = (long long)per_sm * std::max(n_sms, 1);
@@ -471,6 +475,7 @@ ms_status msa_create(const ms_params *p, const msb_voxel_spec *spec, int32_t n_r
     b->smem = (size_t)b->n_cap * 6 * sizeof(float4) + (size_t)b->max_vox * 2 * sizeof(float);
     if (b->smem > 200 * 1024) return fail(MS_ERR_ARG, "a robot's adjoint state does not fit in shared memory");
     MSA_CUDA_TRY(cudaFuncSetAttribute(k_adjoint<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    MSA_CUDA_TRY(cudaFuncSetAttribute(k_adjoint<768>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
     MSA_CUDA_TRY(cudaFuncSetAttribute(k_adjoint<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
     MSA_CUDA_TRY(cudaFuncSetAttribute(k_adjoint<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
     {
@@ -526,6 +531,7 @@ ms_status msa_gradients(msa_adjoint *b, int32_t nsteps, const float *phase, cons
     a.loss = b->loss; a.g_phase = b->g_phase; a.g_logk = b->g_logk; a.err = b->err;
     switch (b->threads) {
     case 1024: k_adjoint<1024><<<b->n_robots, 1024, b->smem, b->stream>>>(a); break;
+    case 768: k_adjoint<768><<<b->n_robots, 768, b->smem, b->stream>>>(a); break;
     case 512: k_adjoint<512><<<b->n_robots, 512, b->smem, b->stream>>>(a); break;
     default: k_adjoint<256><<<b->n_robots, 256, b->smem, b->stream>>>(a); break;
     }
@@ -545,8 +551,8 @@ ms_status msa_gradients(msa_adjoint *b, int32_t nsteps, const float *phase, cons
 ms_status msa_set_threads(msa_adjoint *b, int32_t threads)
 {
     if (!b) return fail(MS_ERR_ARG, "adjoint is NULL");
-    if (threads != 1024 && threads != 512 && threads != 256)
-        return fail(MS_ERR_ARG, "threads per robot must be 256, 512 or 1024");
+    if (threads != 1024 && threads != 768 && threads != 512 && threads != 256)
+        return fail(MS_ERR_ARG, "threads per robot must be 256, 512, 768 or 1024");
     b->threads = threads;
     return MS_OK;
 }

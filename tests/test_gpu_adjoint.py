@@ -65,12 +65,12 @@ def base_logk(mat):
     return np.where(mat > 0, np.log(np.maximum(k[mat], 1.0)), 0.0).astype(np.float32)
 
 
-@pytest.mark.parametrize("threads", [0, 256, 512])
+@pytest.mark.parametrize("threads", [0, 256, 512, 768])
 def test_smooth_loss_gradient_matches_fd(ms, ora, threads):
     """No contact, no gravity, loss = sum_i w_i . x_i(T): a smooth function of
     every parameter; every component must match the FD within 1e-3.  With
     each size of the adjoint kernel's CTA (one robot: 1024 threads by the
-    library's choice, 256 and 512 set explicitly)."""
+    library's choice, 256, 512 and 768 set explicitly)."""
     rng = np.random.default_rng(31)
     mat = rng.integers(1, 4, size=(2, 2, 2)).astype(np.uint8)
     phase = rng.uniform(0, 2 * np.pi, size=mat.shape).astype(np.float32)
@@ -295,15 +295,19 @@ def test_adjoint_with_contact_on_a_larger_robot_200_steps(ms, ora):
 
 
 def test_threads_per_robot_follow_the_population(ms):
-    """The kernel's CTA size is chosen from the population: one thread per mass
-    for a few walkers (1024 for 8^3 voxels, 729 masses), and small CTAs when
-    many small robots must share the multiprocessors.  Other sizes are
-    refused."""
+    """The kernel's CTA size is chosen from the population: 1024 threads for a
+    few walkers of 8^3 voxels (729 masses), 768 (one thread per mass, two
+    CTAs per multiprocessor, one wave) for the 256 walkers of the benchmark,
+    and small CTAs when many small robots must share the multiprocessors.
+    Other sizes are refused."""
     params = synth.voxel_params()
     args = (synth.VOXEL_MATERIALS, synth.VOXEL_FREQ, synth.VOXEL_EDGE, synth.VOXEL_MASS, params)
     walkers = [m for m, _ in synth.walker_designs(16, seed=3)]
     with ms.Adjoint(walkers, *args, max_steps=10) as adj:
         assert adj.threads == 1024
+    walkers256 = [m for m, _ in synth.walker_designs(256, seed=3)]
+    with ms.Adjoint(walkers256, *args, max_steps=10) as adj:
+        assert adj.threads == 768
     rng = np.random.default_rng(9)
     small = [rng.integers(1, 4, size=(2, 2, 2)).astype(np.uint8) for _ in range(3000)]
     with ms.Adjoint(small, *args, max_steps=10) as adj:
