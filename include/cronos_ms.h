@@ -360,15 +360,16 @@ ms_status msb_create(const ms_params *p, const msb_voxel_spec *spec, int32_t n_r
 
 /*
  * msb_autotune -- for each CTA size of the persistent kernel (512 and 1024
- * threads), time block-per-robot against warp-per-robot on a sample of
- * robots of every size bucket (sample_steps steps each) and keep the faster
- * schedule per bucket; then time the whole population for sample_steps with
- * those schedules and keep the faster CTA size.  The robots' state is
- * restored afterwards.  Without it, the CTA has 512 threads, robots of up to
- * 64 masses run warp-per-robot and the rest block-per-robot.  Synchronises
- * the stream.  policy: 0 = autotune, 1 = force block-per-robot, 2 = force
- * warp-per-robot wherever a robot fits a warp's share of shared memory
- * (policies 1 and 2 keep the current CTA size).
+ * threads): start from the default schedules, flip one robot-size bucket at
+ * a time ((0,32], (32,64], (64,128], (128,256] masses) between
+ * warp-per-robot and block-per-robot, and keep a flip when the whole
+ * population, run for sample_steps steps from the same state, gets faster;
+ * then keep the faster CTA size.  The robots' state is restored afterwards.
+ * Without it, the CTA has 512 threads, robots of up to 64 masses run
+ * warp-per-robot and the rest block-per-robot.  Synchronises the stream.
+ * policy: 0 = autotune, 1 = force block-per-robot, 2 = force warp-per-robot
+ * wherever a robot fits a warp's share of shared memory (policies 1 and 2
+ * keep the current CTA size).
  */
 ms_status msb_autotune(msb_batch *b, int32_t sample_steps, int32_t policy);
 

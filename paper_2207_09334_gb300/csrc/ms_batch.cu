@@ -121,7 +121,7 @@ __device__ __forceinline__ void run_robot(const BatchArgs &a, int r, int t, floa
 }
 
 template <int T>
-__global__ void __launch_bounds__(T) k_batch(const BatchArgs a)
+__global__ void __launch_bounds__(T, 65536 / (64 * T)) k_batch(const BatchArgs a)
 {
     extern __shared__ float4 smem[];
     __shared__ int item_sh;
@@ -954,40 +954,48 @@ ms_status msb_autotune(msb_batch *b, int32_t sample_steps, int32_t policy)
             MSB_CUDA_TRY(cudaEventElapsedTime(&ms_out, e0, e1));
             return MS_OK;
         };
-        // for each CTA size: the faster schedule per size bucket on a sample of
-        // robots, then the whole population with those schedules
+        // For each CTA size: from the default schedules (warp-per-robot up to 64
+        // masses), flip one size bucket at a time between warp- and
+        // block-per-robot, and keep a flip when the whole population, run for
+        // sample_steps from the saved state, gets faster.  Timing the whole
+        // population measures throughput; a sample of one bucket alone would
+        // not fill the GPU.  Then keep the faster CTA size.
+        auto bucket_of = [&](int n) {
+            int bk = 0;
+            for (int q = 1; q < 5; ++q) if (n > edges[q - 1] && n <= edges[q]) bk = q;
+            return bk;
+        };
+        auto time_all = [&](float &t) -> ms_status {
+            build_items(b);
+            MSB_CUDA_TRY(cudaMemcpyAsync(b->st, b->st2, sizeof(float4) * 2 * b->n_masses, cudaMemcpyDeviceToDevice, b->stream));
+            return time_items(t);
+        };
         float best_t = -1.f;
         int best_threads = b->threads;
         std::vector<uint8_t> best_mode = b->warp_mode;
         for (const int T : {512, 1024}) {
             b->threads = T;
-            std::vector<uint8_t> choice(5, 0);
-            for (int bk = 1; bk < 5; ++bk) {
-                std::vector<int> members;
-                for (int r = 0; r < b->n_robots; ++r)
-                    if (b->h_robots[r].n > edges[bk - 1] && b->h_robots[r].n <= edges[bk] && warp_ok(b->h_robots[r].n))
-                        members.push_back(r);
-                if (members.empty()) continue;
-                if (members.size() > 256) members.resize(256);
-                float t_mode[2] = {0.f, 0.f};
-                for (int mode = 0; mode < 2; ++mode) {
-                    if (mode == 0) set_items(b, members, {});
-                    else set_items(b, {}, members);
-                    if ((st = time_items(t_mode[mode])) != MS_OK) return st;
-                }
-                choice[bk] = t_mode[1] < t_mode[0] ? 1 : 0;
-            }
             for (int r = 0; r < b->n_robots; ++r) {
                 const int n = b->h_robots[r].n;
-                int bk = 0;
-                for (int q = 1; q < 5; ++q) if (n > edges[q - 1] && n <= edges[q]) bk = q;
-                b->warp_mode[r] = (bk > 0 && warp_ok(n)) ? choice[bk] : 0;
+                b->warp_mode[r] = (n <= 64 && warp_ok(n)) ? 1 : 0;
             }
-            build_items(b);
-            MSB_CUDA_TRY(cudaMemcpyAsync(b->st, b->st2, sizeof(float4) * 2 * b->n_masses, cudaMemcpyDeviceToDevice, b->stream));
-            float t_all = 0.f;
-            if ((st = time_items(t_all)) != MS_OK) return st;
-            if (best_t < 0.f || t_all < best_t) { best_t = t_all; best_threads = T; best_mode = b->warp_mode; }
+            float t_cur = 0.f;
+            if ((st = time_all(t_cur)) != MS_OK) return st;
+            for (int bk = 1; bk < 5; ++bk) {
+                std::vector<uint8_t> trial = b->warp_mode;
+                bool any = false;
+                for (int r = 0; r < b->n_robots; ++r) {
+                    const int n = b->h_robots[r].n;
+                    if (bucket_of(n) == bk && warp_ok(n)) { trial[r] ^= 1; any = true; }
+                }
+                if (!any) continue;
+                std::swap(b->warp_mode, trial);
+                float t = 0.f;
+                if ((st = time_all(t)) != MS_OK) return st;
+                if (t < t_cur) t_cur = t;
+                else std::swap(b->warp_mode, trial);      // keep the previous schedules
+            }
+            if (best_t < 0.f || t_cur < best_t) { best_t = t_cur; best_threads = T; best_mode = b->warp_mode; }
         }
         b->threads = best_threads;
         b->warp_mode = best_mode;
