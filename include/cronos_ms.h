@@ -88,9 +88,10 @@ typedef struct {
                                26-neighbourhood and at most one per pair, one rest length per
                                lattice direction, one dashpot value; topology and rest lengths
                                then come from the grid and only k is stored per spring (the
-                               paper's cubic and voxel lattices, "Generating a Lattice").
-                               MS_ERR_ARG (with the reason) for any other network; no actuation
-                               (ms_set_actuation returns MS_ERR_ARG) */
+                               paper's cubic and voxel lattices, "Generating a Lattice"), plus
+                               each spring's actuation coefficients once ms_set_actuation is
+                               called (8 bytes per spring more).
+                               MS_ERR_ARG (with the reason) for any other network */
 } ms_params;
 
 /* Optional device allocator (e.g. a framework's caching allocator).

@@ -72,7 +72,8 @@ struct ms_sim {
     std::vector<int32_t> iperm;     // caller -> internal
 
     // host copies needed to rebuild actuation coefficients
-    std::vector<uint32_t> spring_rec;   // caller spring -> merged record
+    std::vector<uint32_t> spring_rec;   // caller spring -> merged record (lattice: the cell it leaves forward)
+    std::vector<uint8_t> spring_dir;    // lattice: caller spring -> forward direction
     std::vector<uint32_t> rec_slot_a, rec_slot_b;   // merged record -> device slot(s)
     std::vector<float> k_caller, L0_caller;
     std::vector<double> rec_KL;         // per merged record: sum k * L0
@@ -118,6 +119,7 @@ struct ms_sim {
     ms::LatticeArgs lat{};              // lattice layout (kernel 4): stiffness arrays, rest lengths, extents
     ms::LatticeMaps lat_maps;           // its tensor maps (TMA descriptors) per state buffer
     int64_t lat_cells = 0;              // padded cells of the lattice layout
+    float2 *lat_ab = nullptr;           // lattice actuation: (alpha, beta) per forward slot, 13 x cells
     float *stage = nullptr;             // (N,3)*2 floats for host copies
     int *err = nullptr;
     float c_uniform = 0.f;
@@ -217,6 +219,8 @@ struct LatticeShape {
     std::vector<float> kf;            // [13][P] stiffness; 0 on a slot that touches a cell without a
                                       // mass, NaN between two masses that have no spring
     bool guard = false;               // some slot between two masses is NaN
+    std::vector<uint32_t> owner;      // per caller spring: the cell it leaves in a forward direction
+    std::vector<uint8_t> dir;         // ... and that direction
     float L[ms::kLatDirs] = {};
     float c = 0.f;
     std::vector<double> sumK;         // per caller mass: sum of the k of its springs
@@ -288,6 +292,8 @@ bool lattice_shape(int32_t N, const float *x0, int64_t S, const int32_t *ij, con
     bool have_L[ms::kLatDirs] = {};
     L.kf.assign((size_t)ms::kLatDirs * (size_t)L.P, std::numeric_limits<float>::quiet_NaN());
     L.sumK.assign(N, 0.0);
+    L.owner.resize(S);
+    L.dir.resize(S);
     for (int64_t e = 0; e < S; ++e) {
         int32_t a = ij[2 * e], b = ij[2 * e + 1];
         int dd[3];
@@ -312,6 +318,8 @@ bool lattice_shape(int32_t N, const float *x0, int64_t S, const int32_t *ij, con
         float &slot = L.kf[(size_t)d * (size_t)L.P + (size_t)L.cidx[a]];
         if (slot == slot) { why = "two springs join the same pair of masses"; return false; }
         slot = k[e];
+        L.owner[e] = (uint32_t)L.cidx[a];
+        L.dir[e] = (uint8_t)d;
         L.sumK[a] += k[e]; L.sumK[b] += k[e];
     }
     // a slot without a spring: k = 0 where it touches a cell without a mass
@@ -394,6 +402,9 @@ ms_status build_lattice(ms_sim *s, const ms_params *p, int32_t N, const float *x
     }
     s->lat.c = L.c;
     s->lat.guard = L.guard ? 1 : 0;
+    s->lat.act = 0;
+    s->spring_rec = std::move(L.owner);
+    s->spring_dir = std::move(L.dir);
     s->lat.X = L.X; s->lat.Y = L.Y; s->lat.Z = L.Z;
     s->lat.nbx = L.nbx; s->lat.nby = L.nby; s->lat.nbz = L.nbz;
     if ((st = upload(s, &s->d_cidx, L.cidx.data(), (size_t)N)) != MS_OK) return st;
@@ -1177,12 +1188,37 @@ ms_status ms_create_materials(const ms_params *p, int32_t N, const float *x0, co
 ms_status ms_set_actuation(ms_sim *s, float freq_hz, const float *amp, const float *phase)
 {
     if (!s) return fail(MS_ERR_ARG, "sim is NULL");
-    if (!amp) { s->actuated = false; s->freq = 0.0; return MS_OK; }
+    if (!amp) { s->actuated = false; s->freq = 0.0; s->lat.act = 0; return MS_OK; }
     if (!phase) return fail(MS_ERR_ARG, "phase is required with amp");
     if (!std::isfinite(freq_hz)) return fail(MS_ERR_ARG, "freq must be finite");
-    if (s->kernel == ms::kKernelLattice)
-        return fail(MS_ERR_ARG, "the lattice kernel stores no actuation coefficients; create the system with the "
-                                "tiled kernel (kernel = 2)");
+    if (s->kernel == ms::kKernelLattice) {
+        // one spring per pair: alpha = A cos(phi), beta = A sin(phi) in the slot of
+        // the cell the spring leaves forward (reading R3 of the actuated rest length)
+        const size_t P = (size_t)s->lat_cells;
+        std::vector<float2> abh((size_t)ms::kLatDirs * P, make_float2(0.f, 0.f));
+        for (int64_t e = 0; e < s->S; ++e) {
+            if (!std::isfinite(amp[e]) || !std::isfinite(phase[e]))
+                return fail(MS_ERR_ARG, "non-finite amp or phase at spring " + std::to_string(e));
+            abh[(size_t)s->spring_dir[e] * P + s->spring_rec[e]] =
+                make_float2((float)((double)amp[e] * std::cos((double)phase[e])),
+                            (float)((double)amp[e] * std::sin((double)phase[e])));
+        }
+        ms_status st;
+        if (!s->lat_ab && (st = upload<float2>(s, &s->lat_ab, nullptr, abh.size())) != MS_OK) return st;
+        MS_CUDA_TRY(cudaMemcpyAsync(s->lat_ab, abh.data(), sizeof(float2) * abh.size(), cudaMemcpyHostToDevice, s->stream));
+        const int64_t XY = (int64_t)s->lat.X * s->lat.Y;
+        for (int d = 0; d < ms::kLatDirs; ++d) {
+            s->lat.abf[d] = s->lat_ab + (size_t)d * P;
+            const int64_t off = ms::lat_dx(d) + (int64_t)s->lat.X * ms::lat_dy(d) + XY * ms::lat_dz(d);
+            s->lat.abb[d] = reinterpret_cast<const float2 *>(reinterpret_cast<uintptr_t>(s->lat.abf[d]) -
+                                                             (uintptr_t)(off * (int64_t)sizeof(float2)));
+        }
+        MS_CUDA_TRY(cudaStreamSynchronize(s->stream));    // the host array must outlive the copy
+        s->lat.act = 1;
+        s->actuated = true;
+        s->freq = freq_hz;
+        return MS_OK;
+    }
     if ((s->persistent && ms::cluster_smem_bytes(s->cl_tm, s->cl_slots, s->cl_c != nullptr, true) > 227 * 1024) ||
         (s->grid_persistent && ms::grid_smem_bytes(s->max_tile_local, s->max_fwd, s->f_c != nullptr, true) > ms::kTileSmemMax))
         return fail(MS_ERR_ARG, "the persistent kernel cannot hold the actuation coefficients of this system in "

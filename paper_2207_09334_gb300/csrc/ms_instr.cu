@@ -144,7 +144,12 @@ __global__ void __launch_bounds__(kBrickCells) k_energy_lattice(const EnergyArgs
             if (!(k == k) || k == 0.f) continue;            // no spring, or one that adds no energy
             const float4 xj = __ldg(&a.sa[i + lat_dx(d) + g.X * (lat_dy(d) + g.Y * lat_dz(d))]);
             const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-            const float e = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - g.L[d];
+            float L = g.L[d];
+            if (g.act) {                                    // the actuated rest length at t_n
+                const float2 ab = __ldg(g.abf[d] + i);
+                L = L * (1.0f + fmaf(ab.x, a.s_n, ab.y * a.c_n));
+            }
+            const float e = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - L;
             pe += k * e * e;
         }
         t.pe = 0.5f * pe;

@@ -155,6 +155,12 @@ struct LatticeArgs {
     int X, Y, Z;                 // padded extents (cells)
     int nbx, nby, nbz;           // bricks per axis
     int guard;                   // 1: some neighbouring masses have no spring between them (k = NaN there)
+    // actuation (act = 1): (alpha, beta) of the spring from cell i in direction d,
+    // abf[d][i], and abb[d][i] = abf[d][i - off(d)] as for k; the rest length is
+    // L[d] (1 + alpha sin(2 pi f t) + beta cos(2 pi f t))
+    const float2 *abf[kLatDirs];
+    const float2 *abb[kLatDirs];
+    int act;
 };
 // Cells without a mass (padding, holes) hold this position and zero velocity,
 // and every spring slot that touches one holds k = 0: the squared distance to

@@ -27,7 +27,9 @@
 //     R2), written as f = s d, s = k + (c (dv . d)/l - k L)/l, with one
 //     hardware reciprocal square root; k comes from the cell's own array for a
 //     forward direction and from the partner's (kb[d][i] = kf[d][i - off(d)])
-//     for a backward one.  A cell without a mass sits at a far sentinel
+//     for a backward one; an actuated lattice (ACT) reads the spring's
+//     (alpha, beta) the same way and uses L (1 + alpha sin + beta cos) of the
+//     step's 2 pi f t (reading R3).  A cell without a mass sits at a far sentinel
 //     position with k = 0 on its springs, so its terms vanish exactly; only a
 //     lattice where some neighbouring masses lack a spring (k = NaN there)
 //     runs the variant that tests each term (GUARD);
@@ -72,11 +74,24 @@ __device__ __forceinline__ float spring_k(const LatticeArgs &g, int i)
     else return __ldg(g.kb[b] + i);
 }
 
-template <int DX, int DY, int DZ>
-__device__ __forceinline__ float spring_L(const LatticeArgs &g)
+// rest length of the spring of cell i in direction (dx, dy, dz): the
+// direction's L, actuated (ACT) by the spring's (alpha, beta) at the step's
+// (sin, cos)(2 pi f t) = (s_n, c_n), read like k
+template <bool ACT, int DX, int DY, int DZ>
+__device__ __forceinline__ float spring_L(const LatticeArgs &g, int i, float s_n, float c_n)
 {
     constexpr int f = fwd_index(DX, DY, DZ);
-    return g.L[f >= 0 ? f : fwd_index(-DX, -DY, -DZ)];
+    constexpr int b = fwd_index(-DX, -DY, -DZ);
+    const float L = g.L[f >= 0 ? f : b];
+    if constexpr (!ACT) {
+        return L;
+    } else if constexpr (f >= 0) {
+        const float2 ab = __ldg(g.abf[f] + i);
+        return L * (1.0f + fmaf(ab.x, s_n, ab.y * c_n));
+    } else {
+        const float2 ab = __ldg(g.abb[b] + i);
+        return L * (1.0f + fmaf(ab.x, s_n, ab.y * c_n));
+    }
 }
 
 // Magnitude s of the spring term f = s d on the mass at (xi, vi) from the
@@ -132,38 +147,38 @@ __device__ __forceinline__ void add_term(const Own &o, const float4 pa, const fl
 // Springs of the pair (a at z, b at z + 1) into the column (DX, DY): partner
 // cells z - 1 .. z + 2 read once each.  The centre column (0, 0) holds a and b
 // themselves: a's spring to z - 1, the a-b spring once, b's spring to z + 2.
-template <bool GUARD, int DX, int DY>
+template <bool GUARD, bool ACT, int DX, int DY>
 __device__ __forceinline__ void column(const LatticeArgs &g, const float4 *spa, const float2 *spb, int sa_, int ia,
                                        int ib, const Own &oa, const Own &ob, const float4 xb, const float3 vb,
-                                       Force &Fa, Force &Fb)
+                                       float s_n, float c_n, Force &Fa, Force &Fb)
 {
     const int c0 = sa_ + halo_off(DX, DY, 0);
     const float c = g.c;
     {   // z - 1: a only
         const float4 p = spa[c0 - halo_off(0, 0, 1)];
         const float2 q = spb[c0 - halo_off(0, 0, 1)];
-        add_term<GUARD>(oa, p, q, spring_k<DX, DY, -1>(g, ia), spring_L<DX, DY, -1>(g), c, Fa);
+        add_term<GUARD>(oa, p, q, spring_k<DX, DY, -1>(g, ia), spring_L<ACT, DX, DY, -1>(g, ia, s_n, c_n), c, Fa);
     }
     if constexpr (DX != 0 || DY != 0) {
         {   // z: a in-plane, b one below
             const float4 p = spa[c0];
             const float2 q = spb[c0];
-            add_term<GUARD>(oa, p, q, spring_k<DX, DY, 0>(g, ia), spring_L<DX, DY, 0>(g), c, Fa);
-            add_term<GUARD>(ob, p, q, spring_k<DX, DY, -1>(g, ib), spring_L<DX, DY, -1>(g), c, Fb);
+            add_term<GUARD>(oa, p, q, spring_k<DX, DY, 0>(g, ia), spring_L<ACT, DX, DY, 0>(g, ia, s_n, c_n), c, Fa);
+            add_term<GUARD>(ob, p, q, spring_k<DX, DY, -1>(g, ib), spring_L<ACT, DX, DY, -1>(g, ib, s_n, c_n), c, Fb);
         }
         {   // z + 1: a one above, b in-plane
             const float4 p = spa[c0 + halo_off(0, 0, 1)];
             const float2 q = spb[c0 + halo_off(0, 0, 1)];
-            add_term<GUARD>(oa, p, q, spring_k<DX, DY, 1>(g, ia), spring_L<DX, DY, 1>(g), c, Fa);
-            add_term<GUARD>(ob, p, q, spring_k<DX, DY, 0>(g, ib), spring_L<DX, DY, 0>(g), c, Fb);
+            add_term<GUARD>(oa, p, q, spring_k<DX, DY, 1>(g, ia), spring_L<ACT, DX, DY, 1>(g, ia, s_n, c_n), c, Fa);
+            add_term<GUARD>(ob, p, q, spring_k<DX, DY, 0>(g, ib), spring_L<ACT, DX, DY, 0>(g, ib, s_n, c_n), c, Fb);
         }
     } else {
         // the a-b spring, once: +s d on a, -s d on b
         float2 dxy;
         float dz;
         const float s = lattice_term<GUARD>(oa, make_float4(xb.x, xb.y, xb.z, vb.x), make_float2(vb.y, vb.z),
-                                            __ldg(g.kf[fwd_index(0, 0, 1)] + ia), g.L[fwd_index(0, 0, 1)], c, dxy,
-                                            dz);
+                                            __ldg(g.kf[fwd_index(0, 0, 1)] + ia),
+                                            spring_L<ACT, 0, 0, 1>(g, ia, s_n, c_n), c, dxy, dz);
         Fa.xy = __ffma2_rn(make_float2(s, s), dxy, Fa.xy);
         Fa.z = fmaf(s, dz, Fa.z);
         Fb.xy = __ffma2_rn(make_float2(-s, -s), dxy, Fb.xy);
@@ -172,27 +187,27 @@ __device__ __forceinline__ void column(const LatticeArgs &g, const float4 *spa, 
     {   // z + 2: b only
         const float4 p = spa[c0 + halo_off(0, 0, 2)];
         const float2 q = spb[c0 + halo_off(0, 0, 2)];
-        add_term<GUARD>(ob, p, q, spring_k<DX, DY, 1>(g, ib), spring_L<DX, DY, 1>(g), c, Fb);
+        add_term<GUARD>(ob, p, q, spring_k<DX, DY, 1>(g, ib), spring_L<ACT, DX, DY, 1>(g, ib, s_n, c_n), c, Fb);
     }
 }
 
 // all springs of the pair (a, b), column by column
-template <bool GUARD>
+template <bool GUARD, bool ACT>
 __device__ __forceinline__ void pair_forces(const LatticeArgs &g, const float4 *spa, const float2 *spb, int s0, int ia,
                                             int ib, const float4 xa, const float3 va, const float4 xb,
-                                            const float3 vb, float3 &Fa3, float3 &Fb3)
+                                            const float3 vb, float s_n, float c_n, float3 &Fa3, float3 &Fb3)
 {
     const Own oa = own_of(xa, va), ob = own_of(xb, vb);
     Force Fa{make_float2(0.f, 0.f), 0.f}, Fb = Fa;
-    column<GUARD, -1, -1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, Fa, Fb);
-    column<GUARD,  0, -1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, Fa, Fb);
-    column<GUARD,  1, -1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, Fa, Fb);
-    column<GUARD, -1,  0>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, Fa, Fb);
-    column<GUARD,  0,  0>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, Fa, Fb);
-    column<GUARD,  1,  0>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, Fa, Fb);
-    column<GUARD, -1,  1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, Fa, Fb);
-    column<GUARD,  0,  1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, Fa, Fb);
-    column<GUARD,  1,  1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, Fa, Fb);
+    column<GUARD, ACT, -1, -1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, s_n, c_n, Fa, Fb);
+    column<GUARD, ACT,  0, -1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, s_n, c_n, Fa, Fb);
+    column<GUARD, ACT,  1, -1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, s_n, c_n, Fa, Fb);
+    column<GUARD, ACT, -1,  0>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, s_n, c_n, Fa, Fb);
+    column<GUARD, ACT,  0,  0>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, s_n, c_n, Fa, Fb);
+    column<GUARD, ACT,  1,  0>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, s_n, c_n, Fa, Fb);
+    column<GUARD, ACT, -1,  1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, s_n, c_n, Fa, Fb);
+    column<GUARD, ACT,  0,  1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, s_n, c_n, Fa, Fb);
+    column<GUARD, ACT,  1,  1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, s_n, c_n, Fa, Fb);
     Fa3 = make_float3(Fa.xy.x, Fa.xy.y, Fa.z);
     Fb3 = make_float3(Fb.xy.x, Fb.xy.y, Fb.z);
 }
@@ -205,7 +220,7 @@ constexpr uint32_t kStageBytes = (kStageCopied + 127) / 128 * 128;   // stage st
 static_assert(kStageA % 128 == 0 && kStageBytes % 128 == 0, "tensor copies need 128-byte aligned destinations");
 constexpr int kLatCtasPerSm = 2;
 
-template <bool HAS_FEXT, bool RK4, bool GUARD>
+template <bool HAS_FEXT, bool RK4, bool GUARD, bool ACT>
 __global__ void __launch_bounds__(kLatThreads, kLatCtasPerSm)
 k_step_lattice(const StepArgs a, const LatticeArgs g, const __grid_constant__ CUtensorMap map_a,
                const __grid_constant__ CUtensorMap map_b, const __grid_constant__ CUtensorMap map_k)
@@ -264,7 +279,7 @@ k_step_lattice(const StepArgs a, const LatticeArgs g, const __grid_constant__ CU
             const float4 xb = make_float4(r.x, r.y, r.z, wb);
             const float3 vb = make_float3(r.w, t.x, t.y);
             float3 Fa, Fb;
-            pair_forces<GUARD>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, Fa, Fb);
+            pair_forces<GUARD, ACT>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, a.s_n, a.c_n, Fa, Fb);
             float4 xn, vn;
             if (wa == wa) {
                 integrate_mass<HAS_FEXT, RK4>(a, ia, xa, make_float4(va.x, va.y, va.z, 0.f), Fa.x, Fa.y, Fa.z, xn, vn);
@@ -362,7 +377,7 @@ cudaError_t launch_step_lattice(const StepArgs &a, const LatticeArgs &g, const L
     if (q == m.n) return cudaErrorInvalidValue;                // a buffer without tensor maps
     const unsigned grid = (unsigned)std::min<long long>(nbricks, (long long)kLatCtasPerSm * std::max(n_sms, 1));
     const size_t smem = 2 * (size_t)kStageBytes;
-#define MS_LAUNCH_L(F, R, G)                                                                               \
+#define MS_LAUNCH_L(F, R, G, A)                                                                            \
     do {                                                                                                   \
         static std::atomic<uint64_t> opted{0};                                                             \
         int dev = 0;                                                                                       \
@@ -370,20 +385,22 @@ cudaError_t launch_step_lattice(const StepArgs &a, const LatticeArgs &g, const L
         if (e_ != cudaSuccess) return e_;                                                                  \
         const uint64_t bit = dev < 64 ? (uint64_t)1 << dev : 0;                                            \
         if (!bit || !(opted.load() & bit)) {                                                               \
-            e_ = cudaFuncSetAttribute(k_step_lattice<F, R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+            e_ = cudaFuncSetAttribute(k_step_lattice<F, R, G, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                      (int)smem);                                                          \
             if (e_ != cudaSuccess) return e_;                                                              \
             if (bit) opted.fetch_or(bit);                                                                  \
         }                                                                                                  \
-        k_step_lattice<F, R, G><<<grid, kLatThreads, smem, st>>>(a, g, m.a[q], m.b[q], m.k);               \
+        k_step_lattice<F, R, G, A><<<grid, kLatThreads, smem, st>>>(a, g, m.a[q], m.b[q], m.k);            \
+    } while (0)
+#define MS_LAUNCH_L2(G, A)                                                                                 \
+    do {                                                                                                   \
+        if (a.integrator == 3) { if (hf) MS_LAUNCH_L(true, true, G, A); else MS_LAUNCH_L(false, true, G, A); } \
+        else { if (hf) MS_LAUNCH_L(true, false, G, A); else MS_LAUNCH_L(false, false, G, A); }             \
     } while (0)
     const bool hf = a.fext != nullptr;
-    if (g.guard) {
-        if (a.integrator == 3) { if (hf) MS_LAUNCH_L(true, true, true); else MS_LAUNCH_L(false, true, true); }
-        else { if (hf) MS_LAUNCH_L(true, false, true); else MS_LAUNCH_L(false, false, true); }
-    } else {
-        if (a.integrator == 3) { if (hf) MS_LAUNCH_L(true, true, false); else MS_LAUNCH_L(false, true, false); }
-        else { if (hf) MS_LAUNCH_L(true, false, false); else MS_LAUNCH_L(false, false, false); }
-    }
+    if (g.guard) { if (g.act) MS_LAUNCH_L2(true, true); else MS_LAUNCH_L2(true, false); }
+    else { if (g.act) MS_LAUNCH_L2(false, true); else MS_LAUNCH_L2(false, false); }
+#undef MS_LAUNCH_L2
 #undef MS_LAUNCH_L
     return cudaGetLastError();
 }
