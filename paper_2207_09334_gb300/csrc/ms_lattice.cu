@@ -13,10 +13,13 @@
 //     staged in shared memory; a partner in direction d is then the shared
 //     entry at a constant offset, with no index stored anywhere;
 //   * the CTAs are persistent (two per multiprocessor) and walk the bricks
-//     in raster order; while the threads compute brick n, two TMA tensor
-//     copies (one elected thread, completing on an mbarrier) stage brick
-//     n + 1's block into the other shared buffer, and a TMA prefetch brings
-//     its stiffness into L2, so no warp waits for DRAM at a brick's start;
+//     in raster order through two shared buffers: two TMA tensor copies
+//     (completing on the buffer's mbarrier) stage a brick's block, and a TMA
+//     prefetch brings its stiffness into L2.  There is no block-wide barrier
+//     between bricks: a warp done with brick n goes on to brick n + 1 (staged
+//     in the other buffer), and the last warp done with brick n issues brick
+//     n + 2 into the freed buffer, so the warps drift apart by up to a brick
+//     and one warp's loads overlap another's arithmetic;
 //   * a thread walks the 3 x 3 columns around its pair and reads the four
 //     cells z - 1 .. z + 2 of each column once: they are partners of a (z - 1
 //     .. z + 1) and of b (z .. z + 2), so each shared-memory read of a partner
@@ -100,7 +103,9 @@ __device__ __forceinline__ float spring_L(const LatticeArgs &g, int i, float s_n
 // A partner without a mass (at kLatEmptyPos, k = 0) gives l^2 = +inf, 1/l = 0
 // and s = 0.  A spring of zero length adds nothing: GUARD turns its NaN into
 // 0 (as it does for k = NaN, a missing spring between two masses); without
-// GUARD, l^2 is raised to 1e-30, s stays finite and d = 0.
+// GUARD, 1e-30 is added into l^2 (in the FMA that forms dz^2, so it costs no
+// instruction and leaves any l^2 above about 1e-22 as it was, up to the
+// rounding of an exact tie), s stays finite and d = 0.
 constexpr float kLatMinL2 = 1e-30f;
 
 // A mass as the spring terms use it: the negated pairs (-x, -y), (-z, -vx) and
@@ -125,8 +130,8 @@ __device__ __forceinline__ float lattice_term(const Own &o, const float4 pa, con
     const float2 zv = __fadd2_rn(make_float2(pa.z, pa.w), o.nzv);       // (dz, dvx)
     const float2 vyz = __fadd2_rn(pb, o.nvyz);                          // (dvy, dvz)
     dz = zv.x;
-    const float l2 = fmaf(dxy.x, dxy.x, fmaf(dxy.y, dxy.y, dz * dz));
-    const float il = rsqrt_hw(GUARD ? l2 : fmaxf(l2, kLatMinL2));
+    const float l2 = fmaf(dxy.x, dxy.x, fmaf(dxy.y, dxy.y, GUARD ? dz * dz : fmaf(dz, dz, kLatMinL2)));
+    const float il = rsqrt_hw(l2);
     const float dot = fmaf(zv.y, dxy.x, fmaf(vyz.x, dxy.y, vyz.y * dz));
     const float s = fmaf(fmaf(c * dot, il, -(k * L)), il, k);
     if (GUARD) return s == s ? s : 0.0f;
@@ -149,8 +154,8 @@ __device__ __forceinline__ void add_term(const Own &o, const float4 pa, const fl
 // themselves: a's spring to z - 1, the a-b spring once, b's spring to z + 2.
 template <bool GUARD, bool ACT, int DX, int DY>
 __device__ __forceinline__ void column(const LatticeArgs &g, const float4 *spa, const float2 *spb, int sa_, int ia,
-                                       int ib, const Own &oa, const Own &ob, const float4 xb, const float3 vb,
-                                       float s_n, float c_n, Force &Fa, Force &Fb)
+                                       int ib, const Own &oa, const Own &ob, float s_n, float c_n, Force &Fa,
+                                       Force &Fb)
 {
     const int c0 = sa_ + halo_off(DX, DY, 0);
     const float c = g.c;
@@ -176,7 +181,7 @@ __device__ __forceinline__ void column(const LatticeArgs &g, const float4 *spa, 
         // the a-b spring, once: +s d on a, -s d on b
         float2 dxy;
         float dz;
-        const float s = lattice_term<GUARD>(oa, make_float4(xb.x, xb.y, xb.z, vb.x), make_float2(vb.y, vb.z),
+        const float s = lattice_term<GUARD>(oa, spa[c0 + halo_off(0, 0, 1)], spb[c0 + halo_off(0, 0, 1)],
                                             __ldg(g.kf[fwd_index(0, 0, 1)] + ia),
                                             spring_L<ACT, 0, 0, 1>(g, ia, s_n, c_n), c, dxy, dz);
         Fa.xy = __ffma2_rn(make_float2(s, s), dxy, Fa.xy);
@@ -194,20 +199,19 @@ __device__ __forceinline__ void column(const LatticeArgs &g, const float4 *spa, 
 // all springs of the pair (a, b), column by column
 template <bool GUARD, bool ACT>
 __device__ __forceinline__ void pair_forces(const LatticeArgs &g, const float4 *spa, const float2 *spb, int s0, int ia,
-                                            int ib, const float4 xa, const float3 va, const float4 xb,
-                                            const float3 vb, float s_n, float c_n, float3 &Fa3, float3 &Fb3)
+                                            int ib, const Own &oa, const Own &ob, float s_n, float c_n,
+                                            float3 &Fa3, float3 &Fb3)
 {
-    const Own oa = own_of(xa, va), ob = own_of(xb, vb);
     Force Fa{make_float2(0.f, 0.f), 0.f}, Fb = Fa;
-    column<GUARD, ACT, -1, -1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, s_n, c_n, Fa, Fb);
-    column<GUARD, ACT,  0, -1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, s_n, c_n, Fa, Fb);
-    column<GUARD, ACT,  1, -1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, s_n, c_n, Fa, Fb);
-    column<GUARD, ACT, -1,  0>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, s_n, c_n, Fa, Fb);
-    column<GUARD, ACT,  0,  0>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, s_n, c_n, Fa, Fb);
-    column<GUARD, ACT,  1,  0>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, s_n, c_n, Fa, Fb);
-    column<GUARD, ACT, -1,  1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, s_n, c_n, Fa, Fb);
-    column<GUARD, ACT,  0,  1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, s_n, c_n, Fa, Fb);
-    column<GUARD, ACT,  1,  1>(g, spa, spb, s0, ia, ib, oa, ob, xb, vb, s_n, c_n, Fa, Fb);
+    column<GUARD, ACT, -1, -1>(g, spa, spb, s0, ia, ib, oa, ob, s_n, c_n, Fa, Fb);
+    column<GUARD, ACT,  0, -1>(g, spa, spb, s0, ia, ib, oa, ob, s_n, c_n, Fa, Fb);
+    column<GUARD, ACT,  1, -1>(g, spa, spb, s0, ia, ib, oa, ob, s_n, c_n, Fa, Fb);
+    column<GUARD, ACT, -1,  0>(g, spa, spb, s0, ia, ib, oa, ob, s_n, c_n, Fa, Fb);
+    column<GUARD, ACT,  0,  0>(g, spa, spb, s0, ia, ib, oa, ob, s_n, c_n, Fa, Fb);
+    column<GUARD, ACT,  1,  0>(g, spa, spb, s0, ia, ib, oa, ob, s_n, c_n, Fa, Fb);
+    column<GUARD, ACT, -1,  1>(g, spa, spb, s0, ia, ib, oa, ob, s_n, c_n, Fa, Fb);
+    column<GUARD, ACT,  0,  1>(g, spa, spb, s0, ia, ib, oa, ob, s_n, c_n, Fa, Fb);
+    column<GUARD, ACT,  1,  1>(g, spa, spb, s0, ia, ib, oa, ob, s_n, c_n, Fa, Fb);
     Fa3 = make_float3(Fa.xy.x, Fa.xy.y, Fa.z);
     Fb3 = make_float3(Fb.xy.x, Fb.xy.y, Fb.z);
 }
@@ -219,6 +223,7 @@ constexpr uint32_t kStageCopied = kStageA + kStageB;            // bytes the two
 constexpr uint32_t kStageBytes = (kStageCopied + 127) / 128 * 128;   // stage stride: copies land 128-byte aligned
 static_assert(kStageA % 128 == 0 && kStageBytes % 128 == 0, "tensor copies need 128-byte aligned destinations");
 constexpr int kLatCtasPerSm = 2;
+constexpr int kLatWarps = kLatThreads / 32;
 
 template <bool HAS_FEXT, bool RK4, bool GUARD, bool ACT>
 __global__ void __launch_bounds__(kLatThreads, kLatCtasPerSm)
@@ -227,8 +232,10 @@ k_step_lattice(const StepArgs a, const LatticeArgs g, const __grid_constant__ CU
 {
     extern __shared__ __align__(128) unsigned char dyn[];
     __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int done[2];                       // warps done with each buffer, over all its uses
+    __shared__ int issued[2];                     // copies issued into each buffer
     __shared__ int give_up;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int nbricks = g.nbx * g.nby * g.nbz;
     const int XY = g.X * g.Y;
     // brick b: its staged block starts at padded cell (bx*16, by*8, bz*8)
@@ -244,60 +251,84 @@ k_step_lattice(const StepArgs a, const LatticeArgs g, const __grid_constant__ CU
         tma_load_4d(dst, &map_a, 0, ox, oy, oz, &bar[stage]);
         tma_load_3d(dst + kStageA, &map_b, ox, oy, oz, &bar[stage]);
         tma_prefetch_4d(&map_k, ox, oy, oz, 0);
+        ++issued[stage];
     };
     if (tid == 0) {
         give_up = 0;
+        done[0] = done[1] = 0;
+        issued[0] = issued[1] = 0;
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         mbar_fence_init();
+        if ((int)blockIdx.x < nbricks) issue(blockIdx.x, 0);
+        if ((int)(blockIdx.x + gridDim.x) < nbricks) issue(blockIdx.x + gridDim.x, 1);
     }
     __syncthreads();
-    if (tid == 0 && (int)blockIdx.x < nbricks) issue(blockIdx.x, 0);
     const int cx = tid % kBrickX, cy = (tid / kBrickX) % kBrickY, cz = 2 * (tid / (kBrickX * kBrickY));
     const int s0 = (cx + 1) + kHaloX * ((cy + 1) + kHaloY * (cz + 1));     // cell a; b is one layer up
     int n = 0;
+    // No block-wide barrier between bricks: a warp that is done with brick n
+    // goes on to brick n + 1 (already staged in the other buffer), and the last
+    // warp done with brick n refills its buffer with brick n + 2, so the warps
+    // drift apart by up to a brick and their load and arithmetic phases overlap.
     for (int b = blockIdx.x; b < nbricks; b += gridDim.x, ++n) {
         const int stage = n & 1;
-        if (tid == 0 && b + (int)gridDim.x < nbricks) {
-            fence_proxy_async();                  // the other buffer's reads (previous brick) are done
-            issue(b + gridDim.x, stage ^ 1);
-        }
         int ox, oy, oz;
         origin(b, ox, oy, oz);
         const int ia = (ox + cx + 1) + g.X * (oy + cy + 1) + XY * (oz + cz + 1), ib = ia + XY;
         const float wa = __ldg(&a.w[ia]), wb = __ldg(&a.w[ib]);
-        if (!mbar_wait(&bar[stage], (n >> 1) & 1)) give_up = 1;
+        if (!__all_sync(0xffffffffu, mbar_wait(&bar[stage], (n >> 1) & 1))) {   // warp-uniform
+            if (lane == 0) give_up = 1;
+            break;
+        }
         const float4 *spa = reinterpret_cast<const float4 *>(dyn + (size_t)stage * kStageBytes);
         const float2 *spb = reinterpret_cast<const float2 *>(dyn + (size_t)stage * kStageBytes + kStageA);
-        if ((wa == wa || wb == wb) && !give_up) {
+        if (wa == wa || wb == wb) {
+            // the pair's own states, negated (Own); the integration takes them back
+            // from there (negation is exact), so no second copy stays live
             const float4 p = spa[s0];
             const float2 q = spb[s0];
-            const float4 xa = make_float4(p.x, p.y, p.z, wa);
-            const float3 va = make_float3(p.w, q.x, q.y);
             const float4 r = spa[s0 + halo_off(0, 0, 1)];
             const float2 t = spb[s0 + halo_off(0, 0, 1)];
-            const float4 xb = make_float4(r.x, r.y, r.z, wb);
-            const float3 vb = make_float3(r.w, t.x, t.y);
+            const Own oa = own_of(p, make_float3(p.w, q.x, q.y)), ob = own_of(r, make_float3(r.w, t.x, t.y));
             float3 Fa, Fb;
-            pair_forces<GUARD, ACT>(g, spa, spb, s0, ia, ib, xa, va, xb, vb, a.s_n, a.c_n, Fa, Fb);
+            pair_forces<GUARD, ACT>(g, spa, spb, s0, ia, ib, oa, ob, a.s_n, a.c_n, Fa, Fb);
             float4 xn, vn;
             if (wa == wa) {
-                integrate_mass<HAS_FEXT, RK4>(a, ia, xa, make_float4(va.x, va.y, va.z, 0.f), Fa.x, Fa.y, Fa.z, xn, vn);
+                integrate_mass<HAS_FEXT, RK4>(a, ia, make_float4(-oa.nxy.x, -oa.nxy.y, -oa.nzv.x, wa),
+                                              make_float4(-oa.nzv.y, -oa.nvyz.x, -oa.nvyz.y, 0.f), Fa.x, Fa.y, Fa.z,
+                                              xn, vn);
                 store_mass(a, ia, xn, vn);
             }
             if (wb == wb) {
-                integrate_mass<HAS_FEXT, RK4>(a, ib, xb, make_float4(vb.x, vb.y, vb.z, 0.f), Fb.x, Fb.y, Fb.z, xn, vn);
+                integrate_mass<HAS_FEXT, RK4>(a, ib, make_float4(-ob.nxy.x, -ob.nxy.y, -ob.nzv.x, wb),
+                                              make_float4(-ob.nzv.y, -ob.nvyz.x, -ob.nvyz.y, 0.f), Fb.x, Fb.y, Fb.z,
+                                              xn, vn);
                 store_mass(a, ib, xn, vn);
             }
         }
-        __syncthreads();                          // this buffer is consumed before it is refilled
-        if (give_up) break;
+        // this warp's reads of the buffer are done; the last warp refills it
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            const int prev = atomicAdd(&done[stage], 1);
+            if ((prev + 1) % kLatWarps == 0) {
+                __threadfence_block();
+                const int nb = b + 2 * (int)gridDim.x;
+                if (nb < nbricks) {
+                    fence_proxy_async();
+                    issue(nb, stage);
+                }
+            }
+        }
     }
+    __syncthreads();
     if (give_up && tid == 0) {
-        // a stage never landed: flag it, and give the copy issued for the next
-        // brick a bounded chance to land before the shared memory is released
+        // a stage never landed: flag it, and give the copies still in flight a
+        // bounded chance to land before the shared memory is released
         atomicOr(a.err, kErrTimeout);
-        mbar_wait(&bar[(n + 1) & 1], ((n + 1) >> 1) & 1);
+        for (int st = 0; st < 2; ++st)
+            if (issued[st] > 0) mbar_wait(&bar[st], (issued[st] - 1) & 1);
     }
 }
 
