@@ -6,8 +6,10 @@
 // and the force accumulator, 48 bytes per mass.  Spring records stay in
 // global memory and are re-read every step from L2: sliced-ELL rows (32
 // masses per slice, robot-local mass indices) in which every mass lists all
-// of its springs, both directions, so the force sum is one pass of coalesced
-// loads with no dependent back-reference gathers.  (The robot-by-robot loop
+// of its springs, both directions, one slot per lattice direction, so the
+// force sum is one pass of coalesced loads with no dependent back-reference
+// gathers, and a warp's partner reads from shared memory rarely collide in
+// a bank.  (The robot-by-robot loop
 // and the adjoint use the owner-row + back-reference layout.)  A step is
 // two phases separated by a barrier: every mass gathers its spring forces
 // from the shared-memory state at t_n (Jacobi, like the paper's grid-wide
@@ -667,6 +669,7 @@ ms_status build_voxels(const msb_voxel_spec *spec, int n_robots, const int32_t *
         h_kl.resize(h_nbr.size(), make_float2(0.f, 0.f));
         h_ab.resize(h_nbr.size(), make_float2(0.f, 0.f));
         h_c.resize(h_nbr.size(), 0.f);
+        std::vector<int8_t> rdir(h_nbr.size() - R.rec_base, -1);    // forward direction of each record
         std::vector<uint32_t> key_slot;
         if (adjoint_maps) {
             out.slot_vox.resize(h_nbr.size(), make_short4(-1, -1, -1, -1));
@@ -682,6 +685,7 @@ ms_status build_voxels(const msb_voxel_spec *spec, int n_robots, const int32_t *
                 const int j = cmap[(ox + dirs[d].dx) + cx * ((oy + dirs[d].dy) + cy * (oz + dirs[d].dz))];
                 const uint32_t rr = h_slice[slice0 + (o >> 5)].x + 32u * slot + (uint32_t)(o & 31);
                 h_nbr[rr] = j;
+                rdir[rr - R.rec_base] = (int8_t)d;
                 h_kl[rr] = make_float2((float)K[key], L0dir[d]);
                 h_c[rr] = (float)Cc[key];
                 h_ab[rr] = K[key] > 0 ? make_float2((float)(SA[key] / K[key]), (float)(SB[key] / K[key])) : make_float2(0.f, 0.f);
@@ -714,34 +718,59 @@ ms_status build_voxels(const msb_voxel_spec *spec, int n_robots, const int32_t *
             }
         }
         if (!adjoint_maps) {
-            // every-spring rows: per mass its own records, then its back
-            // references (in b_ent order), then padding pointing at itself
-            for (int s_ = 0; s_ < ns; ++s_) {
-                int mx = 0;
-                for (int l = 0; l < 32 && 32 * s_ + l < n; ++l) mx = std::max(mx, deg[32 * s_ + l] + bdeg[32 * s_ + l]);
-                out.aslice.push_back(make_uint2((uint32_t)out.anbr.size(), (uint32_t)mx));
-                const size_t first = out.anbr.size();
-                out.anbr.resize(first + 32 * (size_t)mx, 0);
-                for (int l = 0; l < 32; ++l)
-                    for (int q = 0; q < mx; ++q) out.anbr[first + 32 * (size_t)q + l] = (uint16_t)std::min(32 * s_ + l, n - 1);
-            }
-            out.akl.resize(out.anbr.size(), make_float2(0.f, 0.f));
-            out.aab.resize(out.anbr.size(), make_float2(0.f, 0.f));
-            out.ac.resize(out.anbr.size(), 0.f);
+            // every-spring rows, one slot per lattice direction: slot q of a
+            // slice holds, for each of its 32 masses, the spring in direction
+            // D_q (the directions any of them has, in a fixed order: the 13
+            // forward ones, then their opposites), or padding that points at
+            // the mass itself.  The lanes of a warp then read partners at
+            // nearly the same offset from their own masses, so their
+            // shared-memory reads fall in distinct banks.  A mass sums its
+            // springs in this direction order.
+            std::vector<int> drec((size_t)n * 26, -1), dpart((size_t)n * 26, -1);
             for (int i = 0; i < n; ++i) {
-                const uint2 am = out.aslice[slice0 + (i >> 5)];
-                uint32_t w = am.x + (uint32_t)(i & 31);
-                auto put = [&](int partner, uint32_t rr) {
-                    out.anbr[w] = (uint16_t)partner;
-                    out.akl[w] = h_kl[rr]; out.aab[w] = h_ab[rr]; out.ac[w] = h_c[rr];
-                    w += 32u;
-                };
                 const uint32_t fbase = h_slice[slice0 + (i >> 5)].x + (uint32_t)(i & 31);
-                for (int s_ = 0; s_ < deg[i]; ++s_) put(h_nbr[fbase + 32u * s_], fbase + 32u * s_);
+                for (int s_ = 0; s_ < deg[i]; ++s_) {
+                    const uint32_t rr = fbase + 32u * s_;
+                    const int d = rdir[rr - R.rec_base];
+                    drec[(size_t)i * 26 + d] = (int)rr;
+                    dpart[(size_t)i * 26 + d] = h_nbr[rr];
+                }
                 const uint32_t bbase = h_slice[slice0 + (i >> 5)].y + (uint32_t)(i & 31);
                 for (int t = 0; t < bdeg[i]; ++t) {
                     const uint32_t e = h_b[bbase + 32u * t];
-                    put((int)(e & kRobotOwnerMask), rec0 + (e >> kRobotOwnerBits));
+                    const uint32_t rr = rec0 + (e >> kRobotOwnerBits);
+                    const int d = rdir[rr - R.rec_base];
+                    drec[(size_t)i * 26 + 13 + d] = (int)rr;
+                    dpart[(size_t)i * 26 + 13 + d] = (int)(e & kRobotOwnerMask);
+                }
+            }
+            for (int s_ = 0; s_ < ns; ++s_) {
+                uint32_t mask = 0;
+                for (int l = 0; l < 32 && 32 * s_ + l < n; ++l)
+                    for (int D = 0; D < 26; ++D)
+                        if (drec[(size_t)(32 * s_ + l) * 26 + D] >= 0) mask |= 1u << D;
+                const int mx = __builtin_popcount(mask);
+                out.aslice.push_back(make_uint2((uint32_t)out.anbr.size(), (uint32_t)mx));
+                const size_t first = out.anbr.size();
+                out.anbr.resize(first + 32 * (size_t)mx, 0);
+                out.akl.resize(out.anbr.size(), make_float2(0.f, 0.f));
+                out.aab.resize(out.anbr.size(), make_float2(0.f, 0.f));
+                out.ac.resize(out.anbr.size(), 0.f);
+                int q = 0;
+                for (int D = 0; D < 26; ++D) {
+                    if (!((mask >> D) & 1u)) continue;
+                    for (int l = 0; l < 32; ++l) {
+                        const int i = std::min(32 * s_ + l, n - 1);
+                        const size_t w = first + 32 * (size_t)q + l;
+                        const int rr = 32 * s_ + l < n ? drec[(size_t)i * 26 + D] : -1;
+                        if (rr >= 0) {
+                            out.anbr[w] = (uint16_t)dpart[(size_t)i * 26 + D];
+                            out.akl[w] = h_kl[rr]; out.aab[w] = h_ab[rr]; out.ac[w] = h_c[rr];
+                        } else {
+                            out.anbr[w] = (uint16_t)i;     // k = 0 and zero length: no force
+                        }
+                    }
+                    ++q;
                 }
             }
             if (out.anbr.size() >= (size_t)UINT32_MAX / 2) return fail(MS_ERR_ARG, "population too large for 32-bit record offsets");

@@ -181,9 +181,10 @@ __device__ __forceinline__ float4 robot_force(const Records &a, int slice_base, 
     return make_float4(fx, fy, fz, 0.f);
 }
 
-// The same force from the every-spring rows: the springs of mass i in the
-// order of robot_force (its own records, then the back references), so both
-// give bit-identical sums.
+// The same force from the every-spring rows: the springs of mass i one slot
+// per lattice direction (the 13 forward directions, then their opposites), so
+// the sum agrees with robot_force's (own records, then back references) up
+// to the rounding of a different order.
 template <int UNROLL = 1>
 __device__ __forceinline__ float4 robot_force_all(const AllRows &g, int slice_base, int i, const float4 *xs,
                                                   const float4 *vs, float s_n, float c_n)
