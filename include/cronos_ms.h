@@ -117,7 +117,7 @@ typedef struct {
     int32_t max_fwd_degree;    /* gather: most springs owned by one mass; tiled: most springs of one mass */
     int32_t max_back_degree;
     int32_t kernel;            /* 1 = gather, 2 = tiled, 3 = persistent, 4 = lattice */
-    int32_t n_tiles;           /* tiled: tiles; lattice: bricks of 16 x 8 x 8 cells */
+    int32_t n_tiles;           /* tiled: tiles; lattice: bricks of 16 x 16 x 8 cells */
     int32_t max_tile_local;    /* tiled: largest members + halo of a tile; lattice: cells staged per brick */
     int32_t lattice_guard;     /* lattice: 1 when some neighbouring masses have no spring between them
                                   (the kernel then tests every spring term), else 0 */

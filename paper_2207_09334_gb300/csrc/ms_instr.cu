@@ -121,39 +121,46 @@ __global__ void __launch_bounds__(kTileMasses) k_energy_tiled(const EnergyArgs a
     block_reduce(t, a.partial);
 }
 
-// lattice layout: one CTA per brick, one thread per cell; each spring once,
-// from the cell it leaves in a forward direction (k = NaN: no spring between
-// two masses; k = 0: a slot that touches a cell without a mass, or a spring
-// of zero stiffness, either way no energy)
-__global__ void __launch_bounds__(kBrickCells) k_energy_lattice(const EnergyArgs a, const LatticeArgs g)
+// lattice layout: the terms of cell i; each spring once, from the cell it
+// leaves in a forward direction (k = NaN: no spring between two masses; k = 0:
+// a slot that touches a cell without a mass, or a spring of zero stiffness,
+// either way no energy)
+__device__ __forceinline__ void lattice_cell_terms(const EnergyArgs &a, const LatticeArgs &g, int i, Terms &t)
+{
+    const float w = __ldg(&a.w[i]);
+    if (!(w == w)) return;                               // a cell without a mass
+    mass_terms(a, i, t);
+    const float4 xi = __ldg(&a.sa[i]);
+    float pe = 0.f;
+#pragma unroll
+    for (int d = 0; d < kLatDirs; ++d) {
+        const float k = __ldg(g.kf[d] + i);
+        if (!(k == k) || k == 0.f) continue;                // no spring, or one that adds no energy
+        const float4 xj = __ldg(&a.sa[i + lat_dx(d) + g.X * (lat_dy(d) + g.Y * lat_dz(d))]);
+        const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+        float L = g.L[d];
+        if (g.act) {                                        // the actuated rest length at t_n
+            const float2 ab = __ldg(g.abf[d] + i);
+            L = L * (1.0f + fmaf(ab.x, a.s_n, ab.y * a.c_n));
+        }
+        const float e = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - L;
+        pe += k * e * e;
+    }
+    t.pe += 0.5f * pe;
+}
+
+// one CTA per brick, each thread the two cells stacked in z that the step
+// kernel gives it
+__global__ void __launch_bounds__(kLatThreads) k_energy_lattice(const EnergyArgs a, const LatticeArgs g)
 {
     const int tid = threadIdx.x;
     const int b = blockIdx.x;
     const int bx = b % g.nbx, byz = b / g.nbx, by = byz % g.nby, bz = byz / g.nby;
-    const int cx = tid % kBrickX, cy = (tid / kBrickX) % kBrickY, cz = tid / (kBrickX * kBrickY);
+    const int cx = tid % kBrickX, cy = (tid / kBrickX) % kBrickY, cz = 2 * (tid / (kBrickX * kBrickY));
     const int i = (bx * kBrickX + cx + 1) + g.X * ((by * kBrickY + cy + 1) + g.Y * (bz * kBrickZ + cz + 1));
     Terms t{0.f, 0.f, 0.f, 0.f};
-    const float w = __ldg(&a.w[i]);
-    if (w == w) {                                        // a cell with a mass
-        mass_terms(a, i, t);
-        const float4 xi = __ldg(&a.sa[i]);
-        float pe = 0.f;
-#pragma unroll
-        for (int d = 0; d < kLatDirs; ++d) {
-            const float k = __ldg(g.kf[d] + i);
-            if (!(k == k) || k == 0.f) continue;            // no spring, or one that adds no energy
-            const float4 xj = __ldg(&a.sa[i + lat_dx(d) + g.X * (lat_dy(d) + g.Y * lat_dz(d))]);
-            const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-            float L = g.L[d];
-            if (g.act) {                                    // the actuated rest length at t_n
-                const float2 ab = __ldg(g.abf[d] + i);
-                L = L * (1.0f + fmaf(ab.x, a.s_n, ab.y * a.c_n));
-            }
-            const float e = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - L;
-            pe += k * e * e;
-        }
-        t.pe = 0.5f * pe;
-    }
+    lattice_cell_terms(a, g, i, t);
+    lattice_cell_terms(a, g, i + g.X * g.Y, t);
     block_reduce(t, a.partial);
 }
 
@@ -194,7 +201,7 @@ int energy_blocks(const EnergyArgs &a, const LatticeArgs *lat)
 cudaError_t launch_energy(const EnergyArgs &a, const LatticeArgs *lat, double *out, cudaStream_t s)
 {
     const int nb = energy_blocks(a, lat);
-    if (lat) k_energy_lattice<<<nb, kBrickCells, 0, s>>>(a, *lat);
+    if (lat) k_energy_lattice<<<nb, kLatThreads, 0, s>>>(a, *lat);
     else if (a.tiled) k_energy_tiled<<<nb, kTileMasses, 0, s>>>(a);
     else k_energy_gather<<<nb, kEnergyThreads, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();

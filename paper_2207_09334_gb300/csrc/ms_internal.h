@@ -135,11 +135,11 @@ struct StepArgs {
 //   * Cells without a mass have w = NaN, the position kLatEmptyPos on every
 //     axis and zero velocity; no kernel integrates them.
 constexpr int kKernelLattice = 4;
-constexpr int kBrickX = 16, kBrickY = 8, kBrickZ = 8;
-constexpr int kBrickCells = kBrickX * kBrickY * kBrickZ;        // 1024 cells per brick
-constexpr int kLatThreads = kBrickCells / 2;                    // 512: each thread two cells stacked in z
+constexpr int kBrickX = 16, kBrickY = 16, kBrickZ = 8;
+constexpr int kBrickCells = kBrickX * kBrickY * kBrickZ;        // 2048 cells per brick
+constexpr int kLatThreads = kBrickCells / 2;                    // 1024: each thread two cells stacked in z
 constexpr int kHaloX = kBrickX + 2, kHaloY = kBrickY + 2, kHaloZ = kBrickZ + 2;
-constexpr int kHaloCells = kHaloX * kHaloY * kHaloZ;            // 1800 cells staged per brick
+constexpr int kHaloCells = kHaloX * kHaloY * kHaloZ;            // 3240 cells staged per brick
 constexpr int kLatDirs = 13;
 // forward direction d: (1,0,0); then (dx,1,0) for dx = -1..1; then (dx,dy,1) for
 // dy = -1..1, dx = -1..1 -- the 13 offsets that are positive in (z, y, x) order

@@ -7,12 +7,14 @@
 // quarter of the spring bytes of the general (tiled) layout, which stores
 // partner indices and rest lengths and lists every spring at both masses.
 //
-// Bricks of 16 x 8 x 8 cells; 512 threads per brick, each thread two cells
+// Bricks of 16 x 16 x 8 cells; 1024 threads per brick, each thread two cells
 // stacked in z (a at z, b at z + 1):
-//   * the state of the brick and of its one-cell halo (18 x 10 x 10 cells) is
+//   * the state of the brick and of its one-cell halo (18 x 18 x 10 cells) is
 //     staged in shared memory; a partner in direction d is then the shared
 //     entry at a constant offset, with no index stored anywhere;
-//   * the CTAs are persistent (two per multiprocessor) and walk the bricks
+//   * the CTAs are persistent (one per multiprocessor: two stages of 76 KB;
+//     a brick of this size stages 1.58 cells per cell, against 1.76 for
+//     16 x 8 x 8 bricks at two CTAs per multiprocessor) and walk the bricks
 //     in raster order through two shared buffers: two TMA tensor copies
 //     (completing on the buffer's mbarrier) stage a brick's block, and a TMA
 //     prefetch brings its stiffness into L2.  There is no block-wide barrier
@@ -216,13 +218,13 @@ __device__ __forceinline__ void pair_forces(const LatticeArgs &g, const float4 *
     Fb3 = make_float3(Fb.xy.x, Fb.xy.y, Fb.z);
 }
 
-// one staged block: (x, y, z, vx) then (vy, vz) of the 18 x 10 x 10 cells
-constexpr uint32_t kStageA = kHaloCells * sizeof(float4);       // 28 800 bytes (a multiple of 128)
-constexpr uint32_t kStageB = kHaloCells * sizeof(float2);       // 14 400 bytes
+// one staged block: (x, y, z, vx) then (vy, vz) of the 18 x 18 x 10 cells
+constexpr uint32_t kStageA = kHaloCells * sizeof(float4);       // 51 840 bytes (a multiple of 128)
+constexpr uint32_t kStageB = kHaloCells * sizeof(float2);       // 25 920 bytes
 constexpr uint32_t kStageCopied = kStageA + kStageB;            // bytes the two copies of a stage bring
 constexpr uint32_t kStageBytes = (kStageCopied + 127) / 128 * 128;   // stage stride: copies land 128-byte aligned
 static_assert(kStageA % 128 == 0 && kStageBytes % 128 == 0, "tensor copies need 128-byte aligned destinations");
-constexpr int kLatCtasPerSm = 2;
+constexpr int kLatCtasPerSm = 1;
 constexpr int kLatWarps = kLatThreads / 32;
 
 template <bool HAS_FEXT, bool RK4, bool GUARD, bool ACT>

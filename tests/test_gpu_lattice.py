@@ -4,7 +4,7 @@ k stored per spring) against the FP64 oracle on identical seeded inputs.
 Gates are those of the other step tests: max |x_gpu - x_oracle| <= 1e-5 of the
 body size after a contact-free run, <= 1e-4 after 200 steps with ground
 contact (and the centre-of-mass displacement within 1 %).  The lattices are
-sized so that bricks of 16 x 8 x 8 cells are cut by a ragged tail on every
+sized so that bricks of 16 x 16 x 8 cells are cut by a ragged tail on every
 axis, and some have holes (cells without a mass, inside a brick) with or
 without missing springs between present masses.  A lattice where every pair
 of neighbouring masses has its spring runs the kernel without a per-term
@@ -88,7 +88,7 @@ def run_gpu(ms, s, p, n, chunks=1, integrator="symplectic_euler", kernel="lattic
 
 
 def test_ragged_throughput_lattice_200_steps(ms, ora):
-    """37 x 21 x 11 masses: 3 x 3 x 3 bricks, each axis ending in a partial
+    """37 x 21 x 11 masses: 3 x 2 x 2 bricks, each axis ending in a partial
     brick; gravity, anchored bottom layer, 200 steps in two calls."""
     s = ragged_lattice()
     p = synth.throughput_params()
