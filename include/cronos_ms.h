@@ -69,7 +69,7 @@ typedef struct {
     int32_t reorder;        /* mass order: 0 = library default (Morton for the tiled kernel, caller
                                order for the gather kernel), 1 = Morton order by initial position,
                                2 = caller order */
-    int32_t kernel;         /* 0 = library default: lattice (4) for a box lattice of at least 2^15
+    int32_t kernel;         /* 0 = library default: lattice (4) for a box lattice of at least 2^18
                                masses, else tiled (gather when a tile's partners do not fit shared
                                memory); 1 = gather, 2 = tiled (MS_ERR_ARG if a tile does not fit),
                                3 = persistent: all steps of one ms_step call in one launch.  Up to

@@ -210,7 +210,7 @@ bool finite3(const float *p) { return std::isfinite(p[0]) && std::isfinite(p[1])
 // host and without allocating device memory, that the network is a box
 // lattice of that form, and fills its arrays; build_lattice uploads them.
 // ---------------------------------------------------------------------------
-constexpr int32_t kLatticeAutoMin = 1 << 15;   // default kernel: lattice layout from 32^3 masses up
+constexpr int32_t kLatticeAutoMin = 1 << 18;   // default kernel: lattice layout from 64^3 masses up
 
 struct LatticeShape {
     int nx = 0, ny = 0, nz = 0, nbx = 0, nby = 0, nbz = 0, X = 0, Y = 0, Z = 0;

@@ -295,15 +295,15 @@ def test_actuating_then_stopping_a_lattice(ms, ora):
 
 
 def test_default_kernel_by_size(ms):
-    """With kernel 0 a box lattice takes the lattice layout from 2^15 masses
-    (32^3) and the tiled layout below; an irregular network of that size stays
+    """With kernel 0 a box lattice takes the lattice layout from 2^18 masses
+    (64^3) and the tiled layout below; an irregular network of that size stays
     tiled."""
     p = synth.throughput_params()
-    for dims, want in (((32, 32, 32), 4), ((31, 32, 32), 2)):
+    for dims, want in (((64, 64, 64), 4), ((63, 64, 64), 2)):
         s = ragged_lattice(nx=dims[0], ny=dims[1], nz=dims[2], seed=3)
         with ms.Sim(s, p) as sim:
             assert sim.info()["kernel"] == want, (dims, sim.info()["kernel"])
-    s = ragged_lattice(nx=32, ny=32, nz=32, seed=3)
+    s = ragged_lattice(nx=64, ny=64, nz=64, seed=3)
     s["x"] = s["x"] + np.float32(1e-4) * np.random.default_rng(3).standard_normal(s["x"].shape).astype(np.float32)
     with ms.Sim(s, p) as sim:
         assert sim.info()["kernel"] == 2
