@@ -240,7 +240,7 @@ k_step_lattice(const StepArgs a, const LatticeArgs g, const __grid_constant__ CU
     const int tid = threadIdx.x, lane = tid & 31;
     const int nbricks = g.nbx * g.nby * g.nbz;
     const int XY = g.X * g.Y;
-    // brick b: its staged block starts at padded cell (bx*16, by*8, bz*8)
+    // brick b: its staged block starts at padded cell (bx kBrickX, by kBrickY, bz kBrickZ)
     auto origin = [&](int b, int &ox, int &oy, int &oz) {
         const int bx = b % g.nbx, byz = b / g.nbx;
         ox = bx * kBrickX; oy = (byz % g.nby) * kBrickY; oz = (byz / g.nby) * kBrickZ;
