@@ -17,7 +17,7 @@ import numpy as np
 from .batch import Population
 from .surrogate import Surrogate
 
-__all__ = ["phase_field", "simulate_travel", "train", "screen", "r2"]
+__all__ = ["phase_field", "simulate_travel", "train", "screen", "top_indices", "r2"]
 
 
 def phase_field(side: int = 8):
@@ -91,9 +91,15 @@ def predict(net: Surrogate, materials, mu: float, sd: float):
     return mu + sd * out
 
 
+def top_indices(pred, top_frac: float):
+    """Indices of the top_frac (at least one) largest entries of pred, largest first."""
+    pred = np.asarray(pred)
+    k = max(1, int(round(top_frac * len(pred))))
+    top = np.argpartition(-pred, k - 1)[:k]
+    return top[np.argsort(-pred[top], kind="stable")]
+
+
 def screen(net: Surrogate, candidates, mu: float, sd: float, top_frac: float = 0.01):
     """Indices of the top_frac candidates by predicted travel, best first."""
     pred = predict(net, candidates, mu, sd)
-    k = max(1, int(round(top_frac * len(pred))))
-    top = np.argpartition(-pred, k - 1)[:k]
-    return top[np.argsort(-pred[top])], pred
+    return top_indices(pred, top_frac), pred
